@@ -1,0 +1,219 @@
+/*
+ * loops.h -- C ABI of the GB300 (sm_103a) LOOPS hybrid SpMM library, libloops.so.
+ *
+ * The operation is SpMM, C = A . B, with A sparse (CSR on input) and B dense with N columns
+ * (Sec. 2.1: c_ij = sum_k a_ik b_kj). A plan splits A into a row-wise CSR part and a
+ * vector-wise BCSR part of B_r x 1 tiles (the LOOPS format, Sec. 3.2.1; conversion,
+ * Algorithm 1), and the SpMM runs both parts on one GPU: the CSR part on CUDA cores (the
+ * AXPY row kernel of Sec. 3.3), the BCSR part on tensor cores (the outer-product tile kernel,
+ * Algorithms 2 and 3) -- FP64 DMMA, FP16/BF16 MMA with FP32 accumulation -- or, for FP32, on a
+ * register-blocked CUDA-core outer product. Each output row has exactly one writer, so the
+ * result is deterministic and needs no atomics (Sec. 3.4).
+ *
+ * Conventions shared by every entry point:
+ *  - Errors are returned as loops_status, never by aborting; loops_last_error() gives a
+ *    thread-local message for the last failing call of the calling thread.
+ *  - "device" pointers are CUDA global-memory pointers of the current device; "host"
+ *    pointers are ordinary CPU memory. Dense matrices are row-major with a leading
+ *    dimension (elements between consecutive rows), ld >= number of columns.
+ *  - Every GPU call is ordered on the given stream (NULL = legacy default stream) and does
+ *    not synchronise the device unless its comment says so.
+ *  - Element types per plan dtype:
+ *        dtype      A values stored   B, dC      C, dB, dvals   accumulation
+ *        LOOPS_F64  f64               f64        f64            f64 (DFMA / DMMA)
+ *        LOOPS_F32  f32               f32        f32            f32 (FFMA)
+ *        LOOPS_F16  f16 (x s_A)       f16        f32            f32 (HMMA)
+ *        LOOPS_BF16 bf16 (x s_A)      bf16       f32            f32 (HMMA)
+ *    s_A is a power-of-two plan scale (max|a| * s_A <= 2^14) that the epilogue divides out
+ *    exactly; the 16-bit dense operands may carry per-column power-of-two scales.
+ *  - Inputs must be finite: a zero slot of a BCSR tile multiplies its B row, and 0 * inf
+ *    is NaN under IEEE 754.
+ */
+#ifndef LOOPS_H
+#define LOOPS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A cudaStream_t (struct CUstream_st*); NULL means the legacy default stream. */
+typedef struct CUstream_st* loops_stream_t;
+
+typedef enum {
+  LOOPS_OK = 0,
+  LOOPS_ERR_INVALID_ARG = 1,  /* null pointer, negative size, bad leading dimension, ... */
+  LOOPS_ERR_INVALID_CSR = 2,  /* row_ptr not monotone / wrong ends, column out of range  */
+  LOOPS_ERR_UNSUPPORTED = 3,  /* dtype or size this build does not handle               */
+  LOOPS_ERR_OOM = 4,          /* a host or device allocation failed                     */
+  LOOPS_ERR_CUDA = 5,         /* a CUDA runtime call failed (message in last_error)     */
+  LOOPS_ERR_TIMEOUT = 6,      /* a bounded device-side wait gave up (see loops_plan_check) */
+  LOOPS_ERR_STATE = 7         /* destroyed / mismatched plan, or wrong call order       */
+} loops_status;
+
+typedef enum { LOOPS_F64 = 0, LOOPS_F32 = 1, LOOPS_F16 = 2, LOOPS_BF16 = 3 } loops_dtype;
+
+/* Sparse input A in CSR form, all arrays on the HOST and borrowed only for the call.
+ * row_ptr: int64[n_rows + 1], row_ptr[0] = 0, non-decreasing, row_ptr[n_rows] = nnz.
+ * col_idx: int32[nnz], 0 <= col < n_cols; columns may be unsorted and may repeat (repeats
+ *          are summed). vals: nnz values of type vals_dtype (LOOPS_F64 or LOOPS_F32). */
+typedef struct {
+  int64_t n_rows;
+  int64_t n_cols;
+  int64_t nnz;
+  const int64_t* row_ptr;
+  const int32_t* col_idx;
+  const void* vals;
+  loops_dtype vals_dtype;
+} loops_csr;
+
+/* Plan options; loops_plan_opts_default() fills the defaults.
+ * tau: split threshold on row-block density d = nnz_rb / distinct columns of the block
+ *      (nnz per B_r x 1 tile, the paper's block density, Sec. 4.2/4.5). A block with
+ *      nnz_rb >= tau * distinct_cols goes to the BCSR part. tau < 0: autotune (time
+ *      candidate thresholds on the plan's stream); +inf: CSR only (the pure vector-unit
+ *      configuration of Sec. 4.3); 0: every non-empty block BCSR (pure matrix unit).
+ * block_rows: B_r (tile height); 0 = default (8 for F64, 16 otherwise); F64 needs 8,
+ *      F16/BF16 need 16, F32 accepts 8 or 16.
+ * contiguous_split: paper mode (Eq. 1, Algorithm 1): rows [0, r_boundary) rounded up to a
+ *      multiple of B_r form the CSR part and every later row block is BCSR; tau ignored.
+ * want_backward: also build the transposed plan and keep A's pattern so that
+ *      loops_spmm_backward works. */
+typedef struct {
+  double tau;
+  int32_t block_rows;
+  int32_t contiguous_split;
+  int64_t r_boundary;
+  int32_t want_backward;
+  int32_t split_len;      /* CSR rows longer than this are split in segments; 0 = default */
+  int32_t reserved[6];
+} loops_plan_opts;
+
+typedef struct loops_plan_s* loops_plan_t;
+
+/* Counts describing a plan (loops_plan_info). */
+typedef struct {
+  loops_dtype dtype;
+  int32_t block_rows;      /* B_r */
+  int32_t k_pad;           /* tiles per block are padded to a multiple of this (MMA K) */
+  int32_t has_backward;
+  int64_t n_rows, n_cols, nnz, N;
+  double tau;              /* threshold actually used (after autotuning) */
+  double scale;            /* s_A */
+  int64_t n_csr_rows, nnz_csr;
+  int64_t n_row_blocks, n_tiles, nnz_bcsr;  /* n_tiles includes padding tiles */
+  int64_t n_split_rows, n_segments;
+  int64_t n_subnormal_vals;/* stored 16-bit A values that are subnormal */
+  int64_t device_bytes;    /* device memory owned by the plan */
+} loops_plan_info;
+
+/* Canonical partition (host arrays, malloc'ed by the library; release with
+ * loops_partition_free). csr_rows ascending; each CSR row keeps its entries in input order.
+ * rb_ids ascending; tiles of a block ordered by column; tile t of block b holds rows
+ * b*B_r .. b*B_r+B_r-1 in tile_val[t*B_r ...]; padding tiles have tile_col = -1 and zero
+ * values. Values are the stored (rounded, s_A-scaled) values converted to f64. */
+typedef struct {
+  int64_t n_rows, n_cols;
+  int32_t block_rows, k_pad;
+  double scale;
+  int64_t n_csr_rows, nnz_csr, n_row_blocks, n_tiles;
+  int32_t* csr_rows;
+  int64_t* csr_ptr;
+  int32_t* csr_col;
+  double* csr_val;
+  int32_t* rb_ids;
+  int64_t* rb_ptr;
+  int32_t* tile_col;
+  double* tile_val;
+} loops_partition;
+
+/* ---------------------------------------------------------------------------------------- */
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int32_t loops_version(void);
+
+/* Static description of a status code. */
+const char* loops_status_str(loops_status status);
+
+/* Thread-local message of the last failing call on this thread ("" if none). */
+const char* loops_last_error(void);
+
+/* Fill *opts with defaults: tau = 2.0, block_rows = 0, no contiguous split, no backward. */
+void loops_plan_opts_default(loops_plan_opts* opts);
+
+/* Host-only partition of A (Algorithm 1 with the structural split) -- no GPU needed.
+ * Produces exactly the arrays loops_plan would upload (in canonical order). tau must be
+ * >= 0 (no autotuning here). *out must be released with loops_partition_free. */
+loops_status loops_partition_host(const loops_csr* A, loops_dtype dtype,
+                                  const loops_plan_opts* opts, loops_partition* out);
+
+/* Release the arrays of a partition filled by loops_partition_host / loops_plan_export. */
+void loops_partition_free(loops_partition* part);
+
+/* Build a plan for C = A . B with B of N columns in `dtype` (Sec. 3.1 pipeline: choose the
+ * split, convert with Algorithm 1, upload). Validates A (LOOPS_ERR_INVALID_CSR). The plan
+ * owns all device memory it allocates. With tau < 0 the call times candidate splits on
+ * `stream` and synchronises it. On success *out is a new plan; on failure *out is NULL. */
+loops_status loops_plan(const loops_csr* A, int64_t N, loops_dtype dtype,
+                        const loops_plan_opts* opts, loops_stream_t stream, loops_plan_t* out);
+
+/* Release a plan and its device memory (synchronises the device first). NULL is a no-op. */
+loops_status loops_plan_destroy(loops_plan_t plan);
+
+/* Counts of the plan (host only, no GPU work). */
+loops_status loops_plan_info_get(loops_plan_t plan, loops_plan_info* out);
+
+/* Copy the plan's device arrays back and return them in canonical order (synchronises). */
+loops_status loops_plan_export(loops_plan_t plan, loops_partition* out);
+
+/* Replace A's values (same pattern as at plan time; host array of nnz values of
+ * vals_dtype, input order) and re-upload both parts (and the transposed plan). The plan
+ * scale s_A is kept; values are rounded into the plan dtype. Synchronises `stream`. */
+loops_status loops_plan_update_values(loops_plan_t plan, const void* vals, loops_dtype vals_dtype,
+                                      loops_stream_t stream);
+
+/* C = A . B. B: device, n_cols x N (row-major, ldb); C: device, n_rows x N (ldc); element
+ * types per the table above. Overwrites C (no accumulation into it). Stream-ordered. */
+loops_status loops_spmm(loops_plan_t plan, const void* B, int64_t ldb, void* C, int64_t ldc,
+                        loops_stream_t stream);
+
+/* As loops_spmm, for the 16-bit dtypes with per-column scales: B holds B'[:, j] = B[:, j] / s_j
+ * and col_scale (device, f32[N], or NULL for all ones) holds s_j; the epilogue writes
+ * C[:, j] = s_j * (A . B')[:, j]. For F64/F32 col_scale must be NULL. */
+loops_status loops_spmm_scaled(loops_plan_t plan, const void* B, int64_t ldb,
+                               const float* col_scale, void* C, int64_t ldc, loops_stream_t stream);
+
+/* End-to-end SpMM with HOST buffers: copies B (host, ideally pinned) to plan-owned device
+ * memory, runs loops_spmm, copies C back to host, and synchronises `stream` before
+ * returning. The staging buffers are allocated on the first call and kept by the plan. */
+loops_status loops_spmm_host(loops_plan_t plan, const void* B_host, int64_t ldb, void* C_host,
+                             int64_t ldc, loops_stream_t stream);
+
+/* Backward of C = A . B for a plan built with want_backward:
+ *   dB = A^T . dC  (transposed hybrid SpMM; dB device, n_cols x N, lddb; NULL to skip)
+ *   dvals[k] = <dC[i_k, :], B[j_k, :]>  (SDDMM on A's pattern, in A's input order;
+ *              dvals device, nnz elements of the C type; NULL to skip)
+ * dC: device, n_rows x N (lddc), B: device, n_cols x N (ldb), both in the plan dtype.
+ * Overwrites dB and dvals. Stream-ordered. */
+loops_status loops_spmm_backward(loops_plan_t plan, const void* dC, int64_t lddc, const void* B,
+                                 int64_t ldb, void* dB, int64_t lddb, void* dvals,
+                                 loops_stream_t stream);
+
+/* Per-column power-of-two scaling and cast for the 16-bit dtypes:
+ *   s_j = 2^ceil(log2 max_i |X_ij|) (1 for an all-zero column), Y_ij = round(X_ij / s_j).
+ * X: device f32, rows x cols (ldx); Y: device, y_dtype (LOOPS_F16 or LOOPS_BF16), ldy;
+ * col_scale: device f32[cols], written. Rounding is to nearest, ties to even. */
+loops_status loops_cast_scaled(const float* X, int64_t rows, int64_t cols, int64_t ldx,
+                               loops_dtype y_dtype, void* Y, int64_t ldy, float* col_scale,
+                               loops_stream_t stream);
+
+/* Read and clear the plan's device error word (synchronises `stream`): LOOPS_OK, or
+ * LOOPS_ERR_TIMEOUT when a bounded device-side wait gave up in an earlier launch. */
+loops_status loops_plan_check(loops_plan_t plan, loops_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LOOPS_H */

@@ -1,0 +1,362 @@
+"""GB300-native LOOPS hybrid SpMM (arxiv 2511.08158): Python binding of libloops.so.
+
+This module only marshals arguments into the C ABI declared in ``include/loops.h``; every
+step of the SpMM runs in the library's CUDA kernels. PyTorch is used for device memory and
+streams. If the library is not built, importing works but every call raises -- there is no
+CPU fallback.
+
+    plan = Plan(A, N=64, dtype="f64", tau=2.0, want_backward=True)
+    C = plan.spmm(B)                      # C = A . B on the current CUDA stream
+    dB, dvals = plan.backward(dC, B)      # A^T . dC and SDDMM(dC, B^T) on A's pattern
+    C = spmm(plan, vals, B)               # autograd-aware (LoopsSpMM)
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libloops.so")
+
+F64, F32, F16, BF16 = 0, 1, 2, 3
+_DT = {"f64": F64, "f32": F32, "f16": F16, "bf16": BF16}
+_ERR = {0: "LOOPS_OK", 1: "LOOPS_ERR_INVALID_ARG", 2: "LOOPS_ERR_INVALID_CSR", 3: "LOOPS_ERR_UNSUPPORTED",
+        4: "LOOPS_ERR_OOM", 5: "LOOPS_ERR_CUDA", 6: "LOOPS_ERR_TIMEOUT", 7: "LOOPS_ERR_STATE"}
+
+# symbols declared in include/loops.h (checked by the tests)
+EXPORTED = ["loops_version", "loops_status_str", "loops_last_error", "loops_plan_opts_default",
+            "loops_partition_host", "loops_partition_free", "loops_plan", "loops_plan_destroy",
+            "loops_plan_info_get", "loops_plan_export", "loops_plan_update_values", "loops_spmm",
+            "loops_spmm_scaled", "loops_spmm_host", "loops_spmm_backward", "loops_cast_scaled",
+            "loops_plan_check"]
+
+
+class LoopsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_ERR.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Csr(ctypes.Structure):
+    _fields_ = [("n_rows", ctypes.c_int64), ("n_cols", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("row_ptr", ctypes.c_void_p), ("col_idx", ctypes.c_void_p), ("vals", ctypes.c_void_p),
+                ("vals_dtype", ctypes.c_int)]
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("tau", ctypes.c_double), ("block_rows", ctypes.c_int32),
+                ("contiguous_split", ctypes.c_int32), ("r_boundary", ctypes.c_int64),
+                ("want_backward", ctypes.c_int32), ("split_len", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("dtype", ctypes.c_int), ("block_rows", ctypes.c_int32), ("k_pad", ctypes.c_int32),
+                ("has_backward", ctypes.c_int32), ("n_rows", ctypes.c_int64), ("n_cols", ctypes.c_int64),
+                ("nnz", ctypes.c_int64), ("N", ctypes.c_int64), ("tau", ctypes.c_double),
+                ("scale", ctypes.c_double), ("n_csr_rows", ctypes.c_int64), ("nnz_csr", ctypes.c_int64),
+                ("n_row_blocks", ctypes.c_int64), ("n_tiles", ctypes.c_int64), ("nnz_bcsr", ctypes.c_int64),
+                ("n_split_rows", ctypes.c_int64), ("n_segments", ctypes.c_int64),
+                ("n_subnormal_vals", ctypes.c_int64), ("device_bytes", ctypes.c_int64)]
+
+
+class _Part(ctypes.Structure):
+    _fields_ = [("n_rows", ctypes.c_int64), ("n_cols", ctypes.c_int64), ("block_rows", ctypes.c_int32),
+                ("k_pad", ctypes.c_int32), ("scale", ctypes.c_double), ("n_csr_rows", ctypes.c_int64),
+                ("nnz_csr", ctypes.c_int64), ("n_row_blocks", ctypes.c_int64), ("n_tiles", ctypes.c_int64),
+                ("csr_rows", ctypes.POINTER(ctypes.c_int32)), ("csr_ptr", ctypes.POINTER(ctypes.c_int64)),
+                ("csr_col", ctypes.POINTER(ctypes.c_int32)), ("csr_val", ctypes.POINTER(ctypes.c_double)),
+                ("rb_ids", ctypes.POINTER(ctypes.c_int32)), ("rb_ptr", ctypes.POINTER(ctypes.c_int64)),
+                ("tile_col", ctypes.POINTER(ctypes.c_int32)), ("tile_val", ctypes.POINTER(ctypes.c_double))]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return LIB_PATH
+
+
+def load():
+    """Load libloops.so (built by ``build()``); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libloops.so is not built: run paper_2511_08158_gb300.build() "
+                           "(or __graft_entry__.build()) first")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+    L.loops_version.restype = i32
+    L.loops_status_str.restype = ctypes.c_char_p
+    L.loops_status_str.argtypes = [ctypes.c_int]
+    L.loops_last_error.restype = ctypes.c_char_p
+    L.loops_plan_opts_default.argtypes = [ctypes.POINTER(_Opts)]
+    L.loops_plan_opts_default.restype = None
+    L.loops_partition_host.argtypes = [ctypes.POINTER(_Csr), ctypes.c_int, ctypes.POINTER(_Opts), ctypes.POINTER(_Part)]
+    L.loops_partition_free.argtypes = [ctypes.POINTER(_Part)]
+    L.loops_partition_free.restype = None
+    L.loops_plan.argtypes = [ctypes.POINTER(_Csr), i64, ctypes.c_int, ctypes.POINTER(_Opts), vp, ctypes.POINTER(vp)]
+    L.loops_plan_destroy.argtypes = [vp]
+    L.loops_plan_info_get.argtypes = [vp, ctypes.POINTER(_Info)]
+    L.loops_plan_export.argtypes = [vp, ctypes.POINTER(_Part)]
+    L.loops_plan_update_values.argtypes = [vp, vp, ctypes.c_int, vp]
+    L.loops_spmm.argtypes = [vp, vp, i64, vp, i64, vp]
+    L.loops_spmm_scaled.argtypes = [vp, vp, i64, vp, vp, i64, vp]
+    L.loops_spmm_host.argtypes = [vp, vp, i64, vp, i64, vp]
+    L.loops_spmm_backward.argtypes = [vp, vp, i64, vp, i64, vp, i64, vp, vp]
+    L.loops_cast_scaled.argtypes = [vp, i64, i64, i64, ctypes.c_int, vp, i64, vp, vp]
+    L.loops_plan_check.argtypes = [vp, vp]
+    for name in EXPORTED:
+        fn = getattr(L, name)
+        if name not in ("loops_version", "loops_status_str", "loops_last_error", "loops_plan_opts_default",
+                        "loops_partition_free"):
+            fn.restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(status: int):
+    if status != 0:
+        raise LoopsError(status, load().loops_last_error().decode())
+
+
+def _csr_struct(A):
+    """Host CSR arrays of A (attributes n_rows, n_cols, row_ptr, col_idx, vals) -> (_Csr, keepalive)."""
+    rp = np.ascontiguousarray(A.row_ptr, dtype=np.int64)
+    ci = np.ascontiguousarray(A.col_idx, dtype=np.int32)
+    v = np.ascontiguousarray(A.vals)
+    if v.dtype == np.float32:
+        vd = F32
+    else:
+        v = np.ascontiguousarray(v, dtype=np.float64)
+        vd = F64
+    s = _Csr(int(A.n_rows), int(A.n_cols), int(rp[-1]) if rp.size else 0, rp.ctypes.data, ci.ctypes.data,
+             v.ctypes.data, vd)
+    return s, (rp, ci, v)
+
+
+def _opts(tau=2.0, block_rows=0, contiguous_split=False, r_boundary=0, want_backward=False, split_len=0):
+    o = _Opts()
+    load().loops_plan_opts_default(ctypes.byref(o))
+    o.tau = float(tau)
+    o.block_rows = int(block_rows)
+    o.contiguous_split = int(bool(contiguous_split))
+    o.r_boundary = int(r_boundary)
+    o.want_backward = int(bool(want_backward))
+    o.split_len = int(split_len)
+    return o
+
+
+def _part_to_dict(p: _Part) -> dict:
+    def arr(ptr, n, dt):
+        return np.ctypeslib.as_array(ptr, shape=(n,)).astype(dt, copy=True) if n > 0 else np.zeros(0, dt)
+    br = int(p.block_rows)
+    out = dict(
+        csr_rows=arr(p.csr_rows, p.n_csr_rows, np.int32), csr_ptr=arr(p.csr_ptr, p.n_csr_rows + 1, np.int64),
+        csr_col=arr(p.csr_col, p.nnz_csr, np.int32), csr_val=arr(p.csr_val, p.nnz_csr, np.float64),
+        rb_ids=arr(p.rb_ids, p.n_row_blocks, np.int32), rb_ptr=arr(p.rb_ptr, p.n_row_blocks + 1, np.int64),
+        tile_col=arr(p.tile_col, p.n_tiles, np.int32),
+        tile_val=arr(p.tile_val, p.n_tiles * br, np.float64).reshape(int(p.n_tiles), br),
+        scale=float(p.scale), block_rows=br, k_pad=int(p.k_pad))
+    return out
+
+
+def partition_host(A, dtype: str = "f64", tau: float = 2.0, block_rows: int = 0, contiguous_split: bool = False,
+                   r_boundary: int = 0) -> dict:
+    """Host-only LOOPS partition (no GPU), canonical arrays as numpy."""
+    L = load()
+    cs, keep = _csr_struct(A)
+    o = _opts(tau, block_rows, contiguous_split, r_boundary)
+    part = _Part()
+    _check(L.loops_partition_host(ctypes.byref(cs), _DT[dtype], ctypes.byref(o), ctypes.byref(part)))
+    try:
+        return _part_to_dict(part)
+    finally:
+        L.loops_partition_free(ctypes.byref(part))
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_handle(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+_TORCH_IN = {F64: "float64", F32: "float32", F16: "float16", BF16: "bfloat16"}
+_TORCH_OUT = {F64: "float64", F32: "float32", F16: "float32", BF16: "float32"}
+
+
+class Plan:
+    """A LOOPS plan for C = A . B with B of N columns (``loops_plan``)."""
+
+    def __init__(self, A, N: int, dtype: str = "f64", tau: float = 2.0, block_rows: int = 0,
+                 want_backward: bool = False, contiguous_split: bool = False, r_boundary: int = 0,
+                 split_len: int = 0, stream=None):
+        L = load()
+        self._L = L
+        self.dtype = _DT[dtype]
+        self.dtype_name = dtype
+        self.N = int(N)
+        self.n_rows, self.n_cols = int(A.n_rows), int(A.n_cols)
+        self.nnz = int(np.asarray(A.row_ptr)[-1]) if len(A.row_ptr) else 0
+        cs, keep = _csr_struct(A)
+        o = _opts(tau, block_rows, contiguous_split, r_boundary, want_backward, split_len)
+        h = ctypes.c_void_p()
+        s = _stream_handle(stream) if _torch().cuda.is_available() else ctypes.c_void_p(0)
+        _check(L.loops_plan(ctypes.byref(cs), self.N, self.dtype, ctypes.byref(o), s, ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def destroy(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._L.loops_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        inf = _Info()
+        _check(self._L.loops_plan_info_get(self._h, ctypes.byref(inf)))
+        return {name: getattr(inf, name) for name, _ in _Info._fields_}
+
+    def export(self) -> dict:
+        part = _Part()
+        _check(self._L.loops_plan_export(self._h, ctypes.byref(part)))
+        try:
+            return _part_to_dict(part)
+        finally:
+            self._L.loops_partition_free(ctypes.byref(part))
+
+    def check(self, stream=None):
+        _check(self._L.loops_plan_check(self._h, _stream_handle(stream)))
+
+    def update_values(self, vals, stream=None):
+        v = np.ascontiguousarray(vals)
+        vd = F32 if v.dtype == np.float32 else F64
+        if vd == F64:
+            v = np.ascontiguousarray(v, dtype=np.float64)
+        _check(self._L.loops_plan_update_values(self._h, v.ctypes.data, vd, _stream_handle(stream)))
+
+    def out_dtype(self):
+        return getattr(_torch(), _TORCH_OUT[self.dtype])
+
+    def in_dtype(self):
+        return getattr(_torch(), _TORCH_IN[self.dtype])
+
+    def _check_dense(self, X, rows, name):
+        torch = _torch()
+        if not (isinstance(X, torch.Tensor) and X.is_cuda):
+            raise TypeError(f"{name} must be a CUDA tensor")
+        if X.dtype != self.in_dtype():
+            raise TypeError(f"{name} must be {self.in_dtype()} for this plan")
+        if X.dim() != 2 or X.shape[0] != rows or X.shape[1] != self.N or X.stride(1) != 1:
+            raise ValueError(f"{name} must be {rows} x {self.N} with unit column stride")
+
+    def spmm(self, B, C=None, col_scale=None, stream=None):
+        """C = A . B (device tensors; C allocated if not given). col_scale: optional f32[N] device
+        tensor of per-column scales (16-bit dtypes)."""
+        torch = _torch()
+        self._check_dense(B, self.n_cols, "B")
+        if C is None:
+            C = torch.empty((self.n_rows, self.N), dtype=self.out_dtype(), device=B.device)
+        cs = 0 if col_scale is None else col_scale.data_ptr()
+        _check(self._L.loops_spmm_scaled(self._h, B.data_ptr(), B.stride(0), cs, C.data_ptr(), C.stride(0),
+                                         _stream_handle(stream)))
+        return C
+
+    def spmm_host(self, B_host, C_host, stream=None):
+        """End-to-end C = A . B with host (ideally pinned) CPU tensors; synchronises."""
+        _check(self._L.loops_spmm_host(self._h, B_host.data_ptr(), B_host.stride(0), C_host.data_ptr(),
+                                       C_host.stride(0), _stream_handle(stream)))
+        return C_host
+
+    def backward(self, dC, B, need_dB=True, need_dvals=True, stream=None):
+        """(dB, dvals) = (A^T . dC, <dC[i_k], B[j_k]> per stored entry in input order)."""
+        torch = _torch()
+        self._check_dense(dC, self.n_rows, "dC")
+        dB = dv = None
+        if need_dB:
+            dB = torch.empty((self.n_cols, self.N), dtype=self.out_dtype(), device=dC.device)
+        if need_dvals:
+            self._check_dense(B, self.n_cols, "B")
+            dv = torch.empty((self.nnz,), dtype=self.out_dtype(), device=dC.device)
+        _check(self._L.loops_spmm_backward(
+            self._h, dC.data_ptr(), dC.stride(0), B.data_ptr() if B is not None else 0,
+            B.stride(0) if B is not None else self.N, dB.data_ptr() if dB is not None else 0,
+            dB.stride(0) if dB is not None else self.N, dv.data_ptr() if dv is not None else 0,
+            _stream_handle(stream)))
+        return dB, dv
+
+
+def cast_scaled(X, dtype: str = "f16", stream=None):
+    """(Y, s): s_j = 2^ceil(log2 max|X[:, j]|), Y = round(X / s) in f16/bf16 (``loops_cast_scaled``)."""
+    torch = _torch()
+    L = load()
+    if X.dtype != torch.float32 or not X.is_cuda or X.dim() != 2 or X.stride(1) != 1:
+        raise TypeError("X must be a 2-D float32 CUDA tensor with unit column stride")
+    yd = _DT[dtype]
+    Y = torch.empty(X.shape, dtype=torch.float16 if yd == F16 else torch.bfloat16, device=X.device)
+    s = torch.empty((X.shape[1],), dtype=torch.float32, device=X.device)
+    _check(L.loops_cast_scaled(X.data_ptr(), X.shape[0], X.shape[1], X.stride(0), yd, Y.data_ptr(), Y.stride(0),
+                               s.data_ptr(), _stream_handle(stream)))
+    return Y, s
+
+
+def _autograd_fn():
+    torch = _torch()
+
+    class LoopsSpMM(torch.autograd.Function):
+        """C = A(vals) . B with the plan's pattern. Backward: dB = A^T . dC (transposed hybrid
+        SpMM), dvals = SDDMM(dC, B^T) on A's pattern. ``vals`` must equal the plan's values
+        (use Plan.update_values after changing them)."""
+
+        @staticmethod
+        def forward(ctx, vals, B, plan):
+            ctx.plan = plan
+            ctx.save_for_backward(B)
+            return plan.spmm(B.contiguous())
+
+        @staticmethod
+        def backward(ctx, dC):
+            (B,) = ctx.saved_tensors
+            plan = ctx.plan
+            dC = dC.to(plan.in_dtype()).contiguous()
+            dB, dv = plan.backward(dC, B.contiguous(), need_dB=ctx.needs_input_grad[1],
+                                   need_dvals=ctx.needs_input_grad[0])
+            if dB is not None:
+                dB = dB.to(B.dtype)
+            return dv, dB, None
+
+    return LoopsSpMM
+
+
+_FN = None
+
+
+def spmm(plan: Plan, vals, B):
+    """Autograd-aware C = A . B (LoopsSpMM)."""
+    global _FN
+    if _FN is None:
+        _FN = _autograd_fn()
+    return _FN.apply(vals, B, plan)
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile libloops.so for sm_103a (see builder.py)."""
+    from .builder import build as _build
+    return _build(force=force, verbose=verbose)

@@ -1,0 +1,597 @@
+// C-ABI entry points of libloops.so (declared in include/loops.h).
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+
+#include "loops_internal.h"
+
+namespace loops {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+void clear_error() { g_last_error.clear(); }
+
+loops_status export_part(const loops_plan_s* p, loops_partition* out);
+loops_status autotune_tau(const loops_csr* A, const double* vals, int64_t N, loops_dtype dtype,
+                          int32_t br, int32_t split_len, cudaStream_t s, double* tau_out);
+
+static loops_status cuda_status(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return LOOPS_OK;
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? LOOPS_ERR_OOM : LOOPS_ERR_CUDA;
+}
+
+static bool valid_dtype(loops_dtype d) {
+  return d == LOOPS_F64 || d == LOOPS_F32 || d == LOOPS_F16 || d == LOOPS_BF16;
+}
+
+static loops_status check_plan(loops_plan_t p) {
+  if (!p || p->magic != kPlanMagic) {
+    set_error("invalid or destroyed plan handle");
+    return LOOPS_ERR_STATE;
+  }
+  return LOOPS_OK;
+}
+
+static void fill_partition(const Canon& c, loops_partition* out) {
+  std::memset(out, 0, sizeof(*out));
+  out->n_rows = c.n_rows;
+  out->n_cols = c.n_cols;
+  out->block_rows = c.br;
+  out->k_pad = c.kpad;
+  out->scale = c.scale;
+  out->n_csr_rows = (int64_t)c.csr_rows.size();
+  out->nnz_csr = (int64_t)c.csr_col.size();
+  out->n_row_blocks = (int64_t)c.rb_ids.size();
+  out->n_tiles = (int64_t)c.tile_col.size();
+  auto dup = [](const void* src, size_t bytes) {
+    void* d = std::malloc(bytes ? bytes : 1);
+    if (bytes) std::memcpy(d, src, bytes);
+    return d;
+  };
+  out->csr_rows = (int32_t*)dup(c.csr_rows.data(), c.csr_rows.size() * 4);
+  out->csr_ptr = (int64_t*)dup(c.csr_ptr.data(), c.csr_ptr.size() * 8);
+  out->csr_col = (int32_t*)dup(c.csr_col.data(), c.csr_col.size() * 4);
+  out->csr_val = (double*)dup(c.csr_val.data(), c.csr_val.size() * 8);
+  out->rb_ids = (int32_t*)dup(c.rb_ids.data(), c.rb_ids.size() * 4);
+  out->rb_ptr = (int64_t*)dup(c.rb_ptr.data(), c.rb_ptr.size() * 8);
+  out->tile_col = (int32_t*)dup(c.tile_col.data(), c.tile_col.size() * 4);
+  out->tile_val = (double*)dup(c.tile_val.data(), c.tile_val.size() * 8);
+}
+
+static loops_status resolve_block_rows(loops_dtype dtype, const loops_plan_opts& o, int32_t* br) {
+  int32_t b = o.block_rows ? o.block_rows : default_block_rows(dtype);
+  const bool ok = (dtype == LOOPS_F64 && b == 8) || ((dtype == LOOPS_F16 || dtype == LOOPS_BF16) && b == 16) ||
+                  (dtype == LOOPS_F32 && (b == 8 || b == 16));
+  if (!ok) {
+    set_error("unsupported block_rows " + std::to_string(b) + " for this dtype");
+    return LOOPS_ERR_UNSUPPORTED;
+  }
+  *br = b;
+  return LOOPS_OK;
+}
+
+static void destroy_plan(loops_plan_s* p) {
+  if (!p) return;
+  if (p->transposed) destroy_plan(p->transposed);
+  free_part(p->dev);
+  void* ptrs[] = {p->sddmm.item_row, p->sddmm.item_beg, p->sddmm.item_end, p->sddmm.col,
+                  p->d_error, p->stage_B, p->stage_C};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  if (p->side) cudaStreamDestroy(p->side);
+  if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+  if (p->ev_join) cudaEventDestroy(p->ev_join);
+  p->magic = 0;
+  delete p;
+}
+
+// Builds a single (non-transposed) plan from validated input and f64 values.
+static loops_status make_plan(const loops_csr* A, const double* vals, int64_t N, loops_dtype dtype,
+                              const loops_plan_opts& o, int32_t br, double tau, loops_plan_s** out) {
+  *out = nullptr;
+  loops_plan_s* p = new (std::nothrow) loops_plan_s();
+  if (!p) { set_error("host allocation failed"); return LOOPS_ERR_OOM; }
+  p->magic = kPlanMagic;
+  p->dtype = dtype;
+  p->n_rows = A->n_rows;
+  p->n_cols = A->n_cols;
+  p->nnz = A->nnz;
+  p->N = N;
+  p->br = br;
+  p->kpad = k_pad_for(dtype);
+  p->tau = tau;
+  p->opts = o;
+  p->split_len = o.split_len > 0 ? o.split_len : 512;
+  p->transposed = nullptr;
+  p->d_error = nullptr;
+  p->side = nullptr;
+  p->ev_fork = p->ev_join = nullptr;
+  p->stage_B = p->stage_C = nullptr;
+  p->stage_B_bytes = p->stage_C_bytes = 0;
+  loops_status st = build_canon(A, vals, dtype, br, tau, o.contiguous_split != 0, o.r_boundary, p->canon);
+  if (st) { destroy_plan(p); return st; }
+  p->scale = p->canon.scale;
+  p->n_subnormal = 0;
+  if (dtype == LOOPS_F16 || dtype == LOOPS_BF16) {
+    const double tiny = dtype == LOOPS_F16 ? std::ldexp(1.0, -14) : std::ldexp(1.0, -126);
+    for (double v : p->canon.csr_val) p->n_subnormal += (v != 0.0 && std::fabs(v) < tiny);
+    for (double v : p->canon.tile_val) p->n_subnormal += (v != 0.0 && std::fabs(v) < tiny);
+  }
+  p->nnz_bcsr = 0;
+  for (uint8_t k : p->canon.src_kind) p->nnz_bcsr += k;
+  if ((st = upload_part(p, N))) { destroy_plan(p); return st; }
+  cudaError_t e = cudaMalloc((void**)&p->d_error, sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMemset(p->d_error, 0, sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming);
+  if (e != cudaSuccess) { st = cuda_status(e, "plan setup"); destroy_plan(p); return st; }
+  p->dev.device_bytes += sizeof(int32_t);
+  *out = p;
+  return LOOPS_OK;
+}
+
+// A^T in CSR (stable counting sort by column): entry e of A^T comes from input entry perm[e].
+static void transpose_csr(const loops_csr* A, std::vector<int64_t>& rp, std::vector<int32_t>& ci,
+                          std::vector<int64_t>& perm) {
+  rp.assign((size_t)A->n_cols + 1, 0);
+  for (int64_t k = 0; k < A->nnz; ++k) rp[(size_t)A->col_idx[k] + 1]++;
+  for (int64_t j = 0; j < A->n_cols; ++j) rp[(size_t)j + 1] += rp[(size_t)j];
+  std::vector<int64_t> pos(rp.begin(), rp.end() - 1);
+  ci.resize((size_t)A->nnz);
+  perm.resize((size_t)A->nnz);
+  for (int64_t i = 0; i < A->n_rows; ++i)
+    for (int64_t k = A->row_ptr[i]; k < A->row_ptr[i + 1]; ++k) {
+      const int64_t e = pos[(size_t)A->col_idx[k]]++;
+      ci[(size_t)e] = (int32_t)i;
+      perm[(size_t)e] = k;
+    }
+}
+
+static loops_status build_sddmm(loops_plan_s* p, const loops_csr* A) {
+  std::vector<int32_t> row;
+  std::vector<int64_t> beg, end;
+  struct It { int32_t r; int64_t b, e; };
+  std::vector<It> it;
+  const int64_t L = p->split_len;
+  for (int64_t i = 0; i < A->n_rows; ++i)
+    for (int64_t b = A->row_ptr[i]; b < A->row_ptr[i + 1]; b += L)
+      it.push_back({(int32_t)i, b, std::min(b + L, A->row_ptr[i + 1])});
+  std::stable_sort(it.begin(), it.end(), [](const It& x, const It& y) { return x.e - x.b > y.e - y.b; });
+  for (auto& x : it) { row.push_back(x.r); beg.push_back(x.b); end.push_back(x.e); }
+  p->sddmm.n_items = (int64_t)it.size();
+  auto up = [&](void** dst, const void* src, size_t bytes) -> loops_status {
+    if (!bytes) { *dst = nullptr; return LOOPS_OK; }
+    cudaError_t e = cudaMalloc(dst, bytes);
+    if (e == cudaSuccess) e = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) p->dev.device_bytes += (int64_t)bytes;
+    return cuda_status(e, "upload SDDMM pattern");
+  };
+  loops_status st;
+  if ((st = up((void**)&p->sddmm.item_row, row.data(), row.size() * 4))) return st;
+  if ((st = up((void**)&p->sddmm.item_beg, beg.data(), beg.size() * 8))) return st;
+  if ((st = up((void**)&p->sddmm.item_end, end.data(), end.size() * 8))) return st;
+  if ((st = up((void**)&p->sddmm.col, A->col_idx, (size_t)A->nnz * 4))) return st;
+  return LOOPS_OK;
+}
+
+static loops_status check_dense(const void* ptr, int64_t rows, int64_t N, int64_t ld, const char* name) {
+  if (ld < N || ld < 0) {
+    set_error(std::string("leading dimension of ") + name + " is smaller than N");
+    return LOOPS_ERR_INVALID_ARG;
+  }
+  if (!ptr && rows > 0 && N > 0) {
+    set_error(std::string(name) + " is NULL");
+    return LOOPS_ERR_INVALID_ARG;
+  }
+  return LOOPS_OK;
+}
+
+// Run C = A.B on the plan: BCSR part on the side stream, CSR part on `s`, joined by events.
+static loops_status run_spmm(loops_plan_s* p, const void* B, int64_t ldb, const float* col_scale,
+                             void* C, int64_t ldc, cudaStream_t s) {
+  if (p->n_rows == 0 || p->N == 0) return LOOPS_OK;
+  DenseArgs a;
+  a.B = B;
+  a.ldb = ldb;
+  a.C = C;
+  a.ldc = ldc;
+  a.col_scale = col_scale;
+  a.inv_scale_d = 1.0 / p->scale;
+  a.inv_scale_f = (float)(1.0 / p->scale);
+  a.N = p->N;
+  a.n_rows = p->n_rows;
+  const bool has_csr = p->dev.csr.n_items > 0;
+  const bool has_bcsr = p->dev.bcsr.n_rb > 0;
+  cudaError_t e = cudaSuccess;
+  if (has_csr && has_bcsr) {
+    e = cudaEventRecord(p->ev_fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->side, p->ev_fork, 0);
+    if (e == cudaSuccess) e = launch_bcsr(p, p->dev.bcsr, a, p->side);
+    if (e == cudaSuccess) e = launch_csr(p, p->dev.csr, a, s);
+    if (e == cudaSuccess) e = cudaEventRecord(p->ev_join, p->side);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->ev_join, 0);
+  } else if (has_bcsr) {
+    e = launch_bcsr(p, p->dev.bcsr, a, s);
+  } else if (has_csr) {
+    e = launch_csr(p, p->dev.csr, a, s);
+  }
+  return cuda_status(e, "SpMM launch");
+}
+
+// Fill a device buffer with finite values of the dense dtype (timing input only).
+static cudaError_t fill_finite(void* p, int64_t bytes, cudaStream_t s) {
+  // 0x3C bytes: f16 1.06, bf16 0.0115, f32 0.0115, f64 1.6e-18 -- all finite
+  return cudaMemsetAsync(p, 0x3C, (size_t)bytes, s);
+}
+
+// Autotuner (replaces the paper's Eq. 2/Eq. 3 CPU model): times C = A.B for candidate split
+// thresholds on synthetic B and keeps the fastest. Candidates that give the same row-block
+// split as an earlier one are skipped.
+loops_status autotune_tau(const loops_csr* A, const double* vals, int64_t N, loops_dtype dtype, int32_t br,
+                          int32_t split_len, cudaStream_t s, double* tau_out) {
+  static const double cands[] = {INFINITY, 8.0, 4.0, 3.0, 2.0, 1.5, 1.25, 0.0};
+  *tau_out = 2.0;
+  if (A->nnz == 0 || N == 0 || A->n_rows == 0) return LOOPS_OK;
+  const int64_t eb = dense_elem_bytes(dtype), ec = out_elem_bytes(dtype);
+  void *dB = nullptr, *dC = nullptr;
+  cudaError_t e = cudaMalloc(&dB, (size_t)std::max<int64_t>(A->n_cols * N * eb, 16));
+  if (e == cudaSuccess) e = cudaMalloc(&dC, (size_t)std::max<int64_t>(A->n_rows * N * ec, 16));
+  if (e == cudaSuccess) e = fill_finite(dB, A->n_cols * N * eb, s);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  loops_status st = cuda_status(e, "autotune setup");
+  double best = INFINITY;
+  std::vector<int64_t> seen;
+  loops_plan_opts o;
+  loops_plan_opts_default(&o);
+  o.split_len = split_len;
+  for (double tau : cands) {
+    if (st) break;
+    loops_plan_s* p = nullptr;
+    if ((st = make_plan(A, vals, N, dtype, o, br, tau, &p))) break;
+    const int64_t key = (int64_t)p->canon.rb_ids.size();
+    if (std::find(seen.begin(), seen.end(), key) != seen.end()) { destroy_plan(p); continue; }
+    seen.push_back(key);
+    float best_ms = INFINITY;
+    for (int it = 0; it < 7 && !st; ++it) {
+      if ((st = run_spmm(p, dB, N, nullptr, dC, N, s))) break;  // it 0, 1: warm-up
+      if (it < 2) continue;
+      cudaEventRecord(e0, s);
+      st = run_spmm(p, dB, N, nullptr, dC, N, s);
+      cudaEventRecord(e1, s);
+      if (!st) st = cuda_status(cudaEventSynchronize(e1), "autotune timing");
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      best_ms = std::min(best_ms, ms);
+    }
+    destroy_plan(p);
+    if (!st && best_ms < best) { best = best_ms; *tau_out = tau; }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (dB) cudaFree(dB);
+  if (dC) cudaFree(dC);
+  return st;
+}
+
+}  // namespace loops
+
+using namespace loops;
+
+extern "C" {
+
+int32_t loops_version(void) { return 10000; }
+
+const char* loops_status_str(loops_status s) {
+  switch (s) {
+    case LOOPS_OK: return "LOOPS_OK";
+    case LOOPS_ERR_INVALID_ARG: return "LOOPS_ERR_INVALID_ARG";
+    case LOOPS_ERR_INVALID_CSR: return "LOOPS_ERR_INVALID_CSR";
+    case LOOPS_ERR_UNSUPPORTED: return "LOOPS_ERR_UNSUPPORTED";
+    case LOOPS_ERR_OOM: return "LOOPS_ERR_OOM";
+    case LOOPS_ERR_CUDA: return "LOOPS_ERR_CUDA";
+    case LOOPS_ERR_TIMEOUT: return "LOOPS_ERR_TIMEOUT";
+    case LOOPS_ERR_STATE: return "LOOPS_ERR_STATE";
+  }
+  return "LOOPS_ERR_UNKNOWN";
+}
+
+const char* loops_last_error(void) { return g_last_error.c_str(); }
+
+void loops_plan_opts_default(loops_plan_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->tau = 2.0;
+}
+
+loops_status loops_partition_host(const loops_csr* A, loops_dtype dtype, const loops_plan_opts* opts,
+                                  loops_partition* out) {
+  clear_error();
+  if (!out) { set_error("out is NULL"); return LOOPS_ERR_INVALID_ARG; }
+  std::memset(out, 0, sizeof(*out));
+  if (!valid_dtype(dtype)) { set_error("bad dtype"); return LOOPS_ERR_INVALID_ARG; }
+  loops_plan_opts o;
+  loops_plan_opts_default(&o);
+  if (opts) o = *opts;
+  loops_status st = validate_csr(A);
+  if (st) return st;
+  if (!(o.tau >= 0.0)) { set_error("tau must be >= 0 for a host partition"); return LOOPS_ERR_INVALID_ARG; }
+  int32_t br;
+  if ((st = resolve_block_rows(dtype, o, &br))) return st;
+  std::vector<double> vals;
+  read_vals_f64(A, vals);
+  Canon c;
+  if ((st = build_canon(A, vals.data(), dtype, br, o.tau, o.contiguous_split != 0, o.r_boundary, c))) return st;
+  fill_partition(c, out);
+  return LOOPS_OK;
+}
+
+void loops_partition_free(loops_partition* part) {
+  if (!part) return;
+  void* ptrs[] = {part->csr_rows, part->csr_ptr, part->csr_col, part->csr_val,
+                  part->rb_ids, part->rb_ptr, part->tile_col, part->tile_val};
+  for (void* q : ptrs) std::free(q);
+  std::memset(part, 0, sizeof(*part));
+}
+
+loops_status loops_plan(const loops_csr* A, int64_t N, loops_dtype dtype, const loops_plan_opts* opts,
+                        loops_stream_t stream, loops_plan_t* out) {
+  clear_error();
+  if (!out) { set_error("out is NULL"); return LOOPS_ERR_INVALID_ARG; }
+  *out = nullptr;
+  if (!valid_dtype(dtype)) { set_error("bad dtype"); return LOOPS_ERR_INVALID_ARG; }
+  if (N < 0) { set_error("N < 0"); return LOOPS_ERR_INVALID_ARG; }
+  if (N > (1 << 20)) { set_error("N above 2^20 is not supported"); return LOOPS_ERR_UNSUPPORTED; }
+  loops_plan_opts o;
+  loops_plan_opts_default(&o);
+  if (opts) o = *opts;
+  if (std::isnan(o.tau)) { set_error("tau is NaN"); return LOOPS_ERR_INVALID_ARG; }
+  loops_status st = validate_csr(A);
+  if (st) return st;
+  int32_t br;
+  if ((st = resolve_block_rows(dtype, o, &br))) return st;
+  if (o.split_len < 0) { set_error("split_len < 0"); return LOOPS_ERR_INVALID_ARG; }
+  std::vector<double> vals;
+  read_vals_f64(A, vals);
+  double tau = o.tau;
+  if (tau < 0.0 && !o.contiguous_split) {
+    if ((st = autotune_tau(A, vals.data(), N, dtype, br, o.split_len, (cudaStream_t)stream, &tau))) return st;
+  }
+  loops_plan_s* p = nullptr;
+  if ((st = make_plan(A, vals.data(), N, dtype, o, br, tau, &p))) return st;
+  if (o.want_backward) {
+    std::vector<int64_t> trp;
+    std::vector<int32_t> tci;
+    transpose_csr(A, trp, tci, p->t_perm);
+    std::vector<double> tv((size_t)A->nnz);
+    for (size_t e = 0; e < tv.size(); ++e) tv[e] = vals[(size_t)p->t_perm[e]];
+    loops_csr At;
+    At.n_rows = A->n_cols;
+    At.n_cols = A->n_rows;
+    At.nnz = A->nnz;
+    At.row_ptr = trp.data();
+    At.col_idx = tci.data();
+    At.vals = tv.data();
+    At.vals_dtype = LOOPS_F64;
+    loops_plan_opts ot = o;
+    ot.want_backward = 0;
+    ot.contiguous_split = 0;
+    loops_plan_s* pt = nullptr;
+    if ((st = make_plan(&At, tv.data(), N, dtype, ot, br, tau, &pt))) { destroy_plan(p); return st; }
+    p->transposed = pt;
+    if ((st = build_sddmm(p, A))) { destroy_plan(p); return st; }
+  }
+  *out = p;
+  return LOOPS_OK;
+}
+
+loops_status loops_plan_destroy(loops_plan_t plan) {
+  clear_error();
+  if (!plan) return LOOPS_OK;
+  loops_status st = check_plan(plan);
+  if (st) return st;
+  cudaDeviceSynchronize();
+  destroy_plan(plan);
+  return LOOPS_OK;
+}
+
+loops_status loops_plan_info_get(loops_plan_t p, loops_plan_info* out) {
+  clear_error();
+  loops_status st = check_plan(p);
+  if (st) return st;
+  if (!out) { set_error("out is NULL"); return LOOPS_ERR_INVALID_ARG; }
+  std::memset(out, 0, sizeof(*out));
+  out->dtype = p->dtype;
+  out->block_rows = p->br;
+  out->k_pad = p->kpad;
+  out->has_backward = p->transposed != nullptr;
+  out->n_rows = p->n_rows;
+  out->n_cols = p->n_cols;
+  out->nnz = p->nnz;
+  out->N = p->N;
+  out->tau = p->tau;
+  out->scale = p->scale;
+  out->n_csr_rows = (int64_t)p->canon.csr_rows.size();
+  out->nnz_csr = (int64_t)p->canon.csr_col.size();
+  out->n_row_blocks = (int64_t)p->canon.rb_ids.size();
+  out->n_tiles = (int64_t)p->canon.tile_col.size();
+  out->nnz_bcsr = p->nnz_bcsr;
+  out->n_split_rows = p->dev.csr.n_split;
+  out->n_segments = p->dev.csr.n_slots;
+  out->n_subnormal_vals = p->n_subnormal;
+  out->device_bytes = p->dev.device_bytes + (p->transposed ? p->transposed->dev.device_bytes : 0);
+  return LOOPS_OK;
+}
+
+loops_status loops_plan_export(loops_plan_t p, loops_partition* out) {
+  clear_error();
+  loops_status st = check_plan(p);
+  if (st) return st;
+  if (!out) { set_error("out is NULL"); return LOOPS_ERR_INVALID_ARG; }
+  std::memset(out, 0, sizeof(*out));
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_status(e, "synchronize before export");
+  st = export_part(p, out);
+  if (st) loops_partition_free(out);
+  return st;
+}
+
+loops_status loops_plan_update_values(loops_plan_t p, const void* vals, loops_dtype vd,
+                                      loops_stream_t stream) {
+  clear_error();
+  loops_status st = check_plan(p);
+  if (st) return st;
+  if (!vals && p->nnz) { set_error("vals is NULL"); return LOOPS_ERR_INVALID_ARG; }
+  if (vd != LOOPS_F64 && vd != LOOPS_F32) { set_error("vals must be F64 or F32"); return LOOPS_ERR_UNSUPPORTED; }
+  std::vector<double> v((size_t)p->nnz);
+  for (int64_t k = 0; k < p->nnz; ++k) v[(size_t)k] = vd == LOOPS_F64 ? ((const double*)vals)[k] : (double)((const float*)vals)[k];
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_status(e, "synchronize before value update");
+  auto refresh = [](loops_plan_s* q, const std::vector<double>& vv) -> loops_status {
+    Canon& c = q->canon;
+    std::fill(c.tile_val.begin(), c.tile_val.end(), 0.0);
+    std::vector<double> raw_tile(c.tile_val.size(), 0.0);
+    for (size_t k = 0; k < vv.size(); ++k) {
+      if (c.src_kind[k] == 0) c.csr_val[(size_t)c.src_slot[k]] = round_store(vv[k], c.scale, q->dtype);
+      else raw_tile[(size_t)c.src_slot[k]] += vv[k];
+    }
+    for (size_t x = 0; x < raw_tile.size(); ++x) c.tile_val[x] = round_store(raw_tile[x], c.scale, q->dtype);
+    const int64_t N = q->N;
+    free_part(q->dev);
+    const int64_t extra = sizeof(int32_t);
+    loops_status s2 = upload_part(q, N);
+    q->dev.device_bytes += extra;
+    return s2;
+  };
+  if ((st = refresh(p, v))) return st;
+  if (p->transposed) {
+    std::vector<double> tv(v.size());
+    for (size_t x = 0; x < tv.size(); ++x) tv[x] = v[(size_t)p->t_perm[x]];
+    if ((st = refresh(p->transposed, tv))) return st;
+  }
+  return LOOPS_OK;
+}
+
+loops_status loops_spmm(loops_plan_t p, const void* B, int64_t ldb, void* C, int64_t ldc,
+                        loops_stream_t stream) {
+  return loops_spmm_scaled(p, B, ldb, nullptr, C, ldc, stream);
+}
+
+loops_status loops_spmm_scaled(loops_plan_t p, const void* B, int64_t ldb, const float* col_scale,
+                               void* C, int64_t ldc, loops_stream_t stream) {
+  clear_error();
+  loops_status st = check_plan(p);
+  if (st) return st;
+  if ((st = check_dense(B, p->n_cols, p->N, ldb, "B"))) return st;
+  if ((st = check_dense(C, p->n_rows, p->N, ldc, "C"))) return st;
+  if (col_scale && (p->dtype == LOOPS_F64 || p->dtype == LOOPS_F32)) {
+    set_error("col_scale is only defined for the 16-bit dtypes");
+    return LOOPS_ERR_INVALID_ARG;
+  }
+  return run_spmm(p, B, ldb, col_scale, C, ldc, (cudaStream_t)stream);
+}
+
+loops_status loops_spmm_host(loops_plan_t p, const void* B_host, int64_t ldb, void* C_host, int64_t ldc,
+                             loops_stream_t stream) {
+  clear_error();
+  loops_status st = check_plan(p);
+  if (st) return st;
+  if ((st = check_dense(B_host, p->n_cols, p->N, ldb, "B"))) return st;
+  if ((st = check_dense(C_host, p->n_rows, p->N, ldc, "C"))) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t eb = dense_elem_bytes(p->dtype), ec = out_elem_bytes(p->dtype);
+  const int64_t need_B = p->n_cols * p->N * eb, need_C = p->n_rows * p->N * ec;
+  cudaError_t e = cudaSuccess;
+  if (need_B > p->stage_B_bytes) {
+    if (p->stage_B) cudaFree(p->stage_B);
+    p->stage_B = nullptr;
+    p->stage_B_bytes = 0;
+    e = cudaMalloc(&p->stage_B, (size_t)need_B);
+    if (e != cudaSuccess) return cuda_status(e, "staging allocation");
+    p->stage_B_bytes = need_B;
+  }
+  if (need_C > p->stage_C_bytes) {
+    if (p->stage_C) cudaFree(p->stage_C);
+    p->stage_C = nullptr;
+    p->stage_C_bytes = 0;
+    e = cudaMalloc(&p->stage_C, (size_t)need_C);
+    if (e != cudaSuccess) return cuda_status(e, "staging allocation");
+    p->stage_C_bytes = need_C;
+  }
+  if (need_B)
+    e = cudaMemcpy2DAsync(p->stage_B, (size_t)(p->N * eb), B_host, (size_t)(ldb * eb), (size_t)(p->N * eb),
+                          (size_t)p->n_cols, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_status(e, "host-to-device copy");
+  if ((st = run_spmm(p, p->stage_B, p->N, nullptr, p->stage_C, p->N, s))) return st;
+  if (need_C)
+    e = cudaMemcpy2DAsync(C_host, (size_t)(ldc * ec), p->stage_C, (size_t)(p->N * ec), (size_t)(p->N * ec),
+                          (size_t)p->n_rows, cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return cuda_status(e, "device-to-host copy");
+  return cuda_status(cudaStreamSynchronize(s), "synchronize");
+}
+
+loops_status loops_spmm_backward(loops_plan_t p, const void* dC, int64_t lddc, const void* B, int64_t ldb,
+                                 void* dB, int64_t lddb, void* dvals, loops_stream_t stream) {
+  clear_error();
+  loops_status st = check_plan(p);
+  if (st) return st;
+  if (!p->transposed) {
+    set_error("plan was built without want_backward");
+    return LOOPS_ERR_STATE;
+  }
+  if ((st = check_dense(dC, p->n_rows, p->N, lddc, "dC"))) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (dB) {
+    if ((st = check_dense(dB, p->n_cols, p->N, lddb, "dB"))) return st;
+    if ((st = run_spmm(p->transposed, dC, lddc, nullptr, dB, lddb, s))) return st;
+  }
+  if (dvals && p->nnz > 0) {
+    if ((st = check_dense(B, p->n_cols, p->N, ldb, "B"))) return st;
+    if ((st = cuda_status(launch_sddmm(p, dC, lddc, B, ldb, dvals, s), "SDDMM launch"))) return st;
+  }
+  return LOOPS_OK;
+}
+
+loops_status loops_cast_scaled(const float* X, int64_t rows, int64_t cols, int64_t ldx, loops_dtype yd,
+                               void* Y, int64_t ldy, float* col_scale, loops_stream_t stream) {
+  clear_error();
+  if (yd != LOOPS_F16 && yd != LOOPS_BF16) { set_error("y_dtype must be F16 or BF16"); return LOOPS_ERR_UNSUPPORTED; }
+  if (rows < 0 || cols < 0 || ldx < cols || ldy < cols) { set_error("bad sizes"); return LOOPS_ERR_INVALID_ARG; }
+  if (cols == 0) return LOOPS_OK;
+  if (!col_scale || (rows > 0 && (!X || !Y))) { set_error("NULL pointer"); return LOOPS_ERR_INVALID_ARG; }
+  return cuda_status(launch_cast_scaled(X, rows, cols, ldx, yd, Y, ldy, col_scale, (cudaStream_t)stream),
+                     "cast launch");
+}
+
+loops_status loops_plan_check(loops_plan_t p, loops_stream_t stream) {
+  clear_error();
+  loops_status st = check_plan(p);
+  if (st) return st;
+  int32_t h = 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(&h, p->d_error, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->d_error, 0, sizeof(int32_t), s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_status(e, "read error word");
+  if (p->transposed) {
+    int32_t ht = 0;
+    e = cudaMemcpyAsync(&ht, p->transposed->d_error, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->transposed->d_error, 0, sizeof(int32_t), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_status(e, "read error word");
+    h |= ht;
+  }
+  if (h & kErrWaitTimeout) {
+    set_error("a device-side wait exceeded its bound");
+    return LOOPS_ERR_TIMEOUT;
+  }
+  return LOOPS_OK;
+}
+
+}  // extern "C"

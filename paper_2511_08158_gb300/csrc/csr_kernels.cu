@@ -1,0 +1,505 @@
+// CSR-part SpMM (the AXPY row kernel of Sec. 3.3 on CUDA cores), the deterministic sum of
+// split-row partials, the SDDMM of the backward pass, and the per-column scaled cast.
+//
+// A group of G lanes (G divides 32) owns one work item (a CSR row or a segment of a long
+// row). Each lane owns VPL 16-byte column vectors of the output row, laid out so that the G
+// lanes read consecutive 16-byte pieces of a B row (coalesced 128-bit loads). The group
+// reads G (col, val) pairs at once and broadcasts them with shuffles; U B-row loads are kept
+// in flight before their FMAs. Accumulation is in f64 for F64 and in f32 otherwise. Every
+// output row has one writer; rows split in segments write partials that a second kernel
+// sums in segment order, so the result does not depend on scheduling.
+#include "device_common.cuh"
+#include "loops_internal.h"
+
+namespace loops {
+
+namespace {
+
+struct CsrKArgs {
+  const int32_t* item_row;
+  const int64_t* item_ptr;
+  const int32_t* col;
+  const void* val;
+  int64_t n_items;
+  const void* B;
+  int64_t ldb;
+  void* C;
+  int64_t ldc;
+  void* scratch;         // n_slots x N accumulators
+  const float* col_scale;
+  float inv_scale_f;
+  double inv_scale_d;
+  int64_t N;
+};
+
+template <class Tr>
+__device__ __forceinline__ typename Tr::TAcc out_scale(const CsrKArgs& a, int64_t n);
+template <>
+__device__ __forceinline__ double out_scale<TrF64>(const CsrKArgs& a, int64_t) { return a.inv_scale_d; }
+template <>
+__device__ __forceinline__ float out_scale<TrF32>(const CsrKArgs& a, int64_t) { return a.inv_scale_f; }
+template <>
+__device__ __forceinline__ float out_scale<TrF16>(const CsrKArgs& a, int64_t n) {
+  return a.col_scale ? a.col_scale[n] * a.inv_scale_f : a.inv_scale_f;
+}
+template <>
+__device__ __forceinline__ float out_scale<TrBF16>(const CsrKArgs& a, int64_t n) {
+  return a.col_scale ? a.col_scale[n] * a.inv_scale_f : a.inv_scale_f;
+}
+
+// Vector path: N % VE == 0, B/C/ld aligned for 16-byte B loads and vector C stores.
+template <class Tr, int G, int VPL, int U>
+__global__ void __launch_bounds__(256) csr_spmm_vec(CsrKArgs a) {
+  using TB = typename Tr::TB;
+  using TAcc = typename Tr::TAcc;
+  using TC = typename Tr::TC;
+  constexpr int VE = Tr::kVE;
+  const int lane = threadIdx.x & 31;
+  const int sub = lane & (G - 1);
+  const int64_t item = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+  if (item >= a.n_items) return;  // a group leaves as a whole
+  const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+  const int64_t beg = a.item_ptr[item];
+  const int64_t end = a.item_ptr[item + 1];
+  const int32_t row = a.item_row[item];
+  const int64_t c_base = (int64_t)blockIdx.y * (G * VPL * VE);
+  bool colok[VPL];
+  int64_t coff[VPL];
+#pragma unroll
+  for (int p = 0; p < VPL; ++p) {
+    coff[p] = c_base + (int64_t)(p * G + sub) * VE;
+    colok[p] = coff[p] < a.N;
+  }
+  TAcc acc[VPL][VE];
+#pragma unroll
+  for (int p = 0; p < VPL; ++p)
+#pragma unroll
+    for (int e = 0; e < VE; ++e) acc[p][e] = TAcc(0);
+
+  const TB* __restrict__ Bp = reinterpret_cast<const TB*>(a.B);
+  const TB* __restrict__ vals = reinterpret_cast<const TB*>(a.val);
+  for (int64_t k0 = beg; k0 < end; k0 += G) {
+    const int64_t k = k0 + sub;
+    int32_t c = 0;
+    TAcc v = TAcc(0);
+    if (k < end) {
+      c = __ldg(a.col + k);
+      v = Tr::to_acc(vals[k]);
+    }
+    const int cnt = (int)(end - k0 < (int64_t)G ? end - k0 : (int64_t)G);
+    for (int j0 = 0; j0 < cnt; j0 += U) {
+      uint4 bv[U][VPL];
+      TAcc av[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int j = j0 + u;
+        const int cj = __shfl_sync(gmask, c, j & (G - 1), G);
+        av[u] = __shfl_sync(gmask, v, j & (G - 1), G);
+        const bool ok = j < cnt;
+        if (!ok) av[u] = TAcc(0);
+        const TB* brow = Bp + (int64_t)cj * a.ldb;
+#pragma unroll
+        for (int p = 0; p < VPL; ++p)
+          bv[u][p] = (ok && colok[p]) ? ldg16(brow + coff[p]) : make_uint4(0, 0, 0, 0);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int p = 0; p < VPL; ++p) {
+          TAcc b[VE];
+          unpack16<Tr>(bv[u][p], b);
+#pragma unroll
+          for (int e = 0; e < VE; ++e) acc[p][e] = fma(av[u], b[e], acc[p][e]);
+        }
+    }
+  }
+  if (row >= 0) {
+    TC* crow = reinterpret_cast<TC*>(a.C) + (int64_t)row * a.ldc;
+#pragma unroll
+    for (int p = 0; p < VPL; ++p) {
+      if (!colok[p]) continue;
+      TC o[VE];
+#pragma unroll
+      for (int e = 0; e < VE; ++e) o[e] = (TC)(acc[p][e] * out_scale<Tr>(a, coff[p] + e));
+      // VE outputs are 16 (F64/F32) or 32 (16-bit inputs, f32 outputs) bytes
+#pragma unroll
+      for (int q = 0; q < (int)(VE * sizeof(TC) / 16); ++q)
+        *reinterpret_cast<uint4*>(crow + coff[p] + q * (16 / sizeof(TC))) =
+            *reinterpret_cast<const uint4*>(&o[q * (16 / sizeof(TC))]);
+    }
+  } else {
+    TAcc* srow = reinterpret_cast<TAcc*>(a.scratch) + (int64_t)(-1 - row) * a.N;
+#pragma unroll
+    for (int p = 0; p < VPL; ++p) {
+      if (!colok[p]) continue;
+#pragma unroll
+      for (int e = 0; e < VE; ++e) srow[coff[p] + e] = acc[p][e];
+    }
+  }
+}
+
+// Scalar path for any N and alignment: 32 lanes per item, one column per lane per pass.
+template <class Tr, int U>
+__global__ void __launch_bounds__(256) csr_spmm_scalar(CsrKArgs a) {
+  using TB = typename Tr::TB;
+  using TAcc = typename Tr::TAcc;
+  using TC = typename Tr::TC;
+  const int lane = threadIdx.x & 31;
+  const int64_t item = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+  if (item >= a.n_items) return;
+  const int64_t beg = a.item_ptr[item];
+  const int64_t end = a.item_ptr[item + 1];
+  const int32_t row = a.item_row[item];
+  const int64_t n = (int64_t)blockIdx.y * 32 + lane;
+  const bool colok = n < a.N;
+  const TB* __restrict__ Bp = reinterpret_cast<const TB*>(a.B);
+  const TB* __restrict__ vals = reinterpret_cast<const TB*>(a.val);
+  TAcc acc = TAcc(0);
+  for (int64_t k0 = beg; k0 < end; k0 += 32) {
+    const int64_t k = k0 + lane;
+    int32_t c = 0;
+    TAcc v = TAcc(0);
+    if (k < end) {
+      c = __ldg(a.col + k);
+      v = Tr::to_acc(vals[k]);
+    }
+    const int cnt = (int)(end - k0 < 32 ? end - k0 : 32);
+    for (int j0 = 0; j0 < cnt; j0 += U) {
+      TAcc bv[U], av[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int j = j0 + u;
+        const int cj = __shfl_sync(0xffffffffu, c, j & 31);
+        av[u] = __shfl_sync(0xffffffffu, v, j & 31);
+        const bool ok = j < cnt && colok;
+        bv[u] = ok ? Tr::to_acc(Bp[(int64_t)cj * a.ldb + n]) : TAcc(0);
+        if (j >= cnt) av[u] = TAcc(0);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) acc = fma(av[u], bv[u], acc);
+    }
+  }
+  if (!colok) return;
+  if (row >= 0) {
+    reinterpret_cast<TC*>(a.C)[(int64_t)row * a.ldc + n] = (TC)(acc * out_scale<Tr>(a, n));
+  } else {
+    reinterpret_cast<TAcc*>(a.scratch)[(int64_t)(-1 - row) * a.N + n] = acc;
+  }
+}
+
+// C[row, n] = scale_n * sum over the row's segments, in segment order.
+template <class Tr>
+__global__ void __launch_bounds__(256) split_reduce(const int32_t* __restrict__ split_row,
+                                                    const int32_t* __restrict__ slot_ptr,
+                                                    int64_t n_split, CsrKArgs a) {
+  using TAcc = typename Tr::TAcc;
+  using TC = typename Tr::TC;
+  const int64_t s = blockIdx.x;
+  if (s >= n_split) return;
+  const int32_t row = split_row[s];
+  const int32_t s0 = slot_ptr[s], s1 = slot_ptr[s + 1];
+  const TAcc* sc = reinterpret_cast<const TAcc*>(a.scratch);
+  for (int64_t n = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; n < a.N; n += (int64_t)gridDim.y * blockDim.x) {
+    TAcc acc = TAcc(0);
+    for (int32_t q = s0; q < s1; ++q) acc += sc[(int64_t)q * a.N + n];
+    reinterpret_cast<TC*>(a.C)[(int64_t)row * a.ldc + n] = (TC)(acc * out_scale<Tr>(a, n));
+  }
+}
+
+inline int next_pow2(int64_t x) {
+  int p = 1;
+  while (p < x && p < 32) p <<= 1;
+  return p;
+}
+
+template <class Tr, int G, int VPL>
+cudaError_t launch_vec_g(const CsrKArgs& a, cudaStream_t s) {
+  constexpr int VE = Tr::kVE;
+  const int64_t per_chunk = (int64_t)G * VPL * VE;
+  const int64_t chunks = (a.N + per_chunk - 1) / per_chunk;
+  const int64_t threads = a.n_items * G;
+  dim3 grid((unsigned)((threads + 255) / 256), (unsigned)chunks);
+  constexpr int U = (G >= 8) ? 8 : 4;
+  csr_spmm_vec<Tr, G, VPL, U><<<grid, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <class Tr>
+cudaError_t launch_csr_t(const loops_plan_s* p, const CsrDev& d, const DenseArgs& da, cudaStream_t s) {
+  CsrKArgs a;
+  a.item_row = d.item_row;
+  a.item_ptr = d.item_ptr;
+  a.col = d.col;
+  a.val = d.val;
+  a.n_items = d.n_items;
+  a.B = da.B;
+  a.ldb = da.ldb;
+  a.C = da.C;
+  a.ldc = da.ldc;
+  a.scratch = d.scratch;
+  a.col_scale = da.col_scale;
+  a.inv_scale_f = da.inv_scale_f;
+  a.inv_scale_d = da.inv_scale_d;
+  a.N = da.N;
+  using TB = typename Tr::TB;
+  using TC = typename Tr::TC;
+  constexpr int VE = Tr::kVE;
+  const bool vec = (a.N % VE == 0) && ((uintptr_t)a.B % 16 == 0) && ((uintptr_t)a.C % 16 == 0) &&
+                   ((a.ldb * (int64_t)sizeof(TB)) % 16 == 0) && ((a.ldc * (int64_t)sizeof(TC)) % 16 == 0);
+  cudaError_t e = cudaSuccess;
+  if (a.n_items > 0) {
+    if (vec) {
+      const int64_t nvec = a.N / VE;
+      const int G = next_pow2(nvec);
+      const bool two = nvec > 32;
+      switch (G) {
+        case 1: e = launch_vec_g<Tr, 1, 1>(a, s); break;
+        case 2: e = launch_vec_g<Tr, 2, 1>(a, s); break;
+        case 4: e = launch_vec_g<Tr, 4, 1>(a, s); break;
+        case 8: e = launch_vec_g<Tr, 8, 1>(a, s); break;
+        case 16: e = launch_vec_g<Tr, 16, 1>(a, s); break;
+        default: e = two ? launch_vec_g<Tr, 32, 2>(a, s) : launch_vec_g<Tr, 32, 1>(a, s); break;
+      }
+    } else {
+      dim3 grid((unsigned)((a.n_items * 32 + 255) / 256), (unsigned)((a.N + 31) / 32));
+      csr_spmm_scalar<Tr, 8><<<grid, 256, 0, s>>>(a);
+      e = cudaGetLastError();
+    }
+  }
+  if (e == cudaSuccess && d.n_split > 0) {
+    dim3 grid((unsigned)d.n_split, (unsigned)std::min<int64_t>((a.N + 255) / 256, 64));
+    split_reduce<Tr><<<grid, 256, 0, s>>>(d.split_row, d.split_slot_ptr, d.n_split, a);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+// ------------------------------------------------------------------ SDDMM
+// dvals[k] = sum_n dC[i, n] * B[j_k, n] for the entries of an item (row i, range [b, e)).
+// G lanes per item hold the dC row slice in registers; each entry's partial dot products are
+// reduced across the group with shuffles (a fixed tree, so the result is deterministic).
+struct SddmmKArgs {
+  const int32_t* item_row;
+  const int64_t* item_beg;
+  const int64_t* item_end;
+  const int32_t* col;
+  int64_t n_items;
+  const void* dC;
+  int64_t lddc;
+  const void* B;
+  int64_t ldb;
+  void* dvals;
+  int64_t N;
+};
+
+template <class Tr, int G, int VPL>
+__global__ void __launch_bounds__(256) sddmm_vec(SddmmKArgs a) {
+  using TB = typename Tr::TB;
+  using TAcc = typename Tr::TAcc;
+  using TC = typename Tr::TC;
+  constexpr int VE = Tr::kVE;
+  const int lane = threadIdx.x & 31;
+  const int sub = lane & (G - 1);
+  const int64_t item = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+  if (item >= a.n_items) return;
+  const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+  const int32_t row = a.item_row[item];
+  const int64_t beg = a.item_beg[item], end = a.item_end[item];
+  const TB* dcrow = reinterpret_cast<const TB*>(a.dC) + (int64_t)row * a.lddc;
+  const TB* Bp = reinterpret_cast<const TB*>(a.B);
+  TAcc g[VPL][VE];
+  bool colok[VPL];
+  int64_t coff[VPL];
+#pragma unroll
+  for (int p = 0; p < VPL; ++p) {
+    coff[p] = (int64_t)(p * G + sub) * VE;
+    colok[p] = coff[p] < a.N;
+    uint4 v = colok[p] ? ldg16(dcrow + coff[p]) : make_uint4(0, 0, 0, 0);
+    unpack16<Tr>(v, g[p]);
+  }
+  constexpr int U = 4;
+  for (int64_t k0 = beg; k0 < end; k0 += U) {
+    int32_t cj[U];
+    uint4 bv[U][VPL];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const bool ok = k0 + u < end;
+      cj[u] = ok ? __ldg(a.col + k0 + u) : 0;
+#pragma unroll
+      for (int p = 0; p < VPL; ++p)
+        bv[u][p] = (ok && colok[p]) ? ldg16(Bp + (int64_t)cj[u] * a.ldb + coff[p]) : make_uint4(0, 0, 0, 0);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      TAcc s = TAcc(0);
+#pragma unroll
+      for (int p = 0; p < VPL; ++p) {
+        TAcc b[VE];
+        unpack16<Tr>(bv[u][p], b);
+#pragma unroll
+        for (int e = 0; e < VE; ++e) s = fma(g[p][e], b[e], s);
+      }
+#pragma unroll
+      for (int off = G / 2; off > 0; off >>= 1) s += __shfl_xor_sync(gmask, s, off, G);
+      if (sub == 0 && k0 + u < end) reinterpret_cast<TC*>(a.dvals)[k0 + u] = (TC)s;
+    }
+  }
+}
+
+template <class Tr>
+__global__ void __launch_bounds__(256) sddmm_scalar(SddmmKArgs a) {
+  using TB = typename Tr::TB;
+  using TAcc = typename Tr::TAcc;
+  using TC = typename Tr::TC;
+  const int lane = threadIdx.x & 31;
+  const int64_t item = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+  if (item >= a.n_items) return;
+  const int32_t row = a.item_row[item];
+  const TB* dcrow = reinterpret_cast<const TB*>(a.dC) + (int64_t)row * a.lddc;
+  const TB* Bp = reinterpret_cast<const TB*>(a.B);
+  for (int64_t k = a.item_beg[item]; k < a.item_end[item]; ++k) {
+    const int32_t c = __ldg(a.col + k);
+    TAcc s = TAcc(0);
+    for (int64_t n = lane; n < a.N; n += 32) s = fma(Tr::to_acc(dcrow[n]), Tr::to_acc(Bp[(int64_t)c * a.ldb + n]), s);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) reinterpret_cast<TC*>(a.dvals)[k] = (TC)s;
+  }
+}
+
+template <class Tr>
+cudaError_t launch_sddmm_t(const loops_plan_s* p, const void* dC, int64_t lddc, const void* B, int64_t ldb,
+                           void* dvals, cudaStream_t s) {
+  SddmmKArgs a;
+  a.item_row = p->sddmm.item_row;
+  a.item_beg = p->sddmm.item_beg;
+  a.item_end = p->sddmm.item_end;
+  a.col = p->sddmm.col;
+  a.n_items = p->sddmm.n_items;
+  a.dC = dC;
+  a.lddc = lddc;
+  a.B = B;
+  a.ldb = ldb;
+  a.dvals = dvals;
+  a.N = p->N;
+  if (a.n_items == 0) return cudaSuccess;
+  using TB = typename Tr::TB;
+  constexpr int VE = Tr::kVE;
+  const bool vec = (a.N % VE == 0) && ((uintptr_t)B % 16 == 0) && ((uintptr_t)dC % 16 == 0) &&
+                   ((ldb * (int64_t)sizeof(TB)) % 16 == 0) && ((lddc * (int64_t)sizeof(TB)) % 16 == 0);
+  const int64_t nvec = a.N / VE;
+  if (vec && nvec <= 64) {
+    const int G = next_pow2(nvec);
+    const int64_t threads = a.n_items * G;
+    dim3 grid((unsigned)((threads + 255) / 256));
+    switch (G) {
+      case 1: sddmm_vec<Tr, 1, 1><<<grid, 256, 0, s>>>(a); break;
+      case 2: sddmm_vec<Tr, 2, 1><<<grid, 256, 0, s>>>(a); break;
+      case 4: sddmm_vec<Tr, 4, 1><<<grid, 256, 0, s>>>(a); break;
+      case 8: sddmm_vec<Tr, 8, 1><<<grid, 256, 0, s>>>(a); break;
+      case 16: sddmm_vec<Tr, 16, 1><<<grid, 256, 0, s>>>(a); break;
+      default:
+        if (nvec > 32) sddmm_vec<Tr, 32, 2><<<grid, 256, 0, s>>>(a);
+        else sddmm_vec<Tr, 32, 1><<<grid, 256, 0, s>>>(a);
+        break;
+    }
+  } else {
+    dim3 grid((unsigned)((a.n_items * 32 + 255) / 256));
+    sddmm_scalar<Tr><<<grid, 256, 0, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ per-column scaled cast
+__global__ void __launch_bounds__(256) colmax_kernel(const float* __restrict__ X, int64_t rows, int64_t cols,
+                                                     int64_t ldx, unsigned int* __restrict__ mx) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= cols) return;
+  const int64_t r_per = (rows + gridDim.y - 1) / gridDim.y;
+  const int64_t r0 = (int64_t)blockIdx.y * r_per;
+  const int64_t r1 = min(rows, r0 + r_per);
+  float m = 0.f;
+  for (int64_t r = r0; r < r1; ++r) m = fmaxf(m, fabsf(X[r * ldx + c]));
+  if (r1 > r0) atomicMax(mx + c, __float_as_uint(m));  // non-negative floats order as integers
+}
+
+__global__ void colscale_kernel(float* __restrict__ s, int64_t cols) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= cols) return;
+  const float m = s[c];
+  float r = 1.f;
+  if (m > 0.f) {
+    int e;
+    const float f = frexpf(m, &e);             // m = f * 2^e, f in [0.5, 1)
+    int cexp = (f == 0.5f) ? e - 1 : e;        // ceil(log2 m)
+    if (cexp > 127) cexp = 127;                // largest power of two of binary32
+    r = ldexpf(1.f, cexp);
+  }
+  s[c] = r;
+}
+
+template <class T>
+__device__ __forceinline__ T cvt_rn(float x);
+template <>
+__device__ __forceinline__ __half cvt_rn<__half>(float x) { return __float2half_rn(x); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 cvt_rn<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
+
+template <class T>
+__global__ void __launch_bounds__(256) scale_cast_kernel(const float* __restrict__ X, int64_t rows, int64_t cols,
+                                                         int64_t ldx, const float* __restrict__ s, T* __restrict__ Y,
+                                                         int64_t ldy) {
+  const int64_t total = rows * cols;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / cols, c = i - r * cols;
+    // division by a power of two: exact unless the quotient falls below binary32's normal range
+    Y[r * ldy + c] = cvt_rn<T>(X[r * ldx + c] / s[c]);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_csr(const loops_plan_s* p, const CsrDev& d, const DenseArgs& a, cudaStream_t s) {
+  switch (p->dtype) {
+    case LOOPS_F64: return launch_csr_t<TrF64>(p, d, a, s);
+    case LOOPS_F32: return launch_csr_t<TrF32>(p, d, a, s);
+    case LOOPS_F16: return launch_csr_t<TrF16>(p, d, a, s);
+    case LOOPS_BF16: return launch_csr_t<TrBF16>(p, d, a, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_sddmm(const loops_plan_s* p, const void* dC, int64_t lddc, const void* B, int64_t ldb,
+                         void* dvals, cudaStream_t s) {
+  switch (p->dtype) {
+    case LOOPS_F64: return launch_sddmm_t<TrF64>(p, dC, lddc, B, ldb, dvals, s);
+    case LOOPS_F32: return launch_sddmm_t<TrF32>(p, dC, lddc, B, ldb, dvals, s);
+    case LOOPS_F16: return launch_sddmm_t<TrF16>(p, dC, lddc, B, ldb, dvals, s);
+    case LOOPS_BF16: return launch_sddmm_t<TrBF16>(p, dC, lddc, B, ldb, dvals, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_cast_scaled(const float* X, int64_t rows, int64_t cols, int64_t ldx, loops_dtype yd, void* Y,
+                               int64_t ldy, float* col_scale, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(col_scale, 0, (size_t)cols * sizeof(float), s);
+  if (e != cudaSuccess) return e;
+  if (rows > 0) {
+    const int64_t ychunks = std::min<int64_t>(std::max<int64_t>(rows / 256, 1), 1024);
+    dim3 g1((unsigned)((cols + 255) / 256), (unsigned)ychunks);
+    colmax_kernel<<<g1, 256, 0, s>>>(X, rows, cols, ldx, reinterpret_cast<unsigned int*>(col_scale));
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  colscale_kernel<<<(unsigned)((cols + 255) / 256), 256, 0, s>>>(col_scale, cols);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (rows == 0) return cudaSuccess;
+  const int64_t total = rows * cols;
+  const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 16);
+  if (yd == LOOPS_F16)
+    scale_cast_kernel<__half><<<blocks, 256, 0, s>>>(X, rows, cols, ldx, col_scale, (__half*)Y, ldy);
+  else
+    scale_cast_kernel<__nv_bfloat16><<<blocks, 256, 0, s>>>(X, rows, cols, ldx, col_scale, (__nv_bfloat16*)Y, ldy);
+  return cudaGetLastError();
+}
+
+}  // namespace loops

@@ -1,0 +1,123 @@
+// Device helpers shared by the kernels: element traits, vector loads, inline PTX wrappers.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace loops {
+
+// Element traits per plan dtype: storage type of A values and B (TB), accumulator (TAcc),
+// output (TC), and conversion of a stored element to the accumulator type.
+struct TrF64 {
+  using TB = double; using TAcc = double; using TC = double;
+  static constexpr int kVE = 2;  // elements per 16-byte vector
+  __device__ static __forceinline__ TAcc to_acc(TB x) { return x; }
+};
+struct TrF32 {
+  using TB = float; using TAcc = float; using TC = float;
+  static constexpr int kVE = 4;
+  __device__ static __forceinline__ TAcc to_acc(TB x) { return x; }
+};
+struct TrF16 {
+  using TB = __half; using TAcc = float; using TC = float;
+  static constexpr int kVE = 8;
+  __device__ static __forceinline__ TAcc to_acc(TB x) { return __half2float(x); }
+};
+struct TrBF16 {
+  using TB = __nv_bfloat16; using TAcc = float; using TC = float;
+  static constexpr int kVE = 8;
+  __device__ static __forceinline__ TAcc to_acc(TB x) { return __bfloat162float(x); }
+};
+
+// 16-byte vector of B elements, unpacked to accumulator values.
+template <class Tr>
+__device__ __forceinline__ void unpack16(const uint4& v, typename Tr::TAcc (&out)[Tr::kVE]);
+
+template <>
+__device__ __forceinline__ void unpack16<TrF64>(const uint4& v, double (&out)[2]) {
+  out[0] = __hiloint2double((int)v.y, (int)v.x);
+  out[1] = __hiloint2double((int)v.w, (int)v.z);
+}
+template <>
+__device__ __forceinline__ void unpack16<TrF32>(const uint4& v, float (&out)[4]) {
+  out[0] = __uint_as_float(v.x); out[1] = __uint_as_float(v.y);
+  out[2] = __uint_as_float(v.z); out[3] = __uint_as_float(v.w);
+}
+template <>
+__device__ __forceinline__ void unpack16<TrF16>(const uint4& v, float (&out)[8]) {
+  const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    __half2 h = *reinterpret_cast<const __half2*>(&w[i]);
+    float2 f = __half22float2(h);
+    out[2 * i] = f.x; out[2 * i + 1] = f.y;
+  }
+}
+template <>
+__device__ __forceinline__ void unpack16<TrBF16>(const uint4& v, float (&out)[8]) {
+  const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    // bfloat16 -> float is exact: the 16 bits become the high half of the binary32 pattern
+    out[2 * i] = __uint_as_float(w[i] << 16);
+    out[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
+  }
+}
+
+__device__ __forceinline__ uint4 ldg16(const void* p) {
+  uint4 r;
+  asm volatile("ld.global.nc.v4.u32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w) : "l"(p));
+  return r;
+}
+
+// ------------------------------------------------------------------ mbarrier / bulk copy
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+               ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+// One bulk copy global -> shared (the TMA engine), completing on `bar` with `bytes`.
+// dst, src 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok) : "r"(smem_addr(bar)), "r"(parity) : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: returns false after `max_polls` unsuccessful polls.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long max_polls) {
+  for (long long i = 0; i < max_polls; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (i > 64) __nanosleep(64);
+  }
+  return false;
+}
+
+}  // namespace loops

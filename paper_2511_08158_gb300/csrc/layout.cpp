@@ -1,0 +1,297 @@
+// Device layout of a plan's two parts, and its inverse (export back to canonical order).
+//
+// CSR part: rows become work items processed in storage order; rows longer than split_len
+// are cut into segments whose partial sums go to scratch slots and are summed afterwards in
+// slot order (deterministic). Items are ordered by decreasing length class, so the longest
+// work starts first; within a class the row order is kept.
+//
+// BCSR part: tile values are stored in the register-fragment order of the dtype's MMA, so a
+// lane loads its whole A fragment of a K-group with one vector load:
+//   F64  (m8n8k4, K = 4 tiles, B_r = 8):  group g, lane l = 4*row + t -> A[row][t]
+//   F16/BF16 (m16n8k16, K = 16, B_r = 16): group g, lane l = 4*q + t, j = 0..7 ->
+//        row = q + 8*(j>>1 & 1), tile = 2t + (j & 1) + 8*(j >> 2)
+//   F32  (CUDA-core outer product): tile-major, B_r values of a tile contiguous.
+#include <algorithm>
+#include <cstring>
+
+#include "loops_internal.h"
+
+namespace loops {
+
+namespace {
+
+template <typename T>
+loops_status dev_upload(T** dst, const T* src, size_t n, int64_t& bytes) {
+  *dst = nullptr;
+  if (n == 0) return LOOPS_OK;
+  cudaError_t e = cudaMalloc((void**)dst, n * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *dst = nullptr;
+    set_error(std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? LOOPS_ERR_OOM : LOOPS_ERR_CUDA;
+  }
+  bytes += (int64_t)(n * sizeof(T));
+  if (src) {
+    e = cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      set_error(std::string("cudaMemcpy failed: ") + cudaGetErrorString(e));
+      return LOOPS_ERR_CUDA;
+    }
+  }
+  return LOOPS_OK;
+}
+
+template <typename T>
+loops_status dev_download(std::vector<T>& dst, const T* src, size_t n) {
+  dst.resize(n);
+  if (n == 0) return LOOPS_OK;
+  cudaError_t e = cudaMemcpy(dst.data(), src, n * sizeof(T), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) {
+    set_error(std::string("cudaMemcpy failed: ") + cudaGetErrorString(e));
+    return LOOPS_ERR_CUDA;
+  }
+  return LOOPS_OK;
+}
+
+// f64 values that are already representable in the dtype -> storage bytes.
+void encode_values(const double* v, size_t n, loops_dtype d, std::vector<uint8_t>& out) {
+  const int es = d == LOOPS_F64 ? 8 : d == LOOPS_F32 ? 4 : 2;
+  out.resize(n * es);
+  for (size_t i = 0; i < n; ++i) {
+    switch (d) {
+      case LOOPS_F64: std::memcpy(&out[i * 8], &v[i], 8); break;
+      case LOOPS_F32: { float f = (float)v[i]; std::memcpy(&out[i * 4], &f, 4); break; }
+      case LOOPS_F16: { uint16_t h = f64_to_f16_bits(v[i]); std::memcpy(&out[i * 2], &h, 2); break; }
+      case LOOPS_BF16: { uint16_t h = f64_to_bf16_bits(v[i]); std::memcpy(&out[i * 2], &h, 2); break; }
+    }
+  }
+}
+
+double decode_value(const uint8_t* p, loops_dtype d) {
+  switch (d) {
+    case LOOPS_F64: { double x; std::memcpy(&x, p, 8); return x; }
+    case LOOPS_F32: { float x; std::memcpy(&x, p, 4); return (double)x; }
+    case LOOPS_F16: { uint16_t h; std::memcpy(&h, p, 2); return f16_bits_to_f64(h); }
+    case LOOPS_BF16: { uint16_t h; std::memcpy(&h, p, 2); return bf16_bits_to_f64(h); }
+  }
+  return 0.0;
+}
+
+int bucket_of(int64_t len) {
+  int b = 0;
+  while ((1ll << (b + 1)) <= len + 1 && b < 62) ++b;
+  return b;  // floor(log2(len + 1))
+}
+
+}  // namespace
+
+// Position in the fragment-ordered tile array of (tile t, row r), per dtype.
+int64_t frag_index(loops_dtype d, int64_t t, int32_t r, int32_t br) {
+  if (d == LOOPS_F64) {  // K = 4 tiles per group, 32 lanes x 1 value
+    const int64_t g = t / 4;
+    const int32_t tt = (int32_t)(t % 4);
+    return g * 32 + (int64_t)(r * 4 + tt);
+  }
+  if (d == LOOPS_F16 || d == LOOPS_BF16) {  // K = 16 tiles per group, 32 lanes x 8 values
+    const int64_t g = t / 16;
+    const int32_t k = (int32_t)(t % 16);
+    const int32_t q = r & 7, hi_r = r >> 3;          // row = q + 8 * hi_r
+    const int32_t hi_k = k >> 3, kk = k & 7;         // tile = 2*tq + lo + 8 * hi_k
+    const int32_t tq = kk >> 1, lo = kk & 1;
+    const int32_t lane = q * 4 + tq;
+    const int32_t j = hi_k * 4 + hi_r * 2 + lo;
+    return g * 256 + lane * 8 + j;
+  }
+  return t * br + r;
+}
+
+loops_status upload_part(loops_plan_s* p, int64_t N) {
+  const Canon& c = p->canon;
+  PartDev& d = p->dev;
+  d = PartDev();
+  loops_status st;
+  const int acc_bytes = p->dtype == LOOPS_F64 ? 8 : 4;
+
+  // ---- CSR work items
+  struct It { int32_t row; int64_t beg, end; int bucket; };
+  std::vector<It> items;
+  const int64_t n_csr = (int64_t)c.csr_rows.size();
+  items.reserve((size_t)n_csr);
+  const int64_t L = std::max<int64_t>(p->split_len, 1);
+  int64_t n_slots = 0;
+  for (int64_t x = 0; x < n_csr; ++x) {
+    const int64_t b = c.csr_ptr[(size_t)x], e = c.csr_ptr[(size_t)x + 1];
+    const int64_t len = e - b;
+    if (len > L) {
+      d.csr.h_split_row.push_back(c.csr_rows[(size_t)x]);
+      d.csr.h_split_slot_ptr.push_back((int32_t)n_slots);
+      for (int64_t s = b; s < e; s += L) {
+        items.push_back({(int32_t)(-1 - n_slots), s, std::min(s + L, e), 63});
+        ++n_slots;
+      }
+    } else {
+      items.push_back({c.csr_rows[(size_t)x], b, e, bucket_of(len)});
+    }
+  }
+  d.csr.h_split_slot_ptr.push_back((int32_t)n_slots);
+  std::stable_sort(items.begin(), items.end(), [](const It& a, const It& b) { return a.bucket > b.bucket; });
+  d.csr.n_items = (int64_t)items.size();
+  d.csr.n_split = (int64_t)d.csr.h_split_row.size();
+  d.csr.n_slots = n_slots;
+  d.csr.h_item_row.resize(items.size());
+  d.csr.h_item_ptr.resize(items.size() + 1);
+  d.csr.nnz = (int64_t)c.csr_col.size();
+  std::vector<int32_t> col((size_t)d.csr.nnz);
+  std::vector<double> val((size_t)d.csr.nnz);
+  int64_t pos = 0;
+  d.csr.h_item_ptr[0] = 0;
+  for (size_t i = 0; i < items.size(); ++i) {
+    d.csr.h_item_row[i] = items[i].row;
+    for (int64_t k = items[i].beg; k < items[i].end; ++k) {
+      col[(size_t)pos] = c.csr_col[(size_t)k];
+      val[(size_t)pos] = c.csr_val[(size_t)k];
+      ++pos;
+    }
+    d.csr.h_item_ptr[i + 1] = pos;
+  }
+  std::vector<uint8_t> enc;
+  encode_values(val.data(), val.size(), p->dtype, enc);
+  int64_t& bytes = d.device_bytes;
+  if ((st = dev_upload(&d.csr.item_row, d.csr.h_item_row.data(), items.size(), bytes))) return st;
+  if ((st = dev_upload(&d.csr.item_ptr, d.csr.h_item_ptr.data(), items.size() + 1, bytes))) return st;
+  if ((st = dev_upload(&d.csr.col, col.data(), col.size(), bytes))) return st;
+  if ((st = dev_upload((uint8_t**)&d.csr.val, enc.data(), enc.size(), bytes))) return st;
+  if (d.csr.n_split) {
+    if ((st = dev_upload(&d.csr.split_row, d.csr.h_split_row.data(), d.csr.h_split_row.size(), bytes))) return st;
+    if ((st = dev_upload(&d.csr.split_slot_ptr, d.csr.h_split_slot_ptr.data(), d.csr.h_split_slot_ptr.size(), bytes))) return st;
+    if ((st = dev_upload((uint8_t**)&d.csr.scratch, (const uint8_t*)nullptr,
+                         (size_t)(n_slots * std::max<int64_t>(N, 1) * acc_bytes), bytes))) return st;
+  }
+
+  // ---- BCSR part
+  const int64_t n_rb = (int64_t)c.rb_ids.size();
+  const int64_t n_t = (int64_t)c.tile_col.size();
+  d.bcsr.n_rb = n_rb;
+  d.bcsr.n_tiles = n_t;
+  if (n_rb) {
+    std::vector<double> fv((size_t)(n_t * c.br), 0.0);
+    for (int64_t t = 0; t < n_t; ++t)
+      for (int32_t r = 0; r < c.br; ++r)
+        fv[(size_t)frag_index(p->dtype, t, r, c.br)] = c.tile_val[(size_t)(t * c.br + r)];
+    encode_values(fv.data(), fv.size(), p->dtype, enc);
+    std::vector<int32_t> order((size_t)n_rb);
+    for (int64_t b = 0; b < n_rb; ++b) order[(size_t)b] = (int32_t)b;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+      return c.rb_ptr[(size_t)a + 1] - c.rb_ptr[(size_t)a] > c.rb_ptr[(size_t)b + 1] - c.rb_ptr[(size_t)b];
+    });
+    if ((st = dev_upload(&d.bcsr.rb_id, c.rb_ids.data(), (size_t)n_rb, bytes))) return st;
+    if ((st = dev_upload(&d.bcsr.rb_ptr, c.rb_ptr.data(), (size_t)n_rb + 1, bytes))) return st;
+    if ((st = dev_upload(&d.bcsr.tile_col, c.tile_col.data(), (size_t)n_t, bytes))) return st;
+    if ((st = dev_upload((uint8_t**)&d.bcsr.tile_val, enc.data(), enc.size(), bytes))) return st;
+    if ((st = dev_upload(&d.bcsr.order, order.data(), order.size(), bytes))) return st;
+  }
+  return LOOPS_OK;
+}
+
+void free_part(PartDev& d) {
+  void* ptrs[] = {d.csr.item_row, d.csr.item_ptr, d.csr.col, d.csr.val, d.csr.split_row,
+                  d.csr.split_slot_ptr, d.csr.scratch, d.bcsr.rb_id, d.bcsr.rb_ptr,
+                  d.bcsr.tile_col, d.bcsr.tile_val, d.bcsr.order};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  d = PartDev();
+}
+
+// Download the device arrays of a plan and rebuild the canonical partition from them.
+loops_status export_part(const loops_plan_s* p, loops_partition* out) {
+  const PartDev& d = p->dev;
+  const int es = p->dtype == LOOPS_F64 ? 8 : p->dtype == LOOPS_F32 ? 4 : 2;
+  loops_status st;
+  std::vector<int32_t> item_row, col, split_row, split_slot;
+  std::vector<int64_t> item_ptr;
+  std::vector<uint8_t> val;
+  if ((st = dev_download(item_row, d.csr.item_row, (size_t)d.csr.n_items))) return st;
+  if ((st = dev_download(item_ptr, d.csr.item_ptr, (size_t)(d.csr.n_items ? d.csr.n_items + 1 : 0)))) return st;
+  if ((st = dev_download(col, d.csr.col, (size_t)d.csr.nnz))) return st;
+  if ((st = dev_download(val, (const uint8_t*)d.csr.val, (size_t)(d.csr.nnz * es)))) return st;
+  if ((st = dev_download(split_row, d.csr.split_row, (size_t)d.csr.n_split))) return st;
+  if ((st = dev_download(split_slot, d.csr.split_slot_ptr, (size_t)(d.csr.n_split ? d.csr.n_split + 1 : 0)))) return st;
+  // slot -> split row index
+  std::vector<int32_t> slot_owner((size_t)d.csr.n_slots, -1);
+  for (int64_t s = 0; s < d.csr.n_split; ++s)
+    for (int32_t q = split_slot[(size_t)s]; q < split_slot[(size_t)s + 1]; ++q) slot_owner[(size_t)q] = (int32_t)s;
+  struct Row { int32_t row; std::vector<std::pair<int64_t, int64_t>> segs; };  // (slot or -1, item)
+  std::vector<Row> rows;
+  std::vector<int64_t> split_pos((size_t)d.csr.n_split, -1);
+  for (int64_t i = 0; i < d.csr.n_items; ++i) {
+    const int32_t r = item_row[(size_t)i];
+    if (r >= 0) {
+      rows.push_back({r, {{-1, i}}});
+    } else {
+      const int32_t slot = -1 - r;
+      const int32_t s = slot_owner[(size_t)slot];
+      if (split_pos[(size_t)s] < 0) {
+        split_pos[(size_t)s] = (int64_t)rows.size();
+        rows.push_back({split_row[(size_t)s], {}});
+      }
+      rows[(size_t)split_pos[(size_t)s]].segs.push_back({slot, i});
+    }
+  }
+  std::sort(rows.begin(), rows.end(), [](const Row& a, const Row& b) { return a.row < b.row; });
+  out->n_rows = p->n_rows;
+  out->n_cols = p->n_cols;
+  out->block_rows = p->br;
+  out->k_pad = p->kpad;
+  out->scale = p->scale;
+  out->n_csr_rows = (int64_t)rows.size();
+  out->nnz_csr = d.csr.nnz;
+  out->csr_rows = (int32_t*)std::malloc(sizeof(int32_t) * (rows.size() + 1));
+  out->csr_ptr = (int64_t*)std::malloc(sizeof(int64_t) * (rows.size() + 1));
+  out->csr_col = (int32_t*)std::malloc(sizeof(int32_t) * (size_t)(d.csr.nnz + 1));
+  out->csr_val = (double*)std::malloc(sizeof(double) * (size_t)(d.csr.nnz + 1));
+  int64_t k = 0;
+  out->csr_ptr[0] = 0;
+  for (size_t x = 0; x < rows.size(); ++x) {
+    auto segs = rows[x].segs;
+    std::sort(segs.begin(), segs.end());
+    out->csr_rows[x] = rows[x].row;
+    for (auto& sg : segs) {
+      for (int64_t e = item_ptr[(size_t)sg.second]; e < item_ptr[(size_t)sg.second + 1]; ++e) {
+        out->csr_col[k] = col[(size_t)e];
+        out->csr_val[k] = decode_value(&val[(size_t)(e * es)], p->dtype);
+        ++k;
+      }
+    }
+    out->csr_ptr[x + 1] = k;
+  }
+  // BCSR
+  std::vector<int32_t> rb_id, tcol;
+  std::vector<int64_t> rb_ptr;
+  std::vector<uint8_t> tval;
+  const int64_t n_rb = d.bcsr.n_rb, n_t = d.bcsr.n_tiles;
+  if ((st = dev_download(rb_id, d.bcsr.rb_id, (size_t)n_rb))) return st;
+  if ((st = dev_download(rb_ptr, d.bcsr.rb_ptr, (size_t)(n_rb ? n_rb + 1 : 0)))) return st;
+  if ((st = dev_download(tcol, d.bcsr.tile_col, (size_t)n_t))) return st;
+  if ((st = dev_download(tval, (const uint8_t*)d.bcsr.tile_val, (size_t)(n_t * p->br * es)))) return st;
+  out->n_row_blocks = n_rb;
+  out->n_tiles = n_t;
+  out->rb_ids = (int32_t*)std::malloc(sizeof(int32_t) * (size_t)(n_rb + 1));
+  out->rb_ptr = (int64_t*)std::malloc(sizeof(int64_t) * (size_t)(n_rb + 1));
+  out->tile_col = (int32_t*)std::malloc(sizeof(int32_t) * (size_t)(n_t + 1));
+  out->tile_val = (double*)std::malloc(sizeof(double) * (size_t)(n_t * p->br + 1));
+  out->rb_ptr[0] = 0;
+  for (int64_t b = 0; b < n_rb; ++b) {
+    out->rb_ids[b] = rb_id[(size_t)b];
+    out->rb_ptr[b + 1] = rb_ptr[(size_t)b + 1];
+  }
+  for (int64_t t = 0; t < n_t; ++t) {
+    out->tile_col[t] = tcol[(size_t)t];
+    for (int32_t r = 0; r < p->br; ++r)
+      out->tile_val[t * p->br + r] =
+          decode_value(&tval[(size_t)(frag_index(p->dtype, t, r, p->br) * es)], p->dtype);
+  }
+  return LOOPS_OK;
+}
+
+}  // namespace loops

@@ -1,0 +1,181 @@
+// Internal declarations shared by the host plan builder, the C-ABI layer and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/loops.h"
+
+namespace loops {
+
+// ------------------------------------------------------------------ errors
+void set_error(const std::string& msg);
+void clear_error();
+
+// A device-side wait gave up (bit set in the plan's error word).
+constexpr int32_t kErrWaitTimeout = 1;
+
+// Bound on mbarrier polls before a kernel records kErrWaitTimeout and leaves its loop.
+constexpr long long kMaxWaitPolls = 1ll << 24;
+
+// ------------------------------------------------------------------ dtypes
+inline int dense_elem_bytes(loops_dtype d) {  // B / dC element size
+  return d == LOOPS_F64 ? 8 : d == LOOPS_F32 ? 4 : 2;
+}
+inline int out_elem_bytes(loops_dtype d) {    // C / dB / dvals element size
+  return d == LOOPS_F64 ? 8 : 4;
+}
+inline int default_block_rows(loops_dtype d) { return d == LOOPS_F64 ? 8 : 16; }
+inline int k_pad_for(loops_dtype d) {  // MMA K of the BCSR kernel (tiles per MMA)
+  return d == LOOPS_F64 ? 4 : (d == LOOPS_F32 ? 1 : 16);
+}
+
+// Host rounding of binary64 into the storage formats (round to nearest, ties to even).
+uint16_t f64_to_f16_bits(double x);
+uint16_t f64_to_bf16_bits(double x);
+double f16_bits_to_f64(uint16_t h);
+double bf16_bits_to_f64(uint16_t h);
+
+// Power of two s with max|a| * s <= 2^14 for 16-bit dtypes, 1 otherwise.
+double plan_scale_for(const double* vals, int64_t nnz, loops_dtype d);
+
+// ------------------------------------------------------------------ canonical partition
+struct Canon {
+  int64_t n_rows = 0, n_cols = 0;
+  int32_t br = 8, kpad = 1;
+  double scale = 1.0;
+  std::vector<int32_t> csr_rows;
+  std::vector<int64_t> csr_ptr;   // size n_csr + 1
+  std::vector<int32_t> csr_col;
+  std::vector<double> csr_val;    // stored values (rounded, scaled) as f64
+  std::vector<int32_t> rb_ids;
+  std::vector<int64_t> rb_ptr;    // size n_rb + 1 (tile offsets)
+  std::vector<int32_t> tile_col;  // -1 for padding tiles
+  std::vector<double> tile_val;   // n_tiles * br
+  // input-entry -> storage map (for value updates): kind 0 CSR (index into csr_val),
+  // 1 BCSR (index into tile_val)
+  std::vector<int64_t> src_slot;  // per input entry k: slot index (CSR) or tile*br + r (BCSR)
+  std::vector<uint8_t> src_kind;
+};
+
+// Validate a CSR input. Returns LOOPS_OK or an error status (message set).
+loops_status validate_csr(const loops_csr* A);
+
+// Read A's values as f64 into `out` (host).
+void read_vals_f64(const loops_csr* A, std::vector<double>& out);
+
+// Algorithm 1 with the structural split (see partition.cpp).
+loops_status build_canon(const loops_csr* A, const double* vals, loops_dtype dtype, int32_t br,
+                         double tau, bool contiguous, int64_t r_boundary, Canon& out);
+
+// Round raw f64 values into the dtype after scaling (used by build_canon and updates).
+double round_store(double v, double scale, loops_dtype d);
+
+// ------------------------------------------------------------------ device layout
+// CSR part work items: item i covers entries [item_ptr[i], item_ptr[i+1]) of col/val and
+// writes C row item_row[i] (>= 0) or partial-sum slot -1 - item_row[i] (< 0).
+struct CsrDev {
+  int64_t n_items = 0, nnz = 0;
+  int32_t* item_row = nullptr;
+  int64_t* item_ptr = nullptr;
+  int32_t* col = nullptr;
+  void* val = nullptr;                 // dtype storage type
+  int64_t n_split = 0, n_slots = 0;
+  int32_t* split_row = nullptr;        // global C row of each split row
+  int32_t* split_slot_ptr = nullptr;   // size n_split + 1
+  void* scratch = nullptr;             // n_slots x N partial sums (accumulator type)
+  // host mirrors used for export
+  std::vector<int32_t> h_item_row;
+  std::vector<int64_t> h_item_ptr;
+  std::vector<int32_t> h_split_row;
+  std::vector<int32_t> h_split_slot_ptr;
+};
+
+// BCSR part: block b has tiles [rb_ptr[b], rb_ptr[b+1]) (a multiple of k_pad), global row
+// block id rb_id[b]. tile_val is stored in the MMA fragment order of the dtype's kernel.
+struct BcsrDev {
+  int64_t n_rb = 0, n_tiles = 0;
+  int32_t* rb_id = nullptr;
+  int64_t* rb_ptr = nullptr;
+  int32_t* tile_col = nullptr;
+  void* tile_val = nullptr;
+  int32_t* order = nullptr;            // processing order of blocks (most tiles first)
+};
+
+struct PartDev {
+  CsrDev csr;
+  BcsrDev bcsr;
+  int64_t device_bytes = 0;
+};
+
+// Original pattern kept for the SDDMM (dvals in A's input order), split in items.
+struct SddmmDev {
+  int64_t n_items = 0;
+  int32_t* item_row = nullptr;
+  int64_t* item_beg = nullptr;         // size n_items + 1 is not used: begin/end pairs
+  int64_t* item_end = nullptr;
+  int32_t* col = nullptr;              // input order columns (nnz)
+};
+
+struct Plan;
+
+}  // namespace loops
+
+// Opaque plan handle of the C ABI.
+struct loops_plan_s {
+  uint64_t magic;
+  loops_dtype dtype;
+  int64_t n_rows, n_cols, nnz, N;
+  int32_t br, kpad;
+  double tau;
+  double scale;
+  int32_t split_len;
+  loops_plan_opts opts;
+  loops::Canon canon;                  // host copy (canonical order)
+  loops::PartDev dev;
+  loops_plan_s* transposed;            // plan of A^T for dB (want_backward)
+  loops::SddmmDev sddmm;
+  std::vector<int64_t> t_perm;         // A^T entry e comes from input entry t_perm[e]
+  int32_t* d_error;                    // device error word
+  cudaStream_t side;                   // second stream for the BCSR part
+  cudaEvent_t ev_fork, ev_join;
+  void* stage_B;                       // loops_spmm_host staging buffers
+  void* stage_C;
+  int64_t stage_B_bytes, stage_C_bytes;
+  int64_t n_subnormal;
+  int64_t nnz_bcsr;
+};
+
+namespace loops {
+
+constexpr uint64_t kPlanMagic = 0x4c4f4f5053504c4eull;  // "LOOPSPLN"
+
+// Device upload of a canonical partition (partition.cpp). Sets plan->dev.
+loops_status upload_part(loops_plan_s* plan, int64_t N);
+void free_part(PartDev& d);
+
+// ------------------------------------------------------------------ kernel launchers
+struct DenseArgs {
+  const void* B;
+  int64_t ldb;
+  void* C;
+  int64_t ldc;
+  const float* col_scale;   // may be null
+  float inv_scale_f;        // 1 / s_A (16-bit)
+  double inv_scale_d;
+  int64_t N;
+  int64_t n_rows;           // rows of C (bounds for BCSR tails)
+};
+
+cudaError_t launch_csr(const loops_plan_s* p, const CsrDev& d, const DenseArgs& a, cudaStream_t s);
+cudaError_t launch_bcsr(const loops_plan_s* p, const BcsrDev& d, const DenseArgs& a, cudaStream_t s);
+cudaError_t launch_sddmm(const loops_plan_s* p, const void* dC, int64_t lddc, const void* B,
+                         int64_t ldb, void* dvals, cudaStream_t s);
+cudaError_t launch_cast_scaled(const float* X, int64_t rows, int64_t cols, int64_t ldx,
+                               loops_dtype yd, void* Y, int64_t ldy, float* col_scale,
+                               cudaStream_t s);
+
+}  // namespace loops

@@ -15,3 +15,11 @@ def pytest_configure(config):
 @pytest.fixture(scope="session")
 def golden_dir():
     return os.path.join(ROOT, "tests", "golden")
+
+
+@pytest.fixture(scope="session")
+def loops_lib():
+    """Build (if needed) and load libloops.so. nvcc cross-compiles for sm_103a without a GPU."""
+    import paper_2511_08158_gb300 as lp
+    lp.build()
+    return lp
