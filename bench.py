@@ -1,0 +1,368 @@
+#!/usr/bin/env python
+"""Benchmark of the LOOPS hybrid SpMM on GB300: SpMM GFLOP/s (2 * nnz * N per call) and the
+roofline fractions, hybrid vs CSR-only, on the FP64 hybrid-split workload: the 512 x 512
+five-point Laplacian with 4,096 random dense 8 x 8 diagonal blocks added (262,144 rows,
+1,480,704 nonzeros), B 262,144 x 64 in FP64 N(0, 1). Synthetic, seeded inputs.
+
+One step is one C = A . B call of the whole hot path (CSR part and BCSR part) on inputs
+resident in HBM; the plan (the partition, built once, as the paper excludes format
+conversion from its timing) is made before timing. L2 is flushed (a 256 MiB write) before
+every timed step and each step is timed on the device with CUDA events.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl loops|reference] [--N 64]
+
+Under torchrun each rank runs its own replica of the workload on its GPU (the path needs no
+exchange); rank 0 prints one JSON line with the whole-job throughput (max time over ranks).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "SpMM GFLOP/s (2·nnz·N) and % HBM roofline, hybrid vs CSR-only at stated rel-L2"
+HBM_NOMINAL_GBS = 8000.0
+# FP64 peak of GB300 from unit counts and clock: 152 SMs x 2 FP64 FMA/clk x 2 FLOP x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+TOL_F64 = 1e-12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["loops", "reference"], default="loops")
+    ap.add_argument("--N", type=int, default=64)
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload(N: int):
+    A, B = W.laplacian_blocks(grid=512, n_blocks=4096, block=8, seed=1, N=N)
+    return A, B
+
+
+def config(N: int):
+    return {"workload": f"laplacian512+4096x8x8 blocks, FP64, N={N}", "n_rows": 262144, "nnz": 1480704,
+            "N": N, "dtype": "f64", "l2": "flushed before every timed step (256 MiB write)",
+            "plan": "built once before timing (conversion excluded as in the paper)"}
+
+
+def alg_bytes(A, N: int, eb: int = 8) -> int:
+    return (A.n_rows + 1) * 8 + A.nnz * (4 + eb) + A.n_cols * N * eb + A.n_rows * N * eb
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"loops_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+def traffic_for(kernel_key: str):
+    """DRAM bytes per launch of a kernel from the committed ncu summary, if the kernel's
+    source is unchanged since the capture (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p)).get(kernel_key)
+    if not d:
+        return None
+    src = os.path.join(ROOT, d["source"])
+    if not os.path.exists(src):
+        return None
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    return d["dram_bytes_per_launch"] if sha == d["source_sha256"] else None
+
+
+def cpu_baseline(A, B, budget_s: float = 12.0):
+    """The oracle as it stands, single-threaded, on the full workload, repeated for about
+    `budget_s` seconds. Returns (GFLOP/s, C_oracle, reps)."""
+    import oracle
+
+    oracle.build()
+    flops = 2.0 * A.nnz * B.shape[1]
+    reps, t_tot, C = 0, 0.0, None
+    while reps < 1 or (t_tot < budget_s and reps < 200):
+        t0 = time.perf_counter()
+        C = oracle.spmm(A, B)
+        t_tot += time.perf_counter() - t0
+        reps += 1
+    return flops * reps / t_tot / 1e9, C, reps, t_tot
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    import oracle
+
+    oracle.build()
+    A, B = workload(args.N)
+    flops = 2.0 * A.nnz * args.N
+    for _ in range(args.warmup):
+        oracle.spmm(A, B)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.spmm(A, B)
+        times.append(time.perf_counter() - t0)
+    t = sum(times) / len(times)
+    v = flops / t / 1e9
+    line = {"metric": METRIC, "value": v, "unit": "GFLOP/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)", "config": config(args.N),
+            "impl": "reference",
+            "cpu_baseline": {"value": v, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+                             "sample": "full workload per step (single-threaded C oracle, FP64)"},
+            "e2e": {"value": v, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def time_plan(torch, plan, Bd, Cd, steps, warmup, flush, part_events=True):
+    """Per-step device times (ms) of plan.spmm, and of its CSR / BCSR parts."""
+    for _ in range(warmup):
+        plan.spmm(Bd, Cd)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    pev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+    stream = torch.cuda.current_stream()
+    if part_events:
+        for row in pev:           # materialise the events so their handles exist
+            for e in row:
+                e.record(stream)
+        torch.cuda.synchronize()
+    for k in range(steps):
+        flush()
+        if part_events:
+            plan.set_timing_events([e.cuda_event for e in pev[k]])
+        ev[k][0].record(stream)
+        plan.spmm(Bd, Cd)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    plan.set_timing_events(None)
+    step = [a.elapsed_time(b) for a, b in ev]
+    csr = [r[0].elapsed_time(r[1]) for r in pev] if part_events else []
+    bcsr = [r[2].elapsed_time(r[3]) for r in pev] if part_events else []
+    return step, csr, bcsr
+
+
+def launches_per_step(info) -> int:
+    return int(info["n_csr_rows"] > 0) + int(info["n_split_rows"] > 0) + int(info["n_row_blocks"] > 0)
+
+
+def run_loops(args):
+    import torch
+
+    import paper_2511_08158_gb300 as lp
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if rank == 0:
+        lp.build()
+    if world > 1:
+        torch.distributed.barrier(device_ids=[local])
+    lp.load()
+    N = args.N
+    A, B = workload(N)
+    flops = 2.0 * A.nnz * N
+    hbm_peak, hbm_src = peaks()
+
+    Bd = torch.as_tensor(B).cuda()
+    Cd = torch.empty((A.n_rows, N), dtype=torch.float64, device="cuda")
+    flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    flush = lambda: flush_buf.zero_()  # noqa: E731
+
+    t0 = time.perf_counter()
+    plan = lp.Plan(A, N, "f64", tau=-1.0)           # autotuned split
+    plan_s = time.perf_counter() - t0
+    info = plan.info()
+    variants = {"csr_only": math.inf, "hybrid_tau2": 2.0, "bcsr_only": 0.0}
+    vplans = {k: lp.Plan(A, N, "f64", tau=t) for k, t in variants.items()}
+
+    # main timed region: K steps, barrier + synchronize on both sides
+    sampler = ClockSampler(local)
+    for _ in range(args.warmup):
+        plan.spmm(Bd, Cd)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier(device_ids=[local])
+    sampler.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    step, csr, bcsr = time_plan(torch, plan, Bd, Cd, args.steps, 0, flush)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    if world > 1:
+        torch.distributed.barrier(device_ids=[local])
+    total_ms = sum(step)
+    t_max = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(t_max, op=torch.distributed.ReduceOp.MAX)
+    total_ms = float(t_max.item())
+    ms_step = total_ms / args.steps
+    value = world * flops / (ms_step * 1e-3) / 1e9
+
+    # variants (same inputs, same accuracy), fewer steps
+    var_out = {}
+    for k, p in vplans.items():
+        s, c, b = time_plan(torch, p, Bd, Cd, max(10, args.steps // 2), 3, flush)
+        inf_ = p.info()
+        var_out[k] = {"tau": variants[k], "gflops": flops / (statistics.mean(s) * 1e-3) / 1e9,
+                      "ms_per_step": statistics.mean(s), "bcsr_row_blocks": inf_["n_row_blocks"],
+                      "bcsr_tiles": inf_["n_tiles"], "csr_ms": statistics.mean(c), "bcsr_ms": statistics.mean(b)}
+    # restore the main plan's output for the parity check below
+    plan.spmm(Bd, Cd)
+    torch.cuda.synchronize()
+
+    # dominant kernel of the step and its roofline (FP64 here is bound by the FP64 pipe)
+    csr_ms, bcsr_ms = statistics.mean(csr), statistics.mean(bcsr)
+    if csr_ms >= bcsr_ms:
+        dom, dom_ms, dom_nnz = "csr_spmm_vec<TrF64,32,1,8>", csr_ms, info["nnz_csr"]
+        tkey = "csr_spmm_f64_n64"
+    else:
+        dom, dom_ms, dom_nnz = "bcsr_dmma<4>", bcsr_ms, info["nnz_bcsr"]
+        tkey = "bcsr_dmma_f64_n64"
+    dom_tflops = 2.0 * dom_nnz * N / (dom_ms * 1e-3) / 1e12
+    traffic = traffic_for(tkey) if N == 64 else None
+    roofline = {"bound": "alu", "kernel": dom, "achieved": dom_tflops, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": dom_tflops / FP64_PEAK_TFLOPS, "traffic": traffic,
+                "peak_source": "FP64: 152 SMs x 2 FMA/clk x 2 FLOP x 2.07 GHz (nominal unit count)",
+                "kernel_ms": dom_ms}
+    step_bytes = alg_bytes(A, N)
+    hbm = {"alg_bytes_per_step": step_bytes, "achieved_gbs": step_bytes / (ms_step * 1e-3) / 1e9,
+           "frac_of_measured": step_bytes / (ms_step * 1e-3) / 1e9 / hbm_peak,
+           "frac_of_8tbs": step_bytes / (ms_step * 1e-3) / 1e9 / HBM_NOMINAL_GBS, "peak_gbs": hbm_peak,
+           "peak_source": hbm_src}
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        Bh = torch.as_tensor(B).pin_memory()
+        Ch = torch.empty((A.n_rows, N), dtype=torch.float64).pin_memory()
+        for _ in range(2):
+            plan.spmm_host(Bh, Ch)
+        k_e2e = max(3, min(args.steps, 20))
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(k_e2e):
+            plan.spmm_host(Bh, Ch)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_e2e = e0.elapsed_time(e1) / k_e2e
+        e2e = {"value": world * flops / (t_e2e * 1e-3) / 1e9, "unit": "GFLOP/s",
+               "h2d_bytes_per_step": int(Bh.numel() * 8), "d2h_bytes_per_step": int(Ch.numel() * 8),
+               "ms_per_step": t_e2e, "api": "loops_spmm_host"}
+
+    if rank != 0:
+        return
+    cpu = None
+    rel = None
+    if world == 1:
+        v_cpu, C_ref, reps, t_tot = cpu_baseline(A, B)
+        cpu = {"value": v_cpu, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+               "sample": f"full workload x {reps} runs ({t_tot:.1f} s, single-threaded FP64 C oracle)"}
+        C = Cd.cpu().numpy()
+        rel = float(np.linalg.norm(C - C_ref) / np.linalg.norm(C_ref))
+    line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Laplacian + dense blocks, N(0,1) B)",
+            "config": dict(config(N), parallelism=f"replicas{world}", tau_autotuned=info["tau"],
+                           bcsr_row_blocks=info["n_row_blocks"], bcsr_tiles=info["n_tiles"],
+                           plan_build_s=plan_s),
+            "roofline": roofline, "hbm": hbm, "variants": var_out,
+            "rel_l2_vs_oracle": rel, "rel_l2_tol": TOL_F64,
+            "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": launches_per_step(info) * args.steps,
+            "part_ms": {"csr": csr_ms, "bcsr": bcsr_ms}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_loops(args)
+
+
+if __name__ == "__main__":
+    main()

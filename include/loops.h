@@ -173,6 +173,14 @@ loops_status loops_plan_export(loops_plan_t plan, loops_partition* out);
 loops_status loops_plan_update_values(loops_plan_t plan, const void* vals, loops_dtype vals_dtype,
                                       loops_stream_t stream);
 
+/* Replace A's values from a DEVICE array (nnz values of vals_dtype, F64 or F32, in A's input
+ * order; same pattern) for a plan built with want_backward: both parts and the transposed
+ * plan are refreshed by a kernel on `stream` (stored value = round(s_A * sum of the entries
+ * of a slot, in input order), exactly as the host packer rounds). Stream-ordered; used by
+ * the autograd path so that C = A(vals) . B follows the current values. */
+loops_status loops_plan_set_values(loops_plan_t plan, const void* vals, loops_dtype vals_dtype,
+                                   loops_stream_t stream);
+
 /* C = A . B. B: device, n_cols x N (row-major, ldb); C: device, n_rows x N (ldc); element
  * types per the table above. Overwrites C (no accumulation into it). Stream-ordered. */
 loops_status loops_spmm(loops_plan_t plan, const void* B, int64_t ldb, void* C, int64_t ldc,
@@ -207,6 +215,12 @@ loops_status loops_spmm_backward(loops_plan_t plan, const void* dC, int64_t lddc
 loops_status loops_cast_scaled(const float* X, int64_t rows, int64_t cols, int64_t ldx,
                                loops_dtype y_dtype, void* Y, int64_t ldy, float* col_scale,
                                loops_stream_t stream);
+
+/* Profiling hook: events[0..3] are caller-owned cudaEvent_t handles (timing enabled). Every
+ * later loops_spmm* call on this plan records events[0]/events[1] around the CSR-part
+ * launches (on the call's stream) and events[2]/events[3] around the BCSR-part launch (on the
+ * stream that runs it), back to back when a part is empty. NULL disables the hook. Host only. */
+loops_status loops_plan_set_timing_events(loops_plan_t plan, void* const* events);
 
 /* Read and clear the plan's device error word (synchronises `stream`): LOOPS_OK, or
  * LOOPS_ERR_TIMEOUT when a bounded device-side wait gave up in an earlier launch. */

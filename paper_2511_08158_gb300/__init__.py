@@ -31,7 +31,7 @@ EXPORTED = ["loops_version", "loops_status_str", "loops_last_error", "loops_plan
             "loops_partition_host", "loops_partition_free", "loops_plan", "loops_plan_destroy",
             "loops_plan_info_get", "loops_plan_export", "loops_plan_update_values", "loops_spmm",
             "loops_spmm_scaled", "loops_spmm_host", "loops_spmm_backward", "loops_cast_scaled",
-            "loops_plan_check"]
+            "loops_plan_check", "loops_plan_set_timing_events", "loops_plan_set_values"]
 
 
 class LoopsError(RuntimeError):
@@ -110,6 +110,8 @@ def load():
     L.loops_spmm_backward.argtypes = [vp, vp, i64, vp, i64, vp, i64, vp, vp]
     L.loops_cast_scaled.argtypes = [vp, i64, i64, i64, ctypes.c_int, vp, i64, vp, vp]
     L.loops_plan_check.argtypes = [vp, vp]
+    L.loops_plan_set_values.argtypes = [vp, vp, ctypes.c_int, vp]
+    L.loops_plan_set_timing_events.argtypes = [vp, ctypes.POINTER(ctypes.c_void_p)]
     for name in EXPORTED:
         fn = getattr(L, name)
         if name not in ("loops_version", "loops_status_str", "loops_last_error", "loops_plan_opts_default",
@@ -242,6 +244,15 @@ class Plan:
         finally:
             self._L.loops_partition_free(ctypes.byref(part))
 
+    def set_timing_events(self, events):
+        """events: 4 raw cudaEvent_t handles (ints) recorded around the CSR and BCSR parts of
+        each later spmm call, or None to stop."""
+        if events is None:
+            _check(self._L.loops_plan_set_timing_events(self._h, None))
+            return
+        arr = (ctypes.c_void_p * 4)(*[ctypes.c_void_p(int(e)) for e in events])
+        _check(self._L.loops_plan_set_timing_events(self._h, arr))
+
     def check(self, stream=None):
         _check(self._L.loops_plan_check(self._h, _stream_handle(stream)))
 
@@ -251,6 +262,17 @@ class Plan:
         if vd == F64:
             v = np.ascontiguousarray(v, dtype=np.float64)
         _check(self._L.loops_plan_update_values(self._h, v.ctypes.data, vd, _stream_handle(stream)))
+
+    def set_values(self, vals, stream=None):
+        """Refresh A's values from a CUDA tensor (float64/float32, input order, nnz entries)."""
+        torch = _torch()
+        if not (isinstance(vals, torch.Tensor) and vals.is_cuda and vals.dim() == 1 and vals.numel() == self.nnz):
+            raise ValueError("vals must be a 1-D CUDA tensor with nnz entries")
+        if vals.dtype not in (torch.float64, torch.float32):
+            raise TypeError("vals must be float64 or float32")
+        vals = vals.contiguous()
+        _check(self._L.loops_plan_set_values(self._h, vals.data_ptr(), F64 if vals.dtype == torch.float64 else F32,
+                                             _stream_handle(stream)))
 
     def out_dtype(self):
         return getattr(_torch(), _TORCH_OUT[self.dtype])
@@ -322,13 +344,14 @@ def _autograd_fn():
 
     class LoopsSpMM(torch.autograd.Function):
         """C = A(vals) . B with the plan's pattern. Backward: dB = A^T . dC (transposed hybrid
-        SpMM), dvals = SDDMM(dC, B^T) on A's pattern. ``vals`` must equal the plan's values
-        (use Plan.update_values after changing them)."""
+        SpMM), dvals = SDDMM(dC, B^T) on A's pattern. The forward refreshes the plan's stored
+        values from ``vals`` on the device (plan built with want_backward)."""
 
         @staticmethod
         def forward(ctx, vals, B, plan):
             ctx.plan = plan
             ctx.save_for_backward(B)
+            plan.set_values(vals.detach())
             return plan.spmm(B.contiguous())
 
         @staticmethod

@@ -78,6 +78,7 @@ static void destroy_plan(loops_plan_s* p) {
   if (!p) return;
   if (p->transposed) destroy_plan(p->transposed);
   free_part(p->dev);
+  free_value_maps(p->vmap);
   void* ptrs[] = {p->sddmm.item_row, p->sddmm.item_beg, p->sddmm.item_end, p->sddmm.col,
                   p->d_error, p->stage_B, p->stage_C};
   for (void* q : ptrs)
@@ -112,6 +113,8 @@ static loops_status make_plan(const loops_csr* A, const double* vals, int64_t N,
   p->ev_fork = p->ev_join = nullptr;
   p->stage_B = p->stage_C = nullptr;
   p->stage_B_bytes = p->stage_C_bytes = 0;
+  p->timing = false;
+  for (auto& ev : p->tev) ev = nullptr;
   loops_status st = build_canon(A, vals, dtype, br, tau, o.contiguous_split != 0, o.r_boundary, p->canon);
   if (st) { destroy_plan(p); return st; }
   p->scale = p->canon.scale;
@@ -207,18 +210,27 @@ static loops_status run_spmm(loops_plan_s* p, const void* B, int64_t ldb, const 
   a.n_rows = p->n_rows;
   const bool has_csr = p->dev.csr.n_items > 0;
   const bool has_bcsr = p->dev.bcsr.n_rb > 0;
+  const bool tm = p->timing;
+  auto rec = [&](int i, cudaStream_t st) { return tm ? cudaEventRecord(p->tev[i], st) : cudaSuccess; };
   cudaError_t e = cudaSuccess;
   if (has_csr && has_bcsr) {
     e = cudaEventRecord(p->ev_fork, s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(p->side, p->ev_fork, 0);
+    if (e == cudaSuccess) e = rec(2, p->side);
     if (e == cudaSuccess) e = launch_bcsr(p, p->dev.bcsr, a, p->side);
+    if (e == cudaSuccess) e = rec(3, p->side);
+    if (e == cudaSuccess) e = rec(0, s);
     if (e == cudaSuccess) e = launch_csr(p, p->dev.csr, a, s);
+    if (e == cudaSuccess) e = rec(1, s);
     if (e == cudaSuccess) e = cudaEventRecord(p->ev_join, p->side);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->ev_join, 0);
-  } else if (has_bcsr) {
-    e = launch_bcsr(p, p->dev.bcsr, a, s);
-  } else if (has_csr) {
-    e = launch_csr(p, p->dev.csr, a, s);
+  } else {
+    if (e == cudaSuccess) e = rec(2, s);
+    if (e == cudaSuccess && has_bcsr) e = launch_bcsr(p, p->dev.bcsr, a, s);
+    if (e == cudaSuccess) e = rec(3, s);
+    if (e == cudaSuccess) e = rec(0, s);
+    if (e == cudaSuccess && has_csr) e = launch_csr(p, p->dev.csr, a, s);
+    if (e == cudaSuccess) e = rec(1, s);
   }
   return cuda_status(e, "SpMM launch");
 }
@@ -386,6 +398,8 @@ loops_status loops_plan(const loops_csr* A, int64_t N, loops_dtype dtype, const 
     if ((st = make_plan(&At, tv.data(), N, dtype, ot, br, tau, &pt))) { destroy_plan(p); return st; }
     p->transposed = pt;
     if ((st = build_sddmm(p, A))) { destroy_plan(p); return st; }
+    if ((st = upload_value_maps(p, nullptr))) { destroy_plan(p); return st; }
+    if ((st = upload_value_maps(pt, &p->t_perm))) { destroy_plan(p); return st; }
   }
   *out = p;
   return LOOPS_OK;
@@ -478,6 +492,22 @@ loops_status loops_plan_update_values(loops_plan_t p, const void* vals, loops_dt
   return LOOPS_OK;
 }
 
+loops_status loops_plan_set_values(loops_plan_t p, const void* vals, loops_dtype vd, loops_stream_t stream) {
+  clear_error();
+  loops_status st = check_plan(p);
+  if (st) return st;
+  if (!p->transposed) {
+    set_error("plan was built without want_backward (no device value maps)");
+    return LOOPS_ERR_STATE;
+  }
+  if (vd != LOOPS_F64 && vd != LOOPS_F32) { set_error("vals must be F64 or F32"); return LOOPS_ERR_UNSUPPORTED; }
+  if (!vals && p->nnz) { set_error("vals is NULL"); return LOOPS_ERR_INVALID_ARG; }
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = launch_set_values(p, vals, vd, s);
+  if (e == cudaSuccess) e = launch_set_values(p->transposed, vals, vd, s);
+  return cuda_status(e, "value refresh launch");
+}
+
 loops_status loops_spmm(loops_plan_t p, const void* B, int64_t ldb, void* C, int64_t ldc,
                         loops_stream_t stream) {
   return loops_spmm_scaled(p, B, ldb, nullptr, C, ldc, stream);
@@ -567,6 +597,23 @@ loops_status loops_cast_scaled(const float* X, int64_t rows, int64_t cols, int64
   if (!col_scale || (rows > 0 && (!X || !Y))) { set_error("NULL pointer"); return LOOPS_ERR_INVALID_ARG; }
   return cuda_status(launch_cast_scaled(X, rows, cols, ldx, yd, Y, ldy, col_scale, (cudaStream_t)stream),
                      "cast launch");
+}
+
+loops_status loops_plan_set_timing_events(loops_plan_t p, void* const* events) {
+  clear_error();
+  loops_status st = check_plan(p);
+  if (st) return st;
+  if (!events) {
+    p->timing = false;
+    for (auto& ev : p->tev) ev = nullptr;
+    return LOOPS_OK;
+  }
+  for (int i = 0; i < 4; ++i) {
+    if (!events[i]) { set_error("timing event is NULL"); return LOOPS_ERR_INVALID_ARG; }
+    p->tev[i] = (cudaEvent_t)events[i];
+  }
+  p->timing = true;
+  return LOOPS_OK;
 }
 
 loops_status loops_plan_check(loops_plan_t p, loops_stream_t stream) {

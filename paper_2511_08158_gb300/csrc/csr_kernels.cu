@@ -457,7 +457,68 @@ __global__ void __launch_bounds__(256) scale_cast_kernel(const float* __restrict
   }
 }
 
+// ------------------------------------------------------------------ value refresh from device
+template <class T>
+__device__ __forceinline__ T from_f64(double x);
+template <>
+__device__ __forceinline__ double from_f64<double>(double x) { return x; }
+template <>
+__device__ __forceinline__ float from_f64<float>(double x) { return __double2float_rn(x); }
+template <>
+__device__ __forceinline__ __half from_f64<__half>(double x) { return __double2half(x); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 from_f64<__nv_bfloat16>(double x) { return __double2bfloat16(x); }
+
+// Stored value = round(scale * sum of the slot's input entries in input order), as the host
+// packer does: CSR positions have one source each, BCSR fragment slots zero or more.
+template <class TB, class TIn>
+__global__ void __launch_bounds__(256) set_values_kernel(const TIn* __restrict__ vals, double scale,
+                                                         const int64_t* __restrict__ csr_src, int64_t n_csr,
+                                                         TB* __restrict__ csr_val,
+                                                         const int64_t* __restrict__ bptr,
+                                                         const int64_t* __restrict__ bsrc, int64_t n_slots,
+                                                         TB* __restrict__ tile_val) {
+  const int64_t total = n_csr + n_slots;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    if (i < n_csr) {
+      csr_val[i] = from_f64<TB>((double)vals[csr_src[i]] * scale);
+    } else {
+      const int64_t f = i - n_csr;
+      double acc = 0.0;
+      for (int64_t q = bptr[f]; q < bptr[f + 1]; ++q) acc += (double)vals[bsrc[q]];
+      tile_val[f] = from_f64<TB>(acc * scale);
+    }
+  }
+}
+
+template <class TB>
+cudaError_t launch_set_values_t(const loops_plan_s* p, const void* vals, loops_dtype vd, cudaStream_t s) {
+  const ValueMapDev& m = p->vmap;
+  const int64_t total = m.n_csr + m.n_slots;
+  if (total == 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 8);
+  if (vd == LOOPS_F64)
+    set_values_kernel<TB, double><<<blocks, 256, 0, s>>>((const double*)vals, p->scale, m.csr_src, m.n_csr,
+                                                          (TB*)p->dev.csr.val, m.bcsr_ptr, m.bcsr_src, m.n_slots,
+                                                          (TB*)p->dev.bcsr.tile_val);
+  else
+    set_values_kernel<TB, float><<<blocks, 256, 0, s>>>((const float*)vals, p->scale, m.csr_src, m.n_csr,
+                                                         (TB*)p->dev.csr.val, m.bcsr_ptr, m.bcsr_src, m.n_slots,
+                                                         (TB*)p->dev.bcsr.tile_val);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_set_values(const loops_plan_s* p, const void* vals, loops_dtype vd, cudaStream_t s) {
+  switch (p->dtype) {
+    case LOOPS_F64: return launch_set_values_t<double>(p, vals, vd, s);
+    case LOOPS_F32: return launch_set_values_t<float>(p, vals, vd, s);
+    case LOOPS_F16: return launch_set_values_t<__half>(p, vals, vd, s);
+    case LOOPS_BF16: return launch_set_values_t<__nv_bfloat16>(p, vals, vd, s);
+  }
+  return cudaErrorInvalidValue;
+}
 
 cudaError_t launch_csr(const loops_plan_s* p, const CsrDev& d, const DenseArgs& a, cudaStream_t s) {
   switch (p->dtype) {

@@ -203,6 +203,80 @@ void free_part(PartDev& d) {
   d = PartDev();
 }
 
+loops_status upload_value_maps(loops_plan_s* p, const std::vector<int64_t>* remap) {
+  const Canon& c = p->canon;
+  const CsrDev& d = p->dev.csr;
+  ValueMapDev& m = p->vmap;
+  free_value_maps(m);
+  const int64_t nnz = (int64_t)c.src_slot.size();
+  // canonical CSR slot -> input entry, then device position -> input entry
+  std::vector<int64_t> canon_src(c.csr_col.size(), -1);
+  for (int64_t k = 0; k < nnz; ++k)
+    if (c.src_kind[(size_t)k] == 0) canon_src[(size_t)c.src_slot[(size_t)k]] = remap ? (*remap)[(size_t)k] : k;
+  // device order of the CSR entries: items in storage order, each a canonical range
+  std::vector<int64_t> csr_src;
+  csr_src.reserve(c.csr_col.size());
+  {
+    // rebuild the canonical start of each item: items cover canonical rows (or segments of
+    // them) and were laid out in item order; recover the canonical range from the row id and
+    // the segment offset
+    std::vector<int64_t> row_pos(c.csr_rows.size());
+    std::vector<int64_t> canon_row_of((size_t)std::max<int64_t>(p->n_rows, 1), -1);
+    for (size_t x = 0; x < c.csr_rows.size(); ++x) canon_row_of[(size_t)c.csr_rows[x]] = (int64_t)x;
+    std::vector<int64_t> seg_cursor(c.csr_rows.size(), 0);
+    // slot -> split row
+    std::vector<int32_t> slot_row((size_t)d.n_slots, -1);
+    for (int64_t sidx = 0; sidx < d.n_split; ++sidx)
+      for (int32_t q = d.h_split_slot_ptr[(size_t)sidx]; q < d.h_split_slot_ptr[(size_t)sidx + 1]; ++q)
+        slot_row[(size_t)q] = d.h_split_row[(size_t)sidx];
+    for (int64_t i = 0; i < d.n_items; ++i) {
+      const int32_t r = d.h_item_row[(size_t)i];
+      const int32_t row = r >= 0 ? r : slot_row[(size_t)(-1 - r)];
+      const int64_t x = canon_row_of[(size_t)row];
+      const int64_t len = d.h_item_ptr[(size_t)i + 1] - d.h_item_ptr[(size_t)i];
+      const int64_t b = c.csr_ptr[(size_t)x] + seg_cursor[(size_t)x];
+      for (int64_t e = 0; e < len; ++e) csr_src.push_back(canon_src[(size_t)(b + e)]);
+      seg_cursor[(size_t)x] += len;
+    }
+  }
+  // BCSR fragment slots -> input entries (ascending input order within a slot)
+  const int64_t n_slots = (int64_t)c.tile_col.size() * c.br;
+  std::vector<int64_t> cnt((size_t)n_slots + 1, 0);
+  for (int64_t k = 0; k < nnz; ++k)
+    if (c.src_kind[(size_t)k] == 1) {
+      const int64_t sl = c.src_slot[(size_t)k];
+      cnt[(size_t)frag_index(p->dtype, sl / c.br, (int32_t)(sl % c.br), c.br) + 1]++;
+    }
+  for (int64_t f = 0; f < n_slots; ++f) cnt[(size_t)f + 1] += cnt[(size_t)f];
+  std::vector<int64_t> pos(cnt.begin(), cnt.end() - 1), bsrc((size_t)cnt[(size_t)n_slots]);
+  // input order: for the transposed plan the entries' input order is given by remap
+  std::vector<std::pair<int64_t, int64_t>> order;  // (input index, entry)
+  for (int64_t k = 0; k < nnz; ++k)
+    if (c.src_kind[(size_t)k] == 1) order.push_back({remap ? (*remap)[(size_t)k] : k, k});
+  std::sort(order.begin(), order.end());
+  for (auto& ok : order) {
+    const int64_t sl = c.src_slot[(size_t)ok.second];
+    const int64_t f = frag_index(p->dtype, sl / c.br, (int32_t)(sl % c.br), c.br);
+    bsrc[(size_t)pos[(size_t)f]++] = ok.first;
+  }
+  m.n_csr = (int64_t)csr_src.size();
+  m.n_slots = n_slots;
+  loops_status st;
+  if ((st = dev_upload(&m.csr_src, csr_src.data(), csr_src.size(), m.bytes))) return st;
+  if (n_slots) {
+    if ((st = dev_upload(&m.bcsr_ptr, cnt.data(), cnt.size(), m.bytes))) return st;
+    if ((st = dev_upload(&m.bcsr_src, bsrc.data(), bsrc.size(), m.bytes))) return st;
+  }
+  return LOOPS_OK;
+}
+
+void free_value_maps(ValueMapDev& m) {
+  void* ptrs[] = {m.csr_src, m.bcsr_ptr, m.bcsr_src};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  m = ValueMapDev();
+}
+
 // Download the device arrays of a plan and rebuild the canonical partition from them.
 loops_status export_part(const loops_plan_s* p, loops_partition* out) {
   const PartDev& d = p->dev;

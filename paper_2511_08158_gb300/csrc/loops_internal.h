@@ -120,7 +120,16 @@ struct SddmmDev {
   int32_t* col = nullptr;              // input order columns (nnz)
 };
 
-struct Plan;
+// Device maps from A's input entries to the stored values, for loops_plan_set_values:
+// CSR position p of the device value array takes input entry csr_src[p]; BCSR fragment slot f
+// takes the sum (in input order) of input entries bcsr_src[bcsr_ptr[f] .. bcsr_ptr[f+1]).
+struct ValueMapDev {
+  int64_t n_csr = 0, n_slots = 0;
+  int64_t* csr_src = nullptr;
+  int64_t* bcsr_ptr = nullptr;
+  int64_t* bcsr_src = nullptr;
+  int64_t bytes = 0;
+};
 
 }  // namespace loops
 
@@ -138,6 +147,7 @@ struct loops_plan_s {
   loops::PartDev dev;
   loops_plan_s* transposed;            // plan of A^T for dB (want_backward)
   loops::SddmmDev sddmm;
+  loops::ValueMapDev vmap;
   std::vector<int64_t> t_perm;         // A^T entry e comes from input entry t_perm[e]
   int32_t* d_error;                    // device error word
   cudaStream_t side;                   // second stream for the BCSR part
@@ -147,6 +157,8 @@ struct loops_plan_s {
   int64_t stage_B_bytes, stage_C_bytes;
   int64_t n_subnormal;
   int64_t nnz_bcsr;
+  cudaEvent_t tev[4];                  // optional caller-owned timing events (may be null)
+  bool timing;
 };
 
 namespace loops {
@@ -156,6 +168,10 @@ constexpr uint64_t kPlanMagic = 0x4c4f4f5053504c4eull;  // "LOOPSPLN"
 // Device upload of a canonical partition (partition.cpp). Sets plan->dev.
 loops_status upload_part(loops_plan_s* plan, int64_t N);
 void free_part(PartDev& d);
+// Build and upload the value maps; `remap` (optional) maps the plan's entry order to the
+// caller's input order (the transposed plan).
+loops_status upload_value_maps(loops_plan_s* plan, const std::vector<int64_t>* remap);
+void free_value_maps(ValueMapDev& m);
 
 // ------------------------------------------------------------------ kernel launchers
 struct DenseArgs {
@@ -174,6 +190,7 @@ cudaError_t launch_csr(const loops_plan_s* p, const CsrDev& d, const DenseArgs& 
 cudaError_t launch_bcsr(const loops_plan_s* p, const BcsrDev& d, const DenseArgs& a, cudaStream_t s);
 cudaError_t launch_sddmm(const loops_plan_s* p, const void* dC, int64_t lddc, const void* B,
                          int64_t ldb, void* dvals, cudaStream_t s);
+cudaError_t launch_set_values(const loops_plan_s* p, const void* vals, loops_dtype vd, cudaStream_t s);
 cudaError_t launch_cast_scaled(const float* X, int64_t rows, int64_t cols, int64_t ldx,
                                loops_dtype yd, void* Y, int64_t ldy, float* col_scale,
                                cudaStream_t s);
