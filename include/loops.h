@@ -226,6 +226,35 @@ loops_status loops_plan_set_timing_events(loops_plan_t plan, void* const* events
  * LOOPS_ERR_TIMEOUT when a bounded device-side wait gave up in an earlier launch. */
 loops_status loops_plan_check(loops_plan_t plan, loops_stream_t stream);
 
+/* ---------------------------------------------------------------------------------------- */
+/* Allocation-free CSR SpMM. The paper has no counterpart: it serves callers that must not
+ * allocate device memory at the point where they multiply -- code being recorded into a CUDA
+ * graph under the global capture mode, host callbacks and latency-critical paths where an
+ * allocation could stall or fail, and services that reserve all device memory up front.
+ * loops_plan allocates (it owns the partition on the device), so such callers cannot build a
+ * plan; this entry point takes their CSR arrays as they are.
+ *
+ * Computes C = A . B with A given by DEVICE arrays row_ptr (int64[n_rows + 1]), col_idx
+ * (int32[nnz]) and vals (nnz values of `dtype`), B (device, n_cols x N, ldb) and C (device,
+ * n_rows x N, ldc) in the element types of the dtype table above (for F16/BF16 the values and
+ * B are used as given: no plan scale, no column scale). Rows are split into chunks of 128
+ * stored entries; the partial sums of rows that cross chunk boundaries are kept in one static
+ * device array of LOOPS_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until
+ * the process exits. The call allocates nothing (no cudaMalloc, no cudaFree, no allocating
+ * library routine) and returns LOOPS_ERR_UNSUPPORTED with a message when the problem needs
+ * more than that array: 2 * ceil(nnz / 128) * N * (8 for F64, else 4) bytes.
+ * Entries whose column lies outside [0, n_cols) are skipped; row_ptr values are clamped to
+ * [0, nnz]. The first call on a device looks up the array's device address (a one-time
+ * set-up with that device current), so make that first call before any stream capture.
+ * Every call uses the same array: calls that overlap on the GPU (for example on two
+ * concurrent streams) race and must be serialised by the caller. Stream-ordered. */
+#define LOOPS_NOALLOC_SCRATCH_BYTES (16u << 20)
+loops_status loops_csr_spmm_noalloc(int64_t n_rows, int64_t n_cols, int64_t nnz,
+                                    const int64_t* row_ptr, const int32_t* col_idx,
+                                    const void* vals, loops_dtype dtype, const void* B,
+                                    int64_t ldb, int64_t N, void* C, int64_t ldc,
+                                    loops_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -31,7 +31,8 @@ EXPORTED = ["loops_version", "loops_status_str", "loops_last_error", "loops_plan
             "loops_partition_host", "loops_partition_free", "loops_plan", "loops_plan_destroy",
             "loops_plan_info_get", "loops_plan_export", "loops_plan_update_values", "loops_spmm",
             "loops_spmm_scaled", "loops_spmm_host", "loops_spmm_backward", "loops_cast_scaled",
-            "loops_plan_check", "loops_plan_set_timing_events", "loops_plan_set_values"]
+            "loops_plan_check", "loops_plan_set_timing_events", "loops_plan_set_values",
+            "loops_csr_spmm_noalloc"]
 
 
 class LoopsError(RuntimeError):
@@ -111,6 +112,7 @@ def load():
     L.loops_cast_scaled.argtypes = [vp, i64, i64, i64, ctypes.c_int, vp, i64, vp, vp]
     L.loops_plan_check.argtypes = [vp, vp]
     L.loops_plan_set_values.argtypes = [vp, vp, ctypes.c_int, vp]
+    L.loops_csr_spmm_noalloc.argtypes = [i64, i64, i64, vp, vp, vp, ctypes.c_int, vp, i64, i64, vp, i64, vp]
     L.loops_plan_set_timing_events.argtypes = [vp, ctypes.POINTER(ctypes.c_void_p)]
     for name in EXPORTED:
         fn = getattr(L, name)
@@ -337,6 +339,17 @@ def cast_scaled(X, dtype: str = "f16", stream=None):
     _check(L.loops_cast_scaled(X.data_ptr(), X.shape[0], X.shape[1], X.stride(0), yd, Y.data_ptr(), Y.stride(0),
                                s.data_ptr(), _stream_handle(stream)))
     return Y, s
+
+
+def csr_spmm_noalloc(row_ptr, col_idx, vals, n_cols, B, C, stream=None):
+    """C = A . B from device CSR tensors (int64 row_ptr, int32 col_idx, vals of B's dtype)
+    without any device allocation (``loops_csr_spmm_noalloc``); C must be preallocated."""
+    torch = _torch()
+    dt = {torch.float64: F64, torch.float32: F32, torch.float16: F16, torch.bfloat16: BF16}[B.dtype]
+    _check(load().loops_csr_spmm_noalloc(
+        row_ptr.numel() - 1, n_cols, col_idx.numel(), row_ptr.data_ptr(), col_idx.data_ptr(), vals.data_ptr(), dt,
+        B.data_ptr(), B.stride(0), B.shape[1], C.data_ptr(), C.stride(0), _stream_handle(stream)))
+    return C
 
 
 def _autograd_fn():
