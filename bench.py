@@ -49,6 +49,10 @@ def parse():
     ap.add_argument("--impl", choices=["loops", "reference"], default="loops")
     ap.add_argument("--N", type=int, default=64)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", choices=["laplacian", "rmat", "gcn", "batched", "uniform"], default="laplacian",
+                    help="laplacian (default, the FP64 hybrid-split workload) or one of the other four "
+                         "synthetic workloads, measured the same way")
+    ap.add_argument("--dtype", default=None, help="rmat: f16 or bf16; batched: f32 or bf16")
     return ap.parse_args()
 
 
@@ -59,7 +63,8 @@ def workload(N: int):
 
 def config(N: int):
     return {"workload": f"laplacian512+4096x8x8 blocks, FP64, N={N}", "n_rows": 262144, "nnz": 1480704,
-            "N": N, "dtype": "f64", "l2": "flushed before every timed step (256 MiB write)",
+            "N": N, "dtype": "f64",
+            "l2": "flushed before every timed step (256 MiB write, then a 256 MiB read to clean it)",
             "plan": "built once before timing (conversion excluded as in the paper)"}
 
 
@@ -192,6 +197,19 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(torch, x: float, world: int, device) -> float:
+    """The largest value of x over all ranks (the job's time is its slowest rank's)."""
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gflops(flops_per_rank_step: float, world: int, ms_step: float) -> float:
+    """Whole-job throughput: every rank processes its own replica of the step."""
+    return world * flops_per_rank_step / (ms_step * 1e-3) / 1e9
+
+
 def time_plan(torch, plan, Bd, Cd, steps, warmup, flush, part_events=True):
     """Per-step device times (ms) of plan.spmm, and of its CSR / BCSR parts."""
     for _ in range(warmup):
@@ -246,8 +264,15 @@ def run_loops(args):
 
     Bd = torch.as_tensor(B).cuda()
     Cd = torch.empty((A.n_rows, N), dtype=torch.float64, device="cuda")
-    flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    flush = lambda: flush_buf.zero_()  # noqa: E731
+    # L2 flush: write a 256 MiB buffer (larger than the 126 MiB L2), then read another one so
+    # the dirty lines are written back before the timed kernel starts, not during it
+    flush_w = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    flush_r = torch.ones(64 << 20, dtype=torch.float32, device="cuda")
+    flush_out = torch.empty((), dtype=torch.float32, device="cuda")
+
+    def flush():
+        flush_w.zero_()
+        torch.sum(flush_r, dim=0, out=flush_out)
 
     t0 = time.perf_counter()
     plan = lp.Plan(A, N, "f64", tau=-1.0)           # autotuned split
@@ -266,18 +291,17 @@ def run_loops(args):
     sampler.start()
     time.sleep(0.3)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("timed")
     step, csr, bcsr = time_plan(torch, plan, Bd, Cd, args.steps, 0, flush)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     clocks = sampler.stop()
     if world > 1:
         torch.distributed.barrier(device_ids=[local])
     total_ms = sum(step)
-    t_max = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(t_max, op=torch.distributed.ReduceOp.MAX)
-    total_ms = float(t_max.item())
+    total_ms = max_over_ranks(torch, total_ms, world, "cuda")
     ms_step = total_ms / args.steps
-    value = world * flops / (ms_step * 1e-3) / 1e9
+    value = whole_job_gflops(flops, world, ms_step)
 
     # variants (same inputs, same accuracy), fewer steps
     var_out = {}
@@ -294,7 +318,7 @@ def run_loops(args):
     # dominant kernel of the step and its roofline (FP64 here is bound by the FP64 pipe)
     csr_ms, bcsr_ms = statistics.mean(csr), statistics.mean(bcsr)
     if csr_ms >= bcsr_ms:
-        dom, dom_ms, dom_nnz = "csr_spmm_vec<TrF64,32,1,8>", csr_ms, info["nnz_csr"]
+        dom, dom_ms, dom_nnz = "csr_spmm_vec<TrF64,32,1,1>", csr_ms, info["nnz_csr"]
         tkey = "csr_spmm_f64_n64"
     else:
         dom, dom_ms, dom_nnz = "bcsr_dmma<4>", bcsr_ms, info["nnz_bcsr"]
@@ -356,10 +380,156 @@ def run_loops(args):
     print(json.dumps(line), flush=True)
 
 
+def make_flush(torch):
+    flush_w = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    flush_r = torch.ones(64 << 20, dtype=torch.float32, device="cuda")
+    flush_out = torch.empty((), dtype=torch.float32, device="cuda")
+
+    def flush():
+        flush_w.zero_()
+        torch.sum(flush_r, dim=0, out=flush_out)
+    return flush
+
+
+def part_bytes(info, N, e, c, part):
+    """Algorithmic bytes of one part of a plan: its rows' pointers, its stored entries
+    (column + value), B once and its rows of C."""
+    if part == "csr":
+        rows, nnz = info["n_csr_rows"], info["nnz_csr"]
+    else:
+        rows, nnz = info["n_row_blocks"] * info["block_rows"], info["nnz_bcsr"]
+    return rows * 8 + nnz * (4 + e) + info["n_cols"] * N * e + rows * N * c
+
+
+def time_fn(torch, fn, steps, warmup, flush):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    stream = torch.cuda.current_stream()
+    for k in range(steps):
+        flush()
+        ev[k][0].record(stream)
+        fn()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def run_other(args):
+    """The other four workloads, one JSON line each (same keys; not the default bench line)."""
+    import torch
+
+    import paper_2511_08158_gb300 as lp
+
+    torch.cuda.set_device(0)
+    lp.build()
+    lp.load()
+    flush = make_flush(torch)
+    hbm_peak, hbm_src = peaks()
+    wl = args.workload
+    out = {"metric": METRIC, "unit": "GFLOP/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "data": "synthetic (seeded)"}
+    if wl == "batched":
+        fmt = args.dtype or "f32"
+        mats = W.batched_mix(count=512, seed=5)
+        As = [A for A, _ in mats]
+        Ns = [N for _, N in mats]
+        flops = sum(2.0 * A.nnz * N for A, N in mats)
+        e = 4 if fmt == "f32" else 2
+        nbytes = sum((A.n_rows + 1) * 8 + A.nnz * (4 + e) + A.n_cols * N * e + A.n_rows * N * 4 for A, N in mats)
+        dt = torch.float32 if fmt == "f32" else torch.bfloat16
+        Bs = [torch.randn((A.n_cols, N), device="cuda").to(dt) for A, N in mats]
+        Cs = [torch.empty((A.n_rows, N), device="cuda") for A, N in mats]
+        res = {}
+        for name, tau in (("autotuned", -1.0), ("csr_only", math.inf), ("hybrid_tau2", 2.0)):
+            t0 = time.perf_counter()
+            bp = lp.BatchedPlan(As, Ns, fmt, tau=tau)
+            build_s = time.perf_counter() - t0
+            st = time_fn(torch, lambda: bp.spmm(Bs, Cs), args.steps, args.warmup, flush)
+            ms = statistics.mean(st)
+            res[name] = {"gflops": flops / (ms * 1e-3) / 1e9, "ms_per_step": ms, "plan_build_s": build_s,
+                         "hbm_gbs": nbytes / (ms * 1e-3) / 1e9, **bp.info()}
+            bp.destroy()
+        best = res["autotuned"]
+        out.update(value=best["gflops"], ms_per_step=best["ms_per_step"], dtype=fmt,
+                   config={"workload": f"batched 512 matrices (1,000-65,536 rows, uniform/banded/16x16 blocks), "
+                                       f"N in {{16,32,64,128}}, {fmt}", "nnz": int(sum(A.nnz for A in As)),
+                           "l2": "flushed before every timed step"},
+                   roofline={"bound": "hbm", "kernel": "batched_persistent", "achieved": best["hbm_gbs"],
+                             "peak": hbm_peak, "unit": "GB/s", "frac": best["hbm_gbs"] / hbm_peak,
+                             "traffic": None, "peak_source": hbm_src},
+                   variants=res, gpu_launches=args.steps)
+        print(json.dumps(out), flush=True)
+        return
+    if wl == "rmat":
+        fmt = args.dtype or "f16"
+        A, B = W.rmat_graph(scale=20, samples_per_node=8, seed=3, N=128)
+        N, e, c = 128, 2, 4
+        X = torch.as_tensor(B, dtype=torch.float32).cuda()
+        Bd, sc = lp.cast_scaled(X, fmt)
+        desc = f"R-MAT 2^20 (a=0.57,b=0.19,c=0.19), avg degree 16, N=128, {fmt} with per-column scaling"
+    elif wl == "uniform":
+        fmt = "f32"
+        A, B = W.uniform_rows(2000, 10, 32, seed=1)
+        N, e, c = 32, 4, 4
+        Bd, sc = torch.as_tensor(B, dtype=torch.float32).cuda(), None
+        desc = "uniform 2,000 x 2,000, 10 nnz/row, N=32, f32"
+    else:  # gcn: forward
+        fmt = "f32"
+        A, X, dY = W.gcn_graph(scale=18, samples_per_node=16, seed=4, N=256)
+        A = W.CSR(A.n_rows, A.n_cols, A.row_ptr, A.col_idx, A.vals.astype(np.float32))
+        N, e, c = 256, 4, 4
+        Bd, sc = torch.as_tensor(X, dtype=torch.float32).cuda(), None
+        desc = "GCN layer: R-MAT 2^18 + I, D^-1/2 (A+I) D^-1/2, N=256, f32 (forward, and backward below)"
+    flops = 2.0 * A.nnz * N
+    Cd = torch.empty((A.n_rows, N), dtype=torch.float32, device="cuda")
+    res = {}
+    plans = {}
+    for name, tau in (("autotuned", -1.0), ("csr_only", math.inf), ("hybrid_tau2", 2.0), ("bcsr_only", 0.0)):
+        p = lp.Plan(A, N, fmt, tau=tau, want_backward=(wl == "gcn" and name == "autotuned"))
+        plans[name] = p
+        st = time_fn(torch, lambda: p.spmm(Bd, Cd, col_scale=sc), args.steps, args.warmup, flush)
+        inf = p.info()
+        ms = statistics.mean(st)
+        res[name] = {"tau": inf["tau"], "gflops": flops / (ms * 1e-3) / 1e9, "ms_per_step": ms,
+                     "bcsr_row_blocks": inf["n_row_blocks"], "nnz_bcsr": inf["nnz_bcsr"]}
+    p = plans["autotuned"]
+    inf = p.info()
+    step, csr, bcsr = time_plan(torch, p, Bd, Cd, args.steps, args.warmup, flush) if sc is None else (
+        None, None, None)
+    if step is None:
+        step = time_fn(torch, lambda: p.spmm(Bd, Cd, col_scale=sc), args.steps, args.warmup, flush)
+        csr, bcsr = step, [0.0]
+    ms = statistics.mean(step)
+    csr_ms, bcsr_ms = statistics.mean(csr), statistics.mean(bcsr)
+    part = "csr" if csr_ms >= bcsr_ms else "bcsr"
+    pb = part_bytes(inf, N, e, c, part)
+    ach = pb / (max(csr_ms, bcsr_ms) * 1e-3) / 1e9
+    alg = (A.n_rows + 1) * 8 + A.nnz * (4 + e) + A.n_cols * N * e + A.n_rows * N * c
+    out.update(value=flops / (ms * 1e-3) / 1e9, ms_per_step=ms, dtype=fmt,
+               config={"workload": desc, "nnz": int(A.nnz), "N": N, "l2": "flushed before every timed step"},
+               roofline={"bound": "hbm", "kernel": f"{part} part", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": ach / hbm_peak, "traffic": None, "peak_source": hbm_src},
+               hbm={"alg_bytes_per_step": alg, "achieved_gbs": alg / (ms * 1e-3) / 1e9,
+                    "frac_of_measured": alg / (ms * 1e-3) / 1e9 / hbm_peak},
+               variants=res, part_ms={"csr": csr_ms, "bcsr": bcsr_ms},
+               gpu_launches=launches_per_step(inf) * args.steps)
+    if wl == "gcn":
+        dYd = torch.as_tensor(dY, dtype=torch.float32).cuda()
+        st = time_fn(torch, lambda: p.backward(dYd, Bd), args.steps, args.warmup, flush)
+        bms = statistics.mean(st)
+        out["backward"] = {"ms_per_step": bms, "gflops": 2 * flops / (bms * 1e-3) / 1e9,
+                           "what": "dX = A^T dY (transposed hybrid plan) + dvals = SDDMM(dY, X^T)"}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload != "laplacian":
+        run_other(args)
     else:
         run_loops(args)
 

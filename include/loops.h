@@ -226,6 +226,30 @@ loops_status loops_plan_set_timing_events(loops_plan_t plan, void* const* events
  * LOOPS_ERR_TIMEOUT when a bounded device-side wait gave up in an earlier launch. */
 loops_status loops_plan_check(loops_plan_t plan, loops_stream_t stream);
 
+/* Batched plan (the benchmark spec batching pattern; the paper runs one matrix at a time): `count`
+ * matrices As[m] (host CSR, as for loops_plan) with their own N = Ns[m], in one dtype
+ * (LOOPS_F32, LOOPS_F16 or LOOPS_BF16). Each N must be a multiple of the elements of a 16-byte
+ * vector (4 for F32, 8 otherwise) and at most 128 (F32: 128, 16-bit: 128). opts->tau < 0 autotunes the
+ * split threshold (and, for F32 with block_rows 0, the tile height) by timing the whole batch
+ * on `stream` (synchronises it). One persistent launch serves every matrix; it is captured in
+ * a CUDA graph by the first loops_spmm_batched call and replayed by later ones. */
+loops_status loops_plan_batched(const loops_csr* As, const int64_t* Ns, int32_t count, loops_dtype dtype,
+                                const loops_plan_opts* opts, loops_stream_t stream, loops_plan_t* out);
+
+/* C_m = A_m . B_m for every matrix of a batched plan. Bs, Cs, ldbs, ldcs: HOST arrays of
+ * `count` entries holding device pointers / leading dimensions (rows 16-byte aligned);
+ * col_scales: NULL, or a host array of `count` device f32[N_m] pointers (16-bit dtypes; NULL
+ * entries mean no scaling). When the pointers differ from the previous call the descriptor
+ * table is re-uploaded first (waiting, on the host, for the previous upload to have been
+ * read). Stream-ordered otherwise. */
+loops_status loops_spmm_batched(loops_plan_t plan, const void* const* Bs, const int64_t* ldbs,
+                                void* const* Cs, const int64_t* ldcs, const float* const* col_scales,
+                                loops_stream_t stream);
+
+/* Counts of a batched plan: matrices, tasks of the persistent launch, tuned tau and B_r. */
+loops_status loops_plan_batched_info(loops_plan_t plan, int32_t* count, int64_t* n_tasks, double* tau,
+                                     int32_t* block_rows);
+
 /* ---------------------------------------------------------------------------------------- */
 /* Allocation-free CSR SpMM. The paper has no counterpart: it serves callers that must not
  * allocate device memory at the point where they multiply -- code being recorded into a CUDA

@@ -32,7 +32,7 @@ EXPORTED = ["loops_version", "loops_status_str", "loops_last_error", "loops_plan
             "loops_plan_info_get", "loops_plan_export", "loops_plan_update_values", "loops_spmm",
             "loops_spmm_scaled", "loops_spmm_host", "loops_spmm_backward", "loops_cast_scaled",
             "loops_plan_check", "loops_plan_set_timing_events", "loops_plan_set_values",
-            "loops_csr_spmm_noalloc"]
+            "loops_csr_spmm_noalloc", "loops_plan_batched", "loops_spmm_batched", "loops_plan_batched_info"]
 
 
 class LoopsError(RuntimeError):
@@ -113,6 +113,12 @@ def load():
     L.loops_plan_check.argtypes = [vp, vp]
     L.loops_plan_set_values.argtypes = [vp, vp, ctypes.c_int, vp]
     L.loops_csr_spmm_noalloc.argtypes = [i64, i64, i64, vp, vp, vp, ctypes.c_int, vp, i64, i64, vp, i64, vp]
+    L.loops_plan_batched.argtypes = [ctypes.POINTER(_Csr), ctypes.POINTER(ctypes.c_int64), ctypes.c_int32, ctypes.c_int,
+                                     ctypes.POINTER(_Opts), vp, ctypes.POINTER(vp)]
+    L.loops_spmm_batched.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(vp),
+                                     ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(vp), vp]
+    L.loops_plan_batched_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64),
+                                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)]
     L.loops_plan_set_timing_events.argtypes = [vp, ctypes.POINTER(ctypes.c_void_p)]
     for name in EXPORTED:
         fn = getattr(L, name)
@@ -325,6 +331,66 @@ class Plan:
             dB.stride(0) if dB is not None else self.N, dv.data_ptr() if dv is not None else 0,
             _stream_handle(stream)))
         return dB, dv
+
+
+class BatchedPlan:
+    """Many matrices with their own N behind one persistent, graph-captured launch
+    (``loops_plan_batched`` / ``loops_spmm_batched``)."""
+
+    def __init__(self, As, Ns, dtype: str = "f32", tau: float = -1.0, block_rows: int = 0, split_len: int = 0,
+                 stream=None):
+        L = load()
+        self._L = L
+        self.dtype = _DT[dtype]
+        self.count = len(As)
+        self.Ns = [int(n) for n in Ns]
+        self.shapes = [(int(A.n_rows), int(A.n_cols)) for A in As]
+        structs, self._keep = [], []
+        for A in As:
+            cs, keep = _csr_struct(A)
+            structs.append(cs)
+            self._keep.append(keep)
+        arr = (_Csr * max(1, self.count))(*structs)
+        ns = (ctypes.c_int64 * max(1, self.count))(*self.Ns)
+        o = _opts(tau, block_rows, False, 0, False, split_len)
+        h = ctypes.c_void_p()
+        _check(L.loops_plan_batched(arr, ns, self.count, self.dtype, ctypes.byref(o), _stream_handle(stream),
+                                    ctypes.byref(h)))
+        self._keep = None  # the plan does not keep the host CSR arrays
+        self._h = h
+
+    def info(self) -> dict:
+        c, t, tau, br = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_double(), ctypes.c_int32()
+        _check(self._L.loops_plan_batched_info(self._h, ctypes.byref(c), ctypes.byref(t), ctypes.byref(tau),
+                                               ctypes.byref(br)))
+        return {"count": c.value, "n_tasks": t.value, "tau": tau.value, "block_rows": br.value}
+
+    def spmm(self, Bs, Cs=None, col_scales=None, stream=None):
+        torch = _torch()
+        if Cs is None:
+            Cs = [torch.empty((r, n), dtype=getattr(torch, _TORCH_OUT[self.dtype]), device=B.device)
+                  for (r, _), n, B in zip(self.shapes, self.Ns, Bs)]
+        n = max(1, self.count)
+        bp = (ctypes.c_void_p * n)(*[B.data_ptr() for B in Bs])
+        cp = (ctypes.c_void_p * n)(*[C.data_ptr() for C in Cs])
+        lb = (ctypes.c_int64 * n)(*[B.stride(0) for B in Bs])
+        lc = (ctypes.c_int64 * n)(*[C.stride(0) for C in Cs])
+        sp = None
+        if col_scales is not None:
+            sp = (ctypes.c_void_p * n)(*[0 if s is None else s.data_ptr() for s in col_scales])
+        _check(self._L.loops_spmm_batched(self._h, bp, lb, cp, lc, sp, _stream_handle(stream)))
+        return Cs
+
+    def destroy(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._L.loops_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
 
 
 def cast_scaled(X, dtype: str = "f16", stream=None):

@@ -19,7 +19,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libloops.so")
 INCLUDE = os.path.join(ROOT, "include")
 
-SOURCES = ["capi.cpp", "partition.cpp", "layout.cpp", "csr_kernels.cu", "bcsr_kernels.cu", "csr_noalloc.cu"]
+SOURCES = ["capi.cpp", "partition.cpp", "layout.cpp", "csr_kernels.cu", "bcsr_kernels.cu", "csr_noalloc.cu",
+           "batched.cu", "batched_plan.cpp"]
 HEADERS = [os.path.join(CSRC, "loops_internal.h"), os.path.join(CSRC, "device_common.cuh"),
            os.path.join(INCLUDE, "loops.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

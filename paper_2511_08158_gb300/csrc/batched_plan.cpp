@@ -1,0 +1,409 @@
+// Batched plans: many sparse matrices of uneven size and N behind one plan, executed by one
+// persistent kernel launch that is captured in a CUDA graph on the first call and replayed.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "loops_internal.h"
+
+namespace loops {
+
+struct BatchState {
+  std::vector<loops_plan_s*> subs;
+  int32_t count = 0;
+  loops_dtype dtype = LOOPS_F32;
+  int32_t br = 16;
+  double tau = 2.0;
+  BatchDesc* h_desc = nullptr;        // pinned host copy of the descriptors
+  BatchDesc* d_desc = nullptr;
+  BatchTask* d_tasks = nullptr;
+  int2* d_splits = nullptr;
+  int64_t n_tasks = 0, n_splits = 0;
+  int grid = 0, smem_per_warp = 0;
+  cudaStream_t cap = nullptr;         // capture stream
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t ev_copied = nullptr;    // the last descriptor upload has read h_desc
+  bool copied_once = false;
+  int64_t device_bytes = 0;
+  int64_t total_nnz = 0, total_rows = 0;
+};
+
+void destroy_batch(BatchState* b) {
+  if (!b) return;
+  for (auto* s : b->subs) destroy_plan(s);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->h_desc) cudaFreeHost(b->h_desc);
+  void* ptrs[] = {b->d_desc, b->d_tasks, b->d_splits};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  if (b->ev_copied) cudaEventDestroy(b->ev_copied);
+  delete b;
+}
+
+namespace {
+
+int elems_per_16b(loops_dtype d) { return d == LOOPS_F32 ? 4 : 8; }
+
+// Build the sub-plans, task list and descriptor tables for a fixed tau.
+loops_status build_batch(const loops_csr* As, const int64_t* Ns, int32_t count, loops_dtype dtype,
+                         const loops_plan_opts& o, int32_t br, double tau, BatchState** out) {
+  *out = nullptr;
+  BatchState* b = new (std::nothrow) BatchState();
+  if (!b) { set_error("host allocation failed"); return LOOPS_ERR_OOM; }
+  b->count = count;
+  b->dtype = dtype;
+  b->br = br;
+  b->tau = tau;
+  loops_status st = LOOPS_OK;
+  const int VE = elems_per_16b(dtype);
+  std::vector<BatchTask> tasks;
+  std::vector<double> cost;
+  std::vector<int2> splits;
+  int64_t max_N = 8;
+  std::vector<double> vals;
+  for (int32_t m = 0; m < count && !st; ++m) {
+    const int64_t N = Ns[m];
+    if (N <= 0 || N % VE != 0 || N > (dtype == LOOPS_F32 ? 32 * VE : 128)) {
+      set_error("batched SpMM needs N a positive multiple of " + std::to_string(VE) + " and at most " +
+                std::to_string(dtype == LOOPS_F32 ? 32 * VE : 128) + " (matrix " + std::to_string(m) + ")");
+      st = LOOPS_ERR_UNSUPPORTED;
+      break;
+    }
+    max_N = std::max(max_N, N);
+    if ((st = validate_csr(&As[m]))) break;
+    read_vals_f64(&As[m], vals);
+    loops_plan_s* p = nullptr;
+    if ((st = make_plan(&As[m], vals.data(), N, dtype, o, br, tau, true, &p))) break;
+    b->subs.push_back(p);
+    b->total_nnz += As[m].nnz;
+    b->total_rows += As[m].n_rows;
+    const int G = (int)(N / VE);
+    const int per_round = 32 / G;
+    // CSR items: consecutive items (similar length, longest first) up to ~1024 entries
+    const CsrDev& c = p->dev.csr;
+    for (int64_t i = 0; i < c.n_items;) {
+      int64_t j = i, nnz = 0;
+      while (j < c.n_items && (j - i) < (int64_t)32 * per_round && (nnz < 1024 || (j - i) < per_round)) {
+        nnz += c.h_item_ptr[(size_t)j + 1] - c.h_item_ptr[(size_t)j];
+        ++j;
+      }
+      tasks.push_back({m, 0, i, (int32_t)(j - i), 0});
+      cost.push_back((double)(nnz + (j - i)) * (double)N);
+      i = j;
+    }
+    // BCSR blocks (positions in the block order, most tiles first)
+    const Canon& cn = p->canon;
+    std::vector<int64_t> tiles_in_order;
+    for (int64_t q = 0; q < p->dev.bcsr.n_rb; ++q) {
+      // the order array sorts blocks by tile count, descending and stable
+      tiles_in_order.push_back(0);
+    }
+    if (p->dev.bcsr.n_rb) {
+      std::vector<int32_t> order((size_t)p->dev.bcsr.n_rb);
+      for (int64_t q = 0; q < p->dev.bcsr.n_rb; ++q) order[(size_t)q] = (int32_t)q;
+      std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
+        return cn.rb_ptr[(size_t)x + 1] - cn.rb_ptr[(size_t)x] > cn.rb_ptr[(size_t)y + 1] - cn.rb_ptr[(size_t)y];
+      });
+      for (int64_t q = 0; q < p->dev.bcsr.n_rb; ++q)
+        tiles_in_order[(size_t)q] = cn.rb_ptr[(size_t)order[(size_t)q] + 1] - cn.rb_ptr[(size_t)order[(size_t)q]];
+    }
+    if (dtype == LOOPS_F32) {
+      for (int64_t q = 0; q < p->dev.bcsr.n_rb; q += per_round) {
+        const int32_t cnt = (int32_t)std::min<int64_t>(per_round, p->dev.bcsr.n_rb - q);
+        tasks.push_back({m, 1, q, cnt, 0});
+        cost.push_back((double)tiles_in_order[(size_t)q] * br * (double)N);
+      }
+    } else {
+      for (int64_t q = 0; q < p->dev.bcsr.n_rb; ++q) {
+        tasks.push_back({m, 2, q, 1, 0});
+        cost.push_back((double)tiles_in_order[(size_t)q] * br * (double)N);
+      }
+    }
+    for (int64_t sidx = 0; sidx < c.n_split; ++sidx) splits.push_back(make_int2(m, (int)sidx));
+  }
+  if (st) { destroy_batch(b); return st; }
+  // longest tasks first; warps take tasks round-robin
+  std::vector<int64_t> idx(tasks.size());
+  for (size_t i = 0; i < idx.size(); ++i) idx[i] = (int64_t)i;
+  std::stable_sort(idx.begin(), idx.end(), [&](int64_t x, int64_t y) { return cost[(size_t)x] > cost[(size_t)y]; });
+  std::vector<BatchTask> sorted(tasks.size());
+  for (size_t i = 0; i < idx.size(); ++i) sorted[i] = tasks[(size_t)idx[i]];
+  b->n_tasks = (int64_t)sorted.size();
+  b->n_splits = (int64_t)splits.size();
+  b->smem_per_warp = dtype == LOOPS_F32 ? 0 : (int)(((16 * (max_N + 8) * 2) + 127) / 128 * 128);
+  b->grid = batched_grid_blocks(dtype, br, b->smem_per_warp);
+  // descriptors (static parts now; B/C pointers per call)
+  cudaError_t e = cudaMallocHost((void**)&b->h_desc, sizeof(BatchDesc) * (size_t)std::max(count, 1));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_desc, sizeof(BatchDesc) * (size_t)std::max(count, 1));
+  if (e == cudaSuccess && b->n_tasks) e = cudaMalloc((void**)&b->d_tasks, sizeof(BatchTask) * (size_t)b->n_tasks);
+  if (e == cudaSuccess && b->n_tasks)
+    e = cudaMemcpy(b->d_tasks, sorted.data(), sizeof(BatchTask) * (size_t)b->n_tasks, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && b->n_splits) e = cudaMalloc((void**)&b->d_splits, sizeof(int2) * (size_t)b->n_splits);
+  if (e == cudaSuccess && b->n_splits)
+    e = cudaMemcpy(b->d_splits, splits.data(), sizeof(int2) * (size_t)b->n_splits, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_copied, cudaEventDisableTiming);
+  if (e != cudaSuccess) { st = cuda_status(e, "batched plan setup"); destroy_batch(b); return st; }
+  b->device_bytes = (int64_t)(sizeof(BatchDesc) * count + sizeof(BatchTask) * b->n_tasks + sizeof(int2) * b->n_splits);
+  for (int32_t m = 0; m < count; ++m) {
+    const loops_plan_s* p = b->subs[(size_t)m];
+    BatchDesc& d = b->h_desc[m];
+    std::memset(&d, 0, sizeof(d));
+    d.item_row = p->dev.csr.item_row;
+    d.item_ptr = p->dev.csr.item_ptr;
+    d.col = p->dev.csr.col;
+    d.val = p->dev.csr.val;
+    d.rb_id = p->dev.bcsr.rb_id;
+    d.rb_ptr = p->dev.bcsr.rb_ptr;
+    d.tile_col = p->dev.bcsr.tile_col;
+    d.tile_val = p->dev.bcsr.tile_val;
+    d.order = p->dev.bcsr.order;
+    d.scratch = p->dev.csr.scratch;
+    d.split_row = p->dev.csr.split_row;
+    d.split_slot_ptr = p->dev.csr.split_slot_ptr;
+    d.N = p->N;
+    d.n_rows = p->n_rows;
+    d.inv_scale = (float)(1.0 / p->scale);
+    d.G = (int32_t)(p->N / VE);
+    b->device_bytes += p->dev.device_bytes;
+  }
+  *out = b;
+  return LOOPS_OK;
+}
+
+cudaError_t run_batch(BatchState* b, cudaStream_t s) {
+  BatchLaunch L;
+  L.descs = b->d_desc;
+  L.tasks = b->d_tasks;
+  L.n_tasks = b->n_tasks;
+  L.splits = b->d_splits;
+  L.n_splits = b->n_splits;
+  L.grid = b->grid;
+  L.smem_per_warp = b->smem_per_warp;
+  return launch_batched(b->dtype, b->br, L, s);
+}
+
+// Per call: refresh the descriptors' dense pointers if they changed (one upload from the
+// pinned copy, which is not rewritten before the previous upload has read it), then replay
+// the captured graph -- one persistent launch, plus the split-row sums if any.
+loops_status spmm_batch(BatchState* b, const void* const* Bs, const int64_t* ldbs, void* const* Cs,
+                        const int64_t* ldcs, const float* const* col_scales, cudaStream_t s) {
+  bool changed = !b->copied_once;
+  for (int32_t m = 0; m < b->count && !changed; ++m) {
+    const BatchDesc& d = b->h_desc[m];
+    const float* cs = col_scales ? col_scales[m] : nullptr;
+    changed = d.B != Bs[m] || d.C != Cs[m] || d.ldb != ldbs[m] || d.ldc != ldcs[m] || d.col_scale != cs;
+  }
+  cudaError_t e = cudaSuccess;
+  if (changed) {
+    if (b->copied_once) {
+      e = cudaEventSynchronize(b->ev_copied);
+      if (e != cudaSuccess) return cuda_status(e, "wait for descriptor upload");
+    }
+    for (int32_t m = 0; m < b->count; ++m) {
+      BatchDesc& d = b->h_desc[m];
+      d.B = Bs[m];
+      d.C = Cs[m];
+      d.ldb = ldbs[m];
+      d.ldc = ldcs[m];
+      d.col_scale = col_scales ? col_scales[m] : nullptr;
+    }
+    e = cudaMemcpyAsync(b->d_desc, b->h_desc, sizeof(BatchDesc) * (size_t)b->count, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaEventRecord(b->ev_copied, s);
+    if (e != cudaSuccess) return cuda_status(e, "descriptor upload");
+    b->copied_once = true;
+  }
+  if (!b->exec) {
+    e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t e2 = run_batch(b, b->cap);
+      e = cudaStreamEndCapture(b->cap, &b->graph);
+      if (e2 != cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return cuda_status(e, "graph capture of the batched launch");
+    }
+  }
+  return cuda_status(cudaGraphLaunch(b->exec, s), "graph launch");
+}
+
+}  // namespace
+
+}  // namespace loops
+
+using namespace loops;
+
+extern "C" {
+
+loops_status loops_plan_batched(const loops_csr* As, const int64_t* Ns, int32_t count, loops_dtype dtype,
+                                const loops_plan_opts* opts, loops_stream_t stream, loops_plan_t* out) {
+  clear_error();
+  if (!out) { set_error("out is NULL"); return LOOPS_ERR_INVALID_ARG; }
+  *out = nullptr;
+  if (count < 0 || (count > 0 && (!As || !Ns))) { set_error("bad batch arrays"); return LOOPS_ERR_INVALID_ARG; }
+  if (dtype != LOOPS_F32 && dtype != LOOPS_F16 && dtype != LOOPS_BF16) {
+    set_error("batched SpMM supports F32, F16 and BF16");
+    return LOOPS_ERR_UNSUPPORTED;
+  }
+  loops_plan_opts o;
+  loops_plan_opts_default(&o);
+  if (opts) o = *opts;
+  if (std::isnan(o.tau)) { set_error("tau is NaN"); return LOOPS_ERR_INVALID_ARG; }
+  o.want_backward = 0;
+  o.contiguous_split = 0;
+  int32_t br;
+  loops_status st = resolve_block_rows(dtype, o, &br);
+  if (st) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  BatchState* best = nullptr;
+  if (o.tau >= 0.0) {
+    if ((st = build_batch(As, Ns, count, dtype, o, br, o.tau, &best))) return st;
+  } else {
+    // autotune: split threshold (and, for F32, the tile height) by timing the whole batch
+    struct Cand { double tau; int32_t br; };
+    std::vector<Cand> cands;
+    for (double t : {(double)INFINITY, 4.0, 2.0, 1.25, 0.0}) cands.push_back({t, br});
+    if (dtype == LOOPS_F32 && o.block_rows == 0) cands.push_back({2.0, br == 16 ? 8 : 16});
+    float best_ms = INFINITY;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    std::vector<void*> bufs;
+    std::vector<const void*> Bs((size_t)count);
+    std::vector<void*> Cs((size_t)count);
+    std::vector<int64_t> ld((size_t)count);
+    const int64_t eb = dtype == LOOPS_F32 ? 4 : 2;
+    cudaError_t e = cudaSuccess;
+    for (int32_t m = 0; m < count && e == cudaSuccess; ++m) {
+      void *pb = nullptr, *pc = nullptr;
+      e = cudaMalloc(&pb, (size_t)std::max<int64_t>(As[m].n_cols * Ns[m] * eb, 16));
+      if (e == cudaSuccess) e = cudaMalloc(&pc, (size_t)std::max<int64_t>(As[m].n_rows * Ns[m] * 4, 16));
+      if (e == cudaSuccess) e = cudaMemsetAsync(pb, 0x3C, (size_t)(As[m].n_cols * Ns[m] * eb), s);
+      bufs.push_back(pb);
+      bufs.push_back(pc);
+      Bs[(size_t)m] = pb;
+      Cs[(size_t)m] = pc;
+      ld[(size_t)m] = Ns[m];
+    }
+    st = cuda_status(e, "autotune buffers");
+    double best_tau = 2.0;
+    for (const Cand& c : cands) {
+      if (st) break;
+      loops_plan_opts oc = o;
+      oc.block_rows = c.br;
+      BatchState* b = nullptr;
+      if ((st = build_batch(As, Ns, count, dtype, oc, c.br, c.tau, &b))) break;
+      float ms = INFINITY;
+      for (int it = 0; it < 5 && !st; ++it) {
+        if (it >= 2) cudaEventRecord(e0, s);
+        st = spmm_batch(b, Bs.data(), ld.data(), Cs.data(), ld.data(), nullptr, s);
+        if (it >= 2) {
+          cudaEventRecord(e1, s);
+          if (!st) st = cuda_status(cudaEventSynchronize(e1), "autotune timing");
+          float t = 0.f;
+          cudaEventElapsedTime(&t, e0, e1);
+          ms = std::min(ms, t);
+        }
+      }
+      if (!st && ms < best_ms) {
+        best_ms = ms;
+        best_tau = c.tau;
+        if (best) destroy_batch(best);
+        best = b;
+        br = c.br;
+      } else {
+        destroy_batch(b);
+      }
+    }
+    cudaStreamSynchronize(s);
+    for (void* q : bufs)
+      if (q) cudaFree(q);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st) { if (best) destroy_batch(best); return st; }
+    (void)best_tau;
+    // a plan built during tuning has captured dummy pointers: drop its graph state so the
+    // first real call uploads the caller's descriptors
+    best->copied_once = false;
+  }
+  loops_plan_s* p = new (std::nothrow) loops_plan_s();
+  if (!p) { destroy_batch(best); set_error("host allocation failed"); return LOOPS_ERR_OOM; }
+  p->magic = kPlanMagic;
+  p->dtype = dtype;
+  p->n_rows = best->total_rows;
+  p->n_cols = 0;
+  p->nnz = best->total_nnz;
+  p->N = 0;
+  p->br = best->br;
+  p->kpad = k_pad_for(dtype);
+  p->tau = best->tau;
+  p->scale = 1.0;
+  p->split_len = 0;
+  p->opts = o;
+  p->transposed = nullptr;
+  p->d_error = nullptr;
+  p->side = nullptr;
+  p->ev_fork = p->ev_join = nullptr;
+  p->stage_B = p->stage_C = nullptr;
+  p->stage_B_bytes = p->stage_C_bytes = 0;
+  p->n_subnormal = 0;
+  p->nnz_bcsr = 0;
+  p->timing = false;
+  for (auto& ev : p->tev) ev = nullptr;
+  p->batch = best;
+  p->other_bytes = best->device_bytes;
+  for (auto* sp : best->subs) {
+    p->nnz_bcsr += sp->nnz_bcsr;
+    p->n_subnormal += sp->n_subnormal;
+  }
+  *out = p;
+  return LOOPS_OK;
+}
+
+loops_status loops_spmm_batched(loops_plan_t p, const void* const* Bs, const int64_t* ldbs, void* const* Cs,
+                                const int64_t* ldcs, const float* const* col_scales, loops_stream_t stream) {
+  clear_error();
+  loops_status st = check_plan(p);
+  if (st) return st;
+  if (!p->batch) { set_error("not a batched plan"); return LOOPS_ERR_STATE; }
+  BatchState* b = p->batch;
+  if (b->count && (!Bs || !Cs || !ldbs || !ldcs)) { set_error("NULL batch array"); return LOOPS_ERR_INVALID_ARG; }
+  for (int32_t m = 0; m < b->count; ++m) {
+    const loops_plan_s* sp = b->subs[(size_t)m];
+    const int64_t N = sp->N;
+    const int64_t eb = b->dtype == LOOPS_F32 ? 4 : 2;
+    if (ldbs[m] < N || ldcs[m] < N || (!Bs[m] && sp->n_cols > 0) || (!Cs[m] && sp->n_rows > 0)) {
+      set_error("bad dense operand of matrix " + std::to_string(m));
+      return LOOPS_ERR_INVALID_ARG;
+    }
+    if (((uintptr_t)Bs[m] % 16) || ((uintptr_t)Cs[m] % 16) || ((ldbs[m] * eb) % 16) || ((ldcs[m] * 4) % 16)) {
+      set_error("batched SpMM needs 16-byte aligned rows of B and C (matrix " + std::to_string(m) + ")");
+      return LOOPS_ERR_UNSUPPORTED;
+    }
+    if (col_scales && col_scales[m] && b->dtype == LOOPS_F32) {
+      set_error("col_scale is only defined for the 16-bit dtypes");
+      return LOOPS_ERR_INVALID_ARG;
+    }
+  }
+  return spmm_batch(b, Bs, ldbs, Cs, ldcs, col_scales, (cudaStream_t)stream);
+}
+
+loops_status loops_plan_batched_info(loops_plan_t p, int32_t* count, int64_t* n_tasks, double* tau,
+                                     int32_t* block_rows) {
+  clear_error();
+  loops_status st = check_plan(p);
+  if (st) return st;
+  if (!p->batch) { set_error("not a batched plan"); return LOOPS_ERR_STATE; }
+  if (count) *count = p->batch->count;
+  if (n_tasks) *n_tasks = p->batch->n_tasks;
+  if (tau) *tau = p->batch->tau;
+  if (block_rows) *block_rows = p->batch->br;
+  return LOOPS_OK;
+}
+
+}  // extern "C"

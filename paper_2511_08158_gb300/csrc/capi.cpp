@@ -18,7 +18,7 @@ loops_status export_part(const loops_plan_s* p, loops_partition* out);
 loops_status autotune_tau(const loops_csr* A, const double* vals, int64_t N, loops_dtype dtype,
                           int32_t br, int32_t split_len, cudaStream_t s, double* tau_out);
 
-static loops_status cuda_status(cudaError_t e, const char* what) {
+loops_status cuda_status(cudaError_t e, const char* what) {
   if (e == cudaSuccess) return LOOPS_OK;
   set_error(std::string(what) + ": " + cudaGetErrorString(e));
   return e == cudaErrorMemoryAllocation ? LOOPS_ERR_OOM : LOOPS_ERR_CUDA;
@@ -28,9 +28,20 @@ static bool valid_dtype(loops_dtype d) {
   return d == LOOPS_F64 || d == LOOPS_F32 || d == LOOPS_F16 || d == LOOPS_BF16;
 }
 
-static loops_status check_plan(loops_plan_t p) {
+loops_status check_plan(loops_plan_t p) {
   if (!p || p->magic != kPlanMagic) {
     set_error("invalid or destroyed plan handle");
+    return LOOPS_ERR_STATE;
+  }
+  return LOOPS_OK;
+}
+
+// A single-matrix plan (not batched).
+static loops_status check_single(loops_plan_t p) {
+  loops_status st = check_plan(p);
+  if (st) return st;
+  if (p->batch) {
+    set_error("this call needs a single-matrix plan, not a batched one");
     return LOOPS_ERR_STATE;
   }
   return LOOPS_OK;
@@ -62,7 +73,7 @@ static void fill_partition(const Canon& c, loops_partition* out) {
   out->tile_val = (double*)dup(c.tile_val.data(), c.tile_val.size() * 8);
 }
 
-static loops_status resolve_block_rows(loops_dtype dtype, const loops_plan_opts& o, int32_t* br) {
+loops_status resolve_block_rows(loops_dtype dtype, const loops_plan_opts& o, int32_t* br) {
   int32_t b = o.block_rows ? o.block_rows : default_block_rows(dtype);
   const bool ok = (dtype == LOOPS_F64 && b == 8) || ((dtype == LOOPS_F16 || dtype == LOOPS_BF16) && b == 16) ||
                   (dtype == LOOPS_F32 && (b == 8 || b == 16));
@@ -74,8 +85,9 @@ static loops_status resolve_block_rows(loops_dtype dtype, const loops_plan_opts&
   return LOOPS_OK;
 }
 
-static void destroy_plan(loops_plan_s* p) {
+void destroy_plan(loops_plan_s* p) {
   if (!p) return;
+  if (p->batch) destroy_batch(p->batch);
   if (p->transposed) destroy_plan(p->transposed);
   free_part(p->dev);
   free_value_maps(p->vmap);
@@ -91,8 +103,8 @@ static void destroy_plan(loops_plan_s* p) {
 }
 
 // Builds a single (non-transposed) plan from validated input and f64 values.
-static loops_status make_plan(const loops_csr* A, const double* vals, int64_t N, loops_dtype dtype,
-                              const loops_plan_opts& o, int32_t br, double tau, loops_plan_s** out) {
+loops_status make_plan(const loops_csr* A, const double* vals, int64_t N, loops_dtype dtype,
+                       const loops_plan_opts& o, int32_t br, double tau, bool light, loops_plan_s** out) {
   *out = nullptr;
   loops_plan_s* p = new (std::nothrow) loops_plan_s();
   if (!p) { set_error("host allocation failed"); return LOOPS_ERR_OOM; }
@@ -115,6 +127,8 @@ static loops_status make_plan(const loops_csr* A, const double* vals, int64_t N,
   p->stage_B_bytes = p->stage_C_bytes = 0;
   p->timing = false;
   for (auto& ev : p->tev) ev = nullptr;
+  p->batch = nullptr;
+  p->other_bytes = 0;
   loops_status st = build_canon(A, vals, dtype, br, tau, o.contiguous_split != 0, o.r_boundary, p->canon);
   if (st) { destroy_plan(p); return st; }
   p->scale = p->canon.scale;
@@ -127,13 +141,17 @@ static loops_status make_plan(const loops_csr* A, const double* vals, int64_t N,
   p->nnz_bcsr = 0;
   for (uint8_t k : p->canon.src_kind) p->nnz_bcsr += k;
   if ((st = upload_part(p, N))) { destroy_plan(p); return st; }
+  if (light) {
+    *out = p;
+    return LOOPS_OK;
+  }
   cudaError_t e = cudaMalloc((void**)&p->d_error, sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMemset(p->d_error, 0, sizeof(int32_t));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming);
   if (e != cudaSuccess) { st = cuda_status(e, "plan setup"); destroy_plan(p); return st; }
-  p->dev.device_bytes += sizeof(int32_t);
+  p->other_bytes += sizeof(int32_t);
   *out = p;
   return LOOPS_OK;
 }
@@ -171,7 +189,7 @@ static loops_status build_sddmm(loops_plan_s* p, const loops_csr* A) {
     if (!bytes) { *dst = nullptr; return LOOPS_OK; }
     cudaError_t e = cudaMalloc(dst, bytes);
     if (e == cudaSuccess) e = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) p->dev.device_bytes += (int64_t)bytes;
+    if (e == cudaSuccess) p->other_bytes += (int64_t)bytes;
     return cuda_status(e, "upload SDDMM pattern");
   };
   loops_status st;
@@ -266,7 +284,7 @@ loops_status autotune_tau(const loops_csr* A, const double* vals, int64_t N, loo
   for (double tau : cands) {
     if (st) break;
     loops_plan_s* p = nullptr;
-    if ((st = make_plan(A, vals, N, dtype, o, br, tau, &p))) break;
+    if ((st = make_plan(A, vals, N, dtype, o, br, tau, false, &p))) break;
     const int64_t key = (int64_t)p->canon.rb_ids.size();
     if (std::find(seen.begin(), seen.end(), key) != seen.end()) { destroy_plan(p); continue; }
     seen.push_back(key);
@@ -376,7 +394,7 @@ loops_status loops_plan(const loops_csr* A, int64_t N, loops_dtype dtype, const 
     if ((st = autotune_tau(A, vals.data(), N, dtype, br, o.split_len, (cudaStream_t)stream, &tau))) return st;
   }
   loops_plan_s* p = nullptr;
-  if ((st = make_plan(A, vals.data(), N, dtype, o, br, tau, &p))) return st;
+  if ((st = make_plan(A, vals.data(), N, dtype, o, br, tau, false, &p))) return st;
   if (o.want_backward) {
     std::vector<int64_t> trp;
     std::vector<int32_t> tci;
@@ -395,7 +413,7 @@ loops_status loops_plan(const loops_csr* A, int64_t N, loops_dtype dtype, const 
     ot.want_backward = 0;
     ot.contiguous_split = 0;
     loops_plan_s* pt = nullptr;
-    if ((st = make_plan(&At, tv.data(), N, dtype, ot, br, tau, &pt))) { destroy_plan(p); return st; }
+    if ((st = make_plan(&At, tv.data(), N, dtype, ot, br, tau, false, &pt))) { destroy_plan(p); return st; }
     p->transposed = pt;
     if ((st = build_sddmm(p, A))) { destroy_plan(p); return st; }
     if ((st = upload_value_maps(p, nullptr))) { destroy_plan(p); return st; }
@@ -439,13 +457,15 @@ loops_status loops_plan_info_get(loops_plan_t p, loops_plan_info* out) {
   out->n_split_rows = p->dev.csr.n_split;
   out->n_segments = p->dev.csr.n_slots;
   out->n_subnormal_vals = p->n_subnormal;
-  out->device_bytes = p->dev.device_bytes + (p->transposed ? p->transposed->dev.device_bytes : 0);
+  out->device_bytes = p->dev.device_bytes + p->other_bytes + p->vmap.bytes;
+  if (p->transposed)
+    out->device_bytes += p->transposed->dev.device_bytes + p->transposed->other_bytes + p->transposed->vmap.bytes;
   return LOOPS_OK;
 }
 
 loops_status loops_plan_export(loops_plan_t p, loops_partition* out) {
   clear_error();
-  loops_status st = check_plan(p);
+  loops_status st = check_single(p);
   if (st) return st;
   if (!out) { set_error("out is NULL"); return LOOPS_ERR_INVALID_ARG; }
   std::memset(out, 0, sizeof(*out));
@@ -459,7 +479,7 @@ loops_status loops_plan_export(loops_plan_t p, loops_partition* out) {
 loops_status loops_plan_update_values(loops_plan_t p, const void* vals, loops_dtype vd,
                                       loops_stream_t stream) {
   clear_error();
-  loops_status st = check_plan(p);
+  loops_status st = check_single(p);
   if (st) return st;
   if (!vals && p->nnz) { set_error("vals is NULL"); return LOOPS_ERR_INVALID_ARG; }
   if (vd != LOOPS_F64 && vd != LOOPS_F32) { set_error("vals must be F64 or F32"); return LOOPS_ERR_UNSUPPORTED; }
@@ -478,10 +498,7 @@ loops_status loops_plan_update_values(loops_plan_t p, const void* vals, loops_dt
     for (size_t x = 0; x < raw_tile.size(); ++x) c.tile_val[x] = round_store(raw_tile[x], c.scale, q->dtype);
     const int64_t N = q->N;
     free_part(q->dev);
-    const int64_t extra = sizeof(int32_t);
-    loops_status s2 = upload_part(q, N);
-    q->dev.device_bytes += extra;
-    return s2;
+    return upload_part(q, N);
   };
   if ((st = refresh(p, v))) return st;
   if (p->transposed) {
@@ -494,7 +511,7 @@ loops_status loops_plan_update_values(loops_plan_t p, const void* vals, loops_dt
 
 loops_status loops_plan_set_values(loops_plan_t p, const void* vals, loops_dtype vd, loops_stream_t stream) {
   clear_error();
-  loops_status st = check_plan(p);
+  loops_status st = check_single(p);
   if (st) return st;
   if (!p->transposed) {
     set_error("plan was built without want_backward (no device value maps)");
@@ -516,7 +533,7 @@ loops_status loops_spmm(loops_plan_t p, const void* B, int64_t ldb, void* C, int
 loops_status loops_spmm_scaled(loops_plan_t p, const void* B, int64_t ldb, const float* col_scale,
                                void* C, int64_t ldc, loops_stream_t stream) {
   clear_error();
-  loops_status st = check_plan(p);
+  loops_status st = check_single(p);
   if (st) return st;
   if ((st = check_dense(B, p->n_cols, p->N, ldb, "B"))) return st;
   if ((st = check_dense(C, p->n_rows, p->N, ldc, "C"))) return st;
@@ -530,7 +547,7 @@ loops_status loops_spmm_scaled(loops_plan_t p, const void* B, int64_t ldb, const
 loops_status loops_spmm_host(loops_plan_t p, const void* B_host, int64_t ldb, void* C_host, int64_t ldc,
                              loops_stream_t stream) {
   clear_error();
-  loops_status st = check_plan(p);
+  loops_status st = check_single(p);
   if (st) return st;
   if ((st = check_dense(B_host, p->n_cols, p->N, ldb, "B"))) return st;
   if ((st = check_dense(C_host, p->n_rows, p->N, ldc, "C"))) return st;
@@ -554,12 +571,16 @@ loops_status loops_spmm_host(loops_plan_t p, const void* B_host, int64_t ldb, vo
     if (e != cudaSuccess) return cuda_status(e, "staging allocation");
     p->stage_C_bytes = need_C;
   }
-  if (need_B)
+  if (need_B && ldb == p->N)
+    e = cudaMemcpyAsync(p->stage_B, B_host, (size_t)need_B, cudaMemcpyHostToDevice, s);
+  else if (need_B)
     e = cudaMemcpy2DAsync(p->stage_B, (size_t)(p->N * eb), B_host, (size_t)(ldb * eb), (size_t)(p->N * eb),
                           (size_t)p->n_cols, cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return cuda_status(e, "host-to-device copy");
   if ((st = run_spmm(p, p->stage_B, p->N, nullptr, p->stage_C, p->N, s))) return st;
-  if (need_C)
+  if (need_C && ldc == p->N)
+    e = cudaMemcpyAsync(C_host, p->stage_C, (size_t)need_C, cudaMemcpyDeviceToHost, s);
+  else if (need_C)
     e = cudaMemcpy2DAsync(C_host, (size_t)(ldc * ec), p->stage_C, (size_t)(p->N * ec), (size_t)(p->N * ec),
                           (size_t)p->n_rows, cudaMemcpyDeviceToHost, s);
   if (e != cudaSuccess) return cuda_status(e, "device-to-host copy");
@@ -569,7 +590,7 @@ loops_status loops_spmm_host(loops_plan_t p, const void* B_host, int64_t ldb, vo
 loops_status loops_spmm_backward(loops_plan_t p, const void* dC, int64_t lddc, const void* B, int64_t ldb,
                                  void* dB, int64_t lddb, void* dvals, loops_stream_t stream) {
   clear_error();
-  loops_status st = check_plan(p);
+  loops_status st = check_single(p);
   if (st) return st;
   if (!p->transposed) {
     set_error("plan was built without want_backward");
@@ -601,7 +622,7 @@ loops_status loops_cast_scaled(const float* X, int64_t rows, int64_t cols, int64
 
 loops_status loops_plan_set_timing_events(loops_plan_t p, void* const* events) {
   clear_error();
-  loops_status st = check_plan(p);
+  loops_status st = check_single(p);
   if (st) return st;
   if (!events) {
     p->timing = false;
@@ -618,7 +639,7 @@ loops_status loops_plan_set_timing_events(loops_plan_t p, void* const* events) {
 
 loops_status loops_plan_check(loops_plan_t p, loops_stream_t stream) {
   clear_error();
-  loops_status st = check_plan(p);
+  loops_status st = check_single(p);
   if (st) return st;
   int32_t h = 0;
   cudaStream_t s = (cudaStream_t)stream;

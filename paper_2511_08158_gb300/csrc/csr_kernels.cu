@@ -8,6 +8,8 @@
 // in flight before their FMAs. Accumulation is in f64 for F64 and in f32 otherwise. Every
 // output row has one writer; rows split in segments write partials that a second kernel
 // sums in segment order, so the result does not depend on scheduling.
+#include <type_traits>
+
 #include "device_common.cuh"
 #include "loops_internal.h"
 
@@ -86,21 +88,18 @@ __global__ void __launch_bounds__(256) csr_spmm_vec(CsrKArgs a) {
       c = __ldg(a.col + k);
       v = Tr::to_acc(vals[k]);
     }
-    const int cnt = (int)(end - k0 < (int64_t)G ? end - k0 : (int64_t)G);
-    for (int j0 = 0; j0 < cnt; j0 += U) {
+    const int cnt = (int)(end - k0 < (int64_t)G ? end - k0 : (int64_t)G);  // uniform in the group
+    int j0 = 0;
+    for (; j0 + U <= cnt; j0 += U) {  // full batches: U loads in flight, then U FMAs each
       uint4 bv[U][VPL];
       TAcc av[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const int j = j0 + u;
-        const int cj = __shfl_sync(gmask, c, j & (G - 1), G);
-        av[u] = __shfl_sync(gmask, v, j & (G - 1), G);
-        const bool ok = j < cnt;
-        if (!ok) av[u] = TAcc(0);
+        const int cj = __shfl_sync(gmask, c, (j0 + u) & (G - 1), G);
+        av[u] = __shfl_sync(gmask, v, (j0 + u) & (G - 1), G);
         const TB* brow = Bp + (int64_t)cj * a.ldb;
 #pragma unroll
-        for (int p = 0; p < VPL; ++p)
-          bv[u][p] = (ok && colok[p]) ? ldg16(brow + coff[p]) : make_uint4(0, 0, 0, 0);
+        for (int p = 0; p < VPL; ++p) bv[u][p] = colok[p] ? ldg16(brow + coff[p]) : make_uint4(0, 0, 0, 0);
       }
 #pragma unroll
       for (int u = 0; u < U; ++u)
@@ -112,6 +111,34 @@ __global__ void __launch_bounds__(256) csr_spmm_vec(CsrKArgs a) {
           for (int e = 0; e < VE; ++e) acc[p][e] = fma(av[u], b[e], acc[p][e]);
         }
     }
+    if constexpr (U > 1) {
+    if (j0 < cnt) {  // tail of 1 .. U-1 entries: no multiply by padded zeros
+      uint4 bv[U - 1][VPL];
+      TAcc av[U - 1];
+#pragma unroll
+      for (int u = 0; u < U - 1; ++u) {
+        if (j0 + u < cnt) {
+          const int cj = __shfl_sync(gmask, c, (j0 + u) & (G - 1), G);
+          av[u] = __shfl_sync(gmask, v, (j0 + u) & (G - 1), G);
+          const TB* brow = Bp + (int64_t)cj * a.ldb;
+#pragma unroll
+          for (int p = 0; p < VPL; ++p) bv[u][p] = colok[p] ? ldg16(brow + coff[p]) : make_uint4(0, 0, 0, 0);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U - 1; ++u) {
+        if (j0 + u < cnt) {
+#pragma unroll
+          for (int p = 0; p < VPL; ++p) {
+            TAcc b[VE];
+            unpack16<Tr>(bv[u][p], b);
+#pragma unroll
+            for (int e = 0; e < VE; ++e) acc[p][e] = fma(av[u], b[e], acc[p][e]);
+          }
+        }
+      }
+    }
+    }
   }
   if (row >= 0) {
     TC* crow = reinterpret_cast<TC*>(a.C) + (int64_t)row * a.ldc;
@@ -120,7 +147,8 @@ __global__ void __launch_bounds__(256) csr_spmm_vec(CsrKArgs a) {
       if (!colok[p]) continue;
       TC o[VE];
 #pragma unroll
-      for (int e = 0; e < VE; ++e) o[e] = (TC)(acc[p][e] * out_scale<Tr>(a, coff[p] + e));
+      for (int e = 0; e < VE; ++e)
+        o[e] = Tr::kScaled ? (TC)(acc[p][e] * out_scale<Tr>(a, coff[p] + e)) : (TC)acc[p][e];
       // VE outputs are 16 (F64/F32) or 32 (16-bit inputs, f32 outputs) bytes
 #pragma unroll
       for (int q = 0; q < (int)(VE * sizeof(TC) / 16); ++q)
@@ -181,7 +209,7 @@ __global__ void __launch_bounds__(256) csr_spmm_scalar(CsrKArgs a) {
   }
   if (!colok) return;
   if (row >= 0) {
-    reinterpret_cast<TC*>(a.C)[(int64_t)row * a.ldc + n] = (TC)(acc * out_scale<Tr>(a, n));
+    reinterpret_cast<TC*>(a.C)[(int64_t)row * a.ldc + n] = Tr::kScaled ? (TC)(acc * out_scale<Tr>(a, n)) : (TC)acc;
   } else {
     reinterpret_cast<TAcc*>(a.scratch)[(int64_t)(-1 - row) * a.N + n] = acc;
   }
@@ -202,7 +230,7 @@ __global__ void __launch_bounds__(256) split_reduce(const int32_t* __restrict__ 
   for (int64_t n = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; n < a.N; n += (int64_t)gridDim.y * blockDim.x) {
     TAcc acc = TAcc(0);
     for (int32_t q = s0; q < s1; ++q) acc += sc[(int64_t)q * a.N + n];
-    reinterpret_cast<TC*>(a.C)[(int64_t)row * a.ldc + n] = (TC)(acc * out_scale<Tr>(a, n));
+    reinterpret_cast<TC*>(a.C)[(int64_t)row * a.ldc + n] = Tr::kScaled ? (TC)(acc * out_scale<Tr>(a, n)) : (TC)acc;
   }
 }
 
@@ -219,7 +247,10 @@ cudaError_t launch_vec_g(const CsrKArgs& a, cudaStream_t s) {
   const int64_t chunks = (a.N + per_chunk - 1) / per_chunk;
   const int64_t threads = a.n_items * G;
   dim3 grid((unsigned)((threads + 255) / 256), (unsigned)chunks);
-  constexpr int U = (G >= 8) ? 8 : 4;
+  // F64 is bound by the FP64 pipe: one entry at a time, so no FMA is ever spent on a padded
+  // slot (a predicated-off DFMA still occupies the pipe) and registers stay low for occupancy.
+  // The other formats are bound by memory: U loads in flight per lane.
+  constexpr int U = std::is_same<Tr, TrF64>::value ? 1 : ((G >= 8) ? 8 : 4);
   csr_spmm_vec<Tr, G, VPL, U><<<grid, 256, 0, s>>>(a);
   return cudaGetLastError();
 }

@@ -12,21 +12,25 @@ namespace loops {
 // output (TC), and conversion of a stored element to the accumulator type.
 struct TrF64 {
   using TB = double; using TAcc = double; using TC = double;
+  static constexpr bool kScaled = false;  // outputs carry 1/s_A and column scales
   static constexpr int kVE = 2;  // elements per 16-byte vector
   __device__ static __forceinline__ TAcc to_acc(TB x) { return x; }
 };
 struct TrF32 {
   using TB = float; using TAcc = float; using TC = float;
+  static constexpr bool kScaled = false;  // outputs carry 1/s_A and column scales
   static constexpr int kVE = 4;
   __device__ static __forceinline__ TAcc to_acc(TB x) { return x; }
 };
 struct TrF16 {
   using TB = __half; using TAcc = float; using TC = float;
+  static constexpr bool kScaled = true;  // outputs carry 1/s_A and column scales
   static constexpr int kVE = 8;
   __device__ static __forceinline__ TAcc to_acc(TB x) { return __half2float(x); }
 };
 struct TrBF16 {
   using TB = __nv_bfloat16; using TAcc = float; using TC = float;
+  static constexpr bool kScaled = true;  // outputs carry 1/s_A and column scales
   static constexpr int kVE = 8;
   __device__ static __forceinline__ TAcc to_acc(TB x) { return __bfloat162float(x); }
 };

@@ -131,6 +131,51 @@ struct ValueMapDev {
   int64_t bytes = 0;
 };
 
+// Device descriptor of one matrix of a batched plan (pointers into its sub-plan, plus the
+// dense operands of the current call).
+struct BatchDesc {
+  const int32_t* item_row;
+  const int64_t* item_ptr;
+  const int32_t* col;
+  const void* val;
+  const int32_t* rb_id;
+  const int64_t* rb_ptr;
+  const int32_t* tile_col;
+  const void* tile_val;
+  const int32_t* order;
+  void* scratch;
+  const int32_t* split_row;
+  const int32_t* split_slot_ptr;
+  const void* B;
+  void* C;
+  const float* col_scale;
+  int64_t ldb, ldc, N, n_rows;
+  float inv_scale;
+  int32_t G;                           // lanes per CSR item / F32 block: N / elements per 16 B
+};
+
+// One task of the persistent batched kernel: kind 0 CSR items [first, first + count) of
+// matrix m, kind 1 F32 row blocks (positions in the block order), kind 2 one F16/BF16 block.
+struct BatchTask {
+  int32_t m;
+  int32_t kind;
+  int64_t first;
+  int32_t count;
+  int32_t pad;
+};
+
+struct BatchLaunch {
+  const BatchDesc* descs;
+  const BatchTask* tasks;
+  int64_t n_tasks;
+  const int2* splits;                  // (matrix, split row) pairs
+  int64_t n_splits;
+  int grid;
+  int smem_per_warp;
+};
+
+struct BatchState;
+
 }  // namespace loops
 
 // Opaque plan handle of the C ABI.
@@ -159,6 +204,8 @@ struct loops_plan_s {
   int64_t nnz_bcsr;
   cudaEvent_t tev[4];                  // optional caller-owned timing events (may be null)
   bool timing;
+  loops::BatchState* batch;            // non-null for a batched plan
+  int64_t other_bytes;                 // device bytes outside the part arrays
 };
 
 namespace loops {
@@ -190,6 +237,19 @@ cudaError_t launch_csr(const loops_plan_s* p, const CsrDev& d, const DenseArgs& 
 cudaError_t launch_bcsr(const loops_plan_s* p, const BcsrDev& d, const DenseArgs& a, cudaStream_t s);
 cudaError_t launch_sddmm(const loops_plan_s* p, const void* dC, int64_t lddc, const void* B,
                          int64_t ldb, void* dvals, cudaStream_t s);
+cudaError_t launch_batched(loops_dtype dtype, int32_t br, const BatchLaunch& L, cudaStream_t s);
+int batched_grid_blocks(loops_dtype dtype, int32_t br, int smem_per_warp);
+
+// Plan construction shared by the single and batched entry points (capi.cpp). `light` plans
+// (sub-plans of a batch) get no side stream, events or error word.
+loops_status make_plan(const loops_csr* A, const double* vals, int64_t N, loops_dtype dtype,
+                       const loops_plan_opts& o, int32_t br, double tau, bool light, loops_plan_s** out);
+void destroy_plan(loops_plan_s* p);
+loops_status cuda_status(cudaError_t e, const char* what);
+loops_status resolve_block_rows(loops_dtype dtype, const loops_plan_opts& o, int32_t* br);
+loops_status check_plan(loops_plan_t p);
+void destroy_batch(BatchState* b);
+
 cudaError_t launch_set_values(const loops_plan_s* p, const void* vals, loops_dtype vd, cudaStream_t s);
 cudaError_t launch_cast_scaled(const float* X, int64_t rows, int64_t cols, int64_t ldx,
                                loops_dtype yd, void* Y, int64_t ldy, float* col_scale,

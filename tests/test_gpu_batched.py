@@ -1,0 +1,111 @@
+"""GPU parity of the batched path: one persistent, graph-captured launch over many matrices of
+uneven size, structure and N, against the oracle per matrix."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from gpu_util import TOL, rel_l2, torch_dtype
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def lp(loops_lib):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return loops_lib
+
+
+@pytest.fixture(scope="module")
+def small_batch():
+    return W.batched_mix(count=18, seed=7, min_rows=100, max_rows=3000)
+
+
+def _run(lp, mats, fmt, tau, split_len=0, scale_columns=False, seed=0):
+    As = [A for A, _ in mats]
+    Ns = [N for _, N in mats]
+    plan = lp.BatchedPlan(As, Ns, fmt, tau=tau, split_len=split_len)
+    Bs, refs, scales = [], [], []
+    for m, (A, N) in enumerate(mats):
+        B = W.dense_normal(A.n_cols, N, seed * 1000 + m)
+        s_a = oracle.plan_scale(A.vals, fmt)
+        A_r = W.CSR(A.n_rows, A.n_cols, A.row_ptr, A.col_idx, oracle.round_to(A.vals * s_a, fmt) / s_a)
+        if scale_columns:
+            Bq, s = oracle.scale_round_columns(B, fmt)
+            scales.append(torch.as_tensor(s, dtype=torch.float32).cuda())
+            refs.append(oracle.spmm(A_r, Bq * s[None, :]))
+        else:
+            Bq = oracle.round_to(B, fmt)
+            refs.append(oracle.spmm(A_r, Bq))
+        Bs.append(torch.as_tensor(Bq).to(torch_dtype(torch, fmt)).cuda())
+    Cs = plan.spmm(Bs, col_scales=scales if scale_columns else None)
+    torch.cuda.synchronize()
+    errs = [rel_l2(C.double().cpu().numpy(), r) for C, r in zip(Cs, refs)]
+    return plan, Bs, Cs, refs, errs
+
+
+@pytest.mark.parametrize("fmt", ["f32", "bf16", "f16"])
+@pytest.mark.parametrize("tau", [math.inf, 2.0, 0.0])
+def test_batched_fixed_tau(lp, small_batch, fmt, tau):
+    plan, _, _, _, errs = _run(lp, small_batch, fmt, tau)
+    assert max(errs) <= TOL[fmt], errs
+
+
+@pytest.mark.parametrize("fmt", ["f32", "bf16"])
+def test_batched_autotuned(lp, small_batch, fmt):
+    plan, _, _, _, errs = _run(lp, small_batch, fmt, -1.0)
+    assert max(errs) <= TOL[fmt], errs
+    inf = plan.info()
+    assert inf["count"] == len(small_batch) and inf["n_tasks"] > 0
+
+
+def test_batched_graph_replay_and_pointer_change(lp, small_batch):
+    fmt = "f32"
+    plan, Bs, Cs, refs, errs = _run(lp, small_batch, fmt, 2.0)
+    assert max(errs) <= TOL[fmt]
+    # same pointers: replay only
+    for C in Cs:
+        C.fill_(float("nan"))
+    plan.spmm(Bs, Cs)
+    torch.cuda.synchronize()
+    assert max(rel_l2(C.double().cpu().numpy(), r) for C, r in zip(Cs, refs)) <= TOL[fmt]
+    # new buffers (different pointers, padded leading dimensions): descriptors re-uploaded
+    Bs2 = []
+    for B in Bs:
+        buf = torch.zeros((B.shape[0], B.shape[1] + 4), dtype=B.dtype, device="cuda")
+        buf[:, : B.shape[1]] = B
+        Bs2.append(buf[:, : B.shape[1]])
+    Cs2 = [torch.full((C.shape[0], C.shape[1] + 8), float("nan"), device="cuda")[:, : C.shape[1]] for C in Cs]
+    plan.spmm(Bs2, Cs2)
+    torch.cuda.synchronize()
+    assert max(rel_l2(C.double().cpu().numpy(), r) for C, r in zip(Cs2, refs)) <= TOL[fmt]
+
+
+def test_batched_split_rows_and_column_scales(lp):
+    mats = W.batched_mix(count=6, seed=9, min_rows=200, max_rows=1500)
+    # a long row in every matrix
+    out = []
+    for A, N in mats:
+        n = A.n_rows
+        r = np.concatenate([A.row_ids(), np.full(n, n // 2)])
+        c = np.concatenate([A.col_idx.astype(np.int64), np.arange(n)])
+        v = np.concatenate([A.vals, np.ones(n) * 0.5])
+        out.append((W.csr_from_coo(n, n, r, c, v), N))
+    for fmt in ("f32", "bf16"):
+        _, _, _, _, errs = _run(lp, out, fmt, 1.5, split_len=64)
+        assert max(errs) <= TOL[fmt], errs
+    _, _, _, _, errs = _run(lp, out, "bf16", 1.5, split_len=64, scale_columns=True)
+    assert max(errs) <= TOL["bf16"], errs
+
+
+def test_batched_rejects_unsupported_n(lp):
+    A = W.random_csr(50, 50, 0.1, 1)
+    with pytest.raises(lp.LoopsError):
+        lp.BatchedPlan([A], [6], "f32", tau=2.0)
+    with pytest.raises(lp.LoopsError):
+        lp.BatchedPlan([A], [32], "f64", tau=2.0)

@@ -1,0 +1,133 @@
+"""GPU parity at the full sizes of the five synthetic workloads, in the launch configuration the
+bench uses: every output against the oracle where it finishes in seconds, sampled rows (random
+rows plus the longest rows) elsewhere. Inputs are seeded stand-ins for the paper's SuiteSparse
+and GNN datasets."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from gpu_util import TOL, rel_l2, torch_dtype
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def lp(loops_lib):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return loops_lib
+
+
+def _rounded(A, fmt):
+    s = oracle.plan_scale(A.vals, fmt)
+    return W.CSR(A.n_rows, A.n_cols, A.row_ptr, A.col_idx, oracle.round_to(A.vals * s, fmt) / s)
+
+
+def _sample_rows(A, k, seed):
+    rng = np.random.default_rng(seed)
+    lens = np.diff(A.row_ptr)
+    longest = np.argsort(lens)[-32:]
+    return np.unique(np.concatenate([rng.integers(0, A.n_rows, k), longest, [0, A.n_rows - 1]]))
+
+
+def test_config1_plain_fp32_csr(lp):
+    A, B = W.uniform_rows(2000, 10, 32, seed=1)
+    for tau in (math.inf, -1.0):
+        plan = lp.Plan(A, 32, "f32", tau=tau)
+        C = plan.spmm(torch.as_tensor(B.astype(np.float32)).cuda()).double().cpu().numpy()
+        ref = oracle.spmm(_rounded(A, "f32"), B.astype(np.float32).astype(np.float64))
+        assert rel_l2(C, ref) <= TOL["f32"]
+
+
+@pytest.mark.parametrize("N", [64, 128])
+def test_config2_fp64_hybrid_split(lp, N):
+    A, B = W.laplacian_blocks(grid=512, n_blocks=4096, block=8, seed=1, N=N)
+    ref = oracle.spmm(A, B)
+    Bd = torch.as_tensor(B).cuda()
+    for tau in (2.0, math.inf, 0.0, -1.0):
+        plan = lp.Plan(A, N, "f64", tau=tau)
+        if tau == 2.0:
+            info = plan.info()
+            assert info["n_row_blocks"] == 4096 and info["n_csr_rows"] == 262144 - 32768
+        C = plan.spmm(Bd).cpu().numpy()
+        assert rel_l2(C, ref) <= TOL["f64"]
+
+
+@pytest.fixture(scope="module")
+def rmat20():
+    A, B = W.rmat_graph(scale=20, samples_per_node=8, seed=3, N=128)
+    return A, B
+
+
+@pytest.mark.parametrize("fmt", ["f16", "bf16"])
+def test_config3_rmat_mixed_precision(lp, rmat20, fmt):
+    A, B = rmat20
+    rows = _sample_rows(A, 4096, 5)
+    Bq, s = oracle.scale_round_columns(B, fmt)
+    A_r = _rounded(A, fmt)
+    ref = oracle.spmm_rows(A_r, Bq * s[None, :], rows)
+    exact = oracle.spmm_rows(A, B, rows)
+    Bd = torch.as_tensor(Bq).to(torch_dtype(torch, fmt)).cuda()
+    sd = torch.as_tensor(s, dtype=torch.float32).cuda()
+    for tau in (-1.0, math.inf):
+        plan = lp.Plan(A, 128, fmt, tau=tau)
+        C = plan.spmm(Bd, col_scale=sd)
+        got = C[torch.as_tensor(rows).cuda()].double().cpu().numpy()
+        assert rel_l2(got, ref) <= TOL[fmt]
+        err_exact = rel_l2(got, exact)
+        print(f"config3 {fmt} tau={plan.info()['tau']}: rel-L2 vs rounded-input oracle "
+              f"{rel_l2(got, ref):.2e}, vs FP64 inputs {err_exact:.2e}, "
+              f"subnormal A values {plan.info()['n_subnormal_vals']}")
+        assert err_exact <= {"f16": 5e-3, "bf16": 2e-2}[fmt]
+
+
+def test_config4_gcn_forward_backward(lp):
+    A, X, dY = W.gcn_graph(scale=18, samples_per_node=16, seed=4, N=256)
+    A32 = W.CSR(A.n_rows, A.n_cols, A.row_ptr, A.col_idx, A.vals.astype(np.float32))
+    A_r = _rounded(A32, "f32")
+    Xq = X.astype(np.float32).astype(np.float64)
+    dYq = dY.astype(np.float32).astype(np.float64)
+    plan = lp.Plan(A32, 256, "f32", tau=-1.0, want_backward=True)
+    Xd = torch.as_tensor(Xq, dtype=torch.float32).cuda()
+    dYd = torch.as_tensor(dYq, dtype=torch.float32).cuda()
+    Y = plan.spmm(Xd)
+    dX, dv = plan.backward(dYd, Xd)
+    rows = _sample_rows(A, 4096, 6)
+    ridx = torch.as_tensor(rows).cuda()
+    assert rel_l2(Y[ridx].double().cpu().numpy(), oracle.spmm_rows(A_r, Xq, rows)) <= TOL["f32"]
+    assert rel_l2(dX.double().cpu().numpy(), oracle.spmm_t(A_r, dYq)) <= TOL["f32"]
+    ks = np.random.default_rng(7).integers(0, A.nnz, 200000)
+    dv_ref = oracle.sddmm(A_r, dYq, Xq)
+    assert rel_l2(dv.double().cpu().numpy()[ks], dv_ref[ks]) <= TOL["f32"]
+
+
+@pytest.fixture(scope="module")
+def batch512():
+    return W.batched_mix(count=512, seed=5)
+
+
+@pytest.mark.parametrize("fmt", ["f32", "bf16"])
+def test_config5_batched_512(lp, batch512, fmt):
+    mats = batch512
+    As = [A for A, _ in mats]
+    Ns = [N for _, N in mats]
+    plan = lp.BatchedPlan(As, Ns, fmt, tau=2.0)
+    Bs, Bqs = [], []
+    for m, (A, N) in enumerate(mats):
+        Bq = oracle.round_to(W.dense_normal(A.n_cols, N, 50 + m), fmt)
+        Bqs.append(Bq)
+        Bs.append(torch.as_tensor(Bq).to(torch_dtype(torch, fmt)).cuda())
+    Cs = plan.spmm(Bs)
+    torch.cuda.synchronize()
+    worst = 0.0
+    for m, (A, N) in enumerate(mats):
+        rows = _sample_rows(A, 16, m)
+        ref = oracle.spmm_rows(_rounded(A, fmt), Bqs[m], rows)
+        got = Cs[m][torch.as_tensor(rows).cuda()].double().cpu().numpy()
+        worst = max(worst, rel_l2(got, ref))
+    assert worst <= TOL[fmt], worst
