@@ -12,8 +12,8 @@ number-format readings, written out with numpy:
   finite value), returned as float64.
 * ``plan_scale(vals, fmt)``: the power of two s_A with max|a| * s_A <= 2^14 applied to A
   before a 16-bit cast (1 when A is all zero or the format is not 16-bit).
-* ``col_scales(B)``: s_j = 2^ceil(log2 max_i |B_ij|) per column (1 for an all-zero column),
-  so that |B_ij / s_j| <= 1 before a 16-bit cast.
+* ``col_scales(B)``: s_j = 2^ceil(log2 max_i |B_ij|) per column (1 for an all-zero column,
+  at most 2^127), so that |B_ij / s_j| <= 1 before a 16-bit cast.
 * ``partition(...)``: Algorithm 1 (CSR -> LOOPS) with the structural-split reading; values
   are the f64 sums of duplicates, rounded once into the compute format.
 
@@ -202,13 +202,14 @@ def plan_scale(vals, fmt: str) -> float:
 
 
 def col_scales(B) -> np.ndarray:
-    """s_j = 2^ceil(log2 max_i |B_ij|) (1 for an all-zero column), float64[N]."""
+    """s_j = 2^ceil(log2 max_i |B_ij|) (1 for an all-zero column), capped at 2^127 (the largest
+    power of two of binary32, in which the scales are kept), float64[N]."""
     B = np.asarray(B, dtype=np.float64)
     mx = np.abs(B).max(axis=0) if B.shape[0] else np.zeros(B.shape[1])
     s = np.ones(B.shape[1], dtype=np.float64)
     nz = mx > 0
     f, e2 = np.frexp(mx[nz])
-    c = np.where(f == 0.5, e2 - 1, e2)
+    c = np.minimum(np.where(f == 0.5, e2 - 1, e2), 127)
     s[nz] = np.ldexp(1.0, c.astype(np.int64))
     return s
 

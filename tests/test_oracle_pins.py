@@ -161,6 +161,9 @@ def test_scales():
     assert list(oracle.col_scales(B)) == [0.5, 4.0, 1.0, 4.0]
     B16, s = oracle.scale_round_columns(B, "f16")
     assert np.all(np.abs(B16) <= 1.0)
+    # a column maximum above 2^127 (binary32 range) keeps the largest binary32 power of two
+    big = np.array([[3.0e38], [1.0]])
+    assert oracle.col_scales(big)[0] == 2.0 ** 127
 
 
 # ------------------------------------------------------------------ Algorithm 1 partition
