@@ -198,6 +198,15 @@ loops_status loops_spmm_scaled(loops_plan_t plan, const void* B, int64_t ldb,
 loops_status loops_spmm_host(loops_plan_t plan, const void* B_host, int64_t ldb, void* C_host,
                              int64_t ldc, loops_stream_t stream);
 
+/* Pipelined end-to-end SpMM with HOST buffers, for a sequence of calls: like loops_spmm_host,
+ * but it does not wait. Two plan-owned staging sets alternate between calls, and the copy of
+ * the next call's B to the device runs on an internal stream while this call's C comes back on
+ * another, so consecutive calls overlap their transfers. Each call's C_host is complete once
+ * `stream` has been synchronised; B_host and C_host must stay valid and unchanged until then.
+ * Calls on one plan must use the same `stream`. */
+loops_status loops_spmm_host_async(loops_plan_t plan, const void* B_host, int64_t ldb, void* C_host,
+                                   int64_t ldc, loops_stream_t stream);
+
 /* Backward of C = A . B for a plan built with want_backward:
  *   dB = A^T . dC  (transposed hybrid SpMM; dB device, n_cols x N, lddb; NULL to skip)
  *   dvals[k] = <dC[i_k, :], B[j_k, :]>  (SDDMM on A's pattern, in A's input order;

@@ -32,7 +32,8 @@ EXPORTED = ["loops_version", "loops_status_str", "loops_last_error", "loops_plan
             "loops_plan_info_get", "loops_plan_export", "loops_plan_update_values", "loops_spmm",
             "loops_spmm_scaled", "loops_spmm_host", "loops_spmm_backward", "loops_cast_scaled",
             "loops_plan_check", "loops_plan_set_timing_events", "loops_plan_set_values",
-            "loops_csr_spmm_noalloc", "loops_plan_batched", "loops_spmm_batched", "loops_plan_batched_info"]
+            "loops_csr_spmm_noalloc", "loops_plan_batched", "loops_spmm_batched", "loops_plan_batched_info",
+            "loops_spmm_host_async"]
 
 
 class LoopsError(RuntimeError):
@@ -108,6 +109,7 @@ def load():
     L.loops_spmm.argtypes = [vp, vp, i64, vp, i64, vp]
     L.loops_spmm_scaled.argtypes = [vp, vp, i64, vp, vp, i64, vp]
     L.loops_spmm_host.argtypes = [vp, vp, i64, vp, i64, vp]
+    L.loops_spmm_host_async.argtypes = [vp, vp, i64, vp, i64, vp]
     L.loops_spmm_backward.argtypes = [vp, vp, i64, vp, i64, vp, i64, vp, vp]
     L.loops_cast_scaled.argtypes = [vp, i64, i64, i64, ctypes.c_int, vp, i64, vp, vp]
     L.loops_plan_check.argtypes = [vp, vp]
@@ -313,6 +315,13 @@ class Plan:
         """End-to-end C = A . B with host (ideally pinned) CPU tensors; synchronises."""
         _check(self._L.loops_spmm_host(self._h, B_host.data_ptr(), B_host.stride(0), C_host.data_ptr(),
                                        C_host.stride(0), _stream_handle(stream)))
+        return C_host
+
+    def spmm_host_async(self, B_host, C_host, stream=None):
+        """Pipelined end-to-end C = A . B with pinned host tensors; C_host is complete after the
+        stream is synchronised (consecutive calls overlap their transfers)."""
+        _check(self._L.loops_spmm_host_async(self._h, B_host.data_ptr(), B_host.stride(0), C_host.data_ptr(),
+                                             C_host.stride(0), _stream_handle(stream)))
         return C_host
 
     def backward(self, dC, B, need_dB=True, need_dvals=True, stream=None):

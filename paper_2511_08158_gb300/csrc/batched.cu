@@ -6,11 +6,13 @@
 // (no atomics, no inter-block waits, so the launch is deterministic and graph-stable).
 //   CSR task   (kind 0): items [first, first + count); a group of G = N / VE lanes per item,
 //              32 / G items at a time per warp (VE elements of a 16-byte B vector per lane).
-//   BCSR task  (kind 1): F32 row blocks [first, first + count) (positions in the matrix's
-//              block order), one group of G lanes per block, register-blocked outer product.
-//   BCSR task  (kind 2): one F16/BF16 row block per warp: the 16 B rows of each K-group are
-//              staged in the warp's own shared-memory slice and fed to mma.sync m16n8k16.
-// Matrices with rows split in segments get a second, small launch that sums the partials.
+//   BCSR task  (kind 1): F32 units [first, first + count) (a unit is a row block, or a K-aligned
+//              range of a block with very many tiles), one group of G lanes per unit,
+//              register-blocked outer product.
+//   BCSR task  (kind 2): one F16/BF16 unit per warp: the 16 B rows of each K-group are staged
+//              in the warp's own shared-memory slice and fed to mma.sync m16n8k16.
+// Rows split in segments and blocks cut into units get small follow-up launches that add
+// their partial sums in a fixed order.
 #include <type_traits>
 
 #include "device_common.cuh"
@@ -106,12 +108,13 @@ __device__ __forceinline__ void csr_item(const BatchDesc& d, int64_t item, int G
   }
 }
 
-// One F32 row block (B_r rows, tile-major values) for a group of G lanes.
+// One F32 BCSR unit (B_r rows, tile-major values) for a group of G lanes.
 template <int BR>
-__device__ __forceinline__ void ffma_block(const BatchDesc& d, int64_t pos, int sub) {
-  const int32_t b = d.order[pos];
+__device__ __forceinline__ void ffma_block(const BatchDesc& d, int64_t u, int sub) {
+  const int32_t b = d.unit_block[u];
   const int64_t rb = d.rb_id[b];
-  const int64_t t0 = d.rb_ptr[b], t1 = d.rb_ptr[b + 1];
+  const int64_t t0 = d.unit_t0[u], t1 = d.unit_t1[u];
+  const int32_t slot = d.unit_slot[u];
   const float* Av = reinterpret_cast<const float*>(d.tile_val);
   const float* Bp = reinterpret_cast<const float*>(d.B);
   const int64_t n = (int64_t)sub * 4;
@@ -134,6 +137,13 @@ __device__ __forceinline__ void ffma_block(const BatchDesc& d, int64_t pos, int 
         for (int e = 0; e < 4; ++e) acc[r4 * 4 + i][e] = fmaf(a4[i], bv[e], acc[r4 * 4 + i][e]);
     }
   }
+  if (slot >= 0) {  // unit of a split block: partial sums
+    float* P = reinterpret_cast<float*>(d.bscratch) + (int64_t)slot * BR * d.N;
+#pragma unroll
+    for (int r = 0; r < BR; ++r)
+      *reinterpret_cast<float4*>(P + r * d.N + n) = make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
+    return;
+  }
   float* C = reinterpret_cast<float*>(d.C);
 #pragma unroll
   for (int r = 0; r < BR; ++r) {
@@ -146,12 +156,13 @@ __device__ __forceinline__ void ffma_block(const BatchDesc& d, int64_t pos, int 
 // One F16/BF16 row block for the whole warp; sB is the warp's shared-memory slice holding the
 // 16 gathered B rows of the current K-group (row stride N + 8 elements).
 template <class T>
-__device__ __forceinline__ void hmma_block(const BatchDesc& d, int64_t pos, T* sB, int lane) {
+__device__ __forceinline__ void hmma_block(const BatchDesc& d, int64_t u, T* sB, int lane) {
   constexpr bool kBF16 = sizeof(T) == 2 && !std::is_same<T, __half>::value;
-  const int32_t b = d.order[pos];
+  const int32_t b = d.unit_block[u];
   const int64_t rb = d.rb_id[b];
-  const int64_t t0 = d.rb_ptr[b];
-  const int n_groups = (int)((d.rb_ptr[b + 1] - t0) / 16);
+  const int64_t t0 = d.unit_t0[u];
+  const int n_groups = (int)((d.unit_t1[u] - t0) / 16);
+  const int32_t slot = d.unit_slot[u];
   const int N = (int)d.N;
   const int RS = N + 8;
   const int NF = N / 8;
@@ -194,6 +205,18 @@ __device__ __forceinline__ void hmma_block(const BatchDesc& d, int64_t pos, T* s
     }
   }
   const int q = lane >> 2, t = lane & 3;
+  if (slot >= 0) {  // unit of a split block: unscaled partial sums
+    float* P = reinterpret_cast<float*>(d.bscratch) + (int64_t)slot * 16 * d.N;
+#pragma unroll
+    for (int f = 0; f < 16; ++f) {
+      if (f >= NF) break;
+      const int64_t n = f * 8 + 2 * t;
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+        *reinterpret_cast<float2*>(P + (int64_t)(q + 8 * h) * d.N + n) = make_float2(acc[f][2 * h], acc[f][2 * h + 1]);
+    }
+    return;
+  }
   float* C = reinterpret_cast<float*>(d.C);
 #pragma unroll
   for (int f = 0; f < 16; ++f) {
@@ -261,6 +284,27 @@ __global__ void __launch_bounds__(128) batched_split_reduce(const BatchDesc* __r
   }
 }
 
+// BCSR blocks cut into units: C rows = scale * sum of the units' partials, in slot order.
+template <class Tr>
+__global__ void __launch_bounds__(256) batched_bsplit_reduce(const BatchDesc* __restrict__ descs,
+                                                             const int2* __restrict__ bsplits) {
+  const int2 sp = bsplits[blockIdx.x];
+  const BatchDesc& d = descs[sp.x];
+  const int32_t b = d.bsplit_block[sp.y];
+  const int64_t rb = d.rb_id[b];
+  const int32_t s0 = d.bsplit_slot_ptr[sp.y], s1 = d.bsplit_slot_ptr[sp.y + 1];
+  const float* P = reinterpret_cast<const float*>(d.bscratch);
+  const int64_t total = (int64_t)d.br * d.N;
+  for (int64_t i = threadIdx.x; i < total; i += blockDim.x) {
+    const int64_t r = i / d.N, n = i - r * d.N;
+    const int64_t row = rb * d.br + r;
+    if (row >= d.n_rows) continue;
+    float acc = 0.f;
+    for (int32_t q = s0; q < s1; ++q) acc += P[((int64_t)q * d.br + r) * d.N + n];
+    reinterpret_cast<float*>(d.C)[row * d.ldc + n] = Tr::kScaled ? acc * col_mult<Tr>(d, n) : acc;
+  }
+}
+
 template <class Tr, int BR>
 cudaError_t launch_batched_t(const BatchLaunch& L, cudaStream_t s) {
   const int smem = L.smem_per_warp * 8;
@@ -276,6 +320,11 @@ cudaError_t launch_batched_t(const BatchLaunch& L, cudaStream_t s) {
   }
   if (L.n_splits > 0) {
     batched_split_reduce<Tr><<<(unsigned)L.n_splits, 128, 0, s>>>(L.descs, L.splits);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (L.n_bsplits > 0) {
+    batched_bsplit_reduce<Tr><<<(unsigned)L.n_bsplits, 256, 0, s>>>(L.descs, L.bsplits);
     return cudaGetLastError();
   }
   return cudaSuccess;

@@ -18,7 +18,8 @@ struct BatchState {
   BatchDesc* d_desc = nullptr;
   BatchTask* d_tasks = nullptr;
   int2* d_splits = nullptr;
-  int64_t n_tasks = 0, n_splits = 0;
+  int2* d_bsplits = nullptr;
+  int64_t n_tasks = 0, n_splits = 0, n_bsplits = 0;
   int grid = 0, smem_per_warp = 0;
   cudaStream_t cap = nullptr;         // capture stream
   cudaGraph_t graph = nullptr;
@@ -35,7 +36,7 @@ void destroy_batch(BatchState* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   if (b->h_desc) cudaFreeHost(b->h_desc);
-  void* ptrs[] = {b->d_desc, b->d_tasks, b->d_splits};
+  void* ptrs[] = {b->d_desc, b->d_tasks, b->d_splits, b->d_bsplits};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (b->cap) cudaStreamDestroy(b->cap);
@@ -61,7 +62,7 @@ loops_status build_batch(const loops_csr* As, const int64_t* Ns, int32_t count, 
   const int VE = elems_per_16b(dtype);
   std::vector<BatchTask> tasks;
   std::vector<double> cost;
-  std::vector<int2> splits;
+  std::vector<int2> splits, bsplits;
   int64_t max_N = 8;
   std::vector<double> vals;
   for (int32_t m = 0; m < count && !st; ++m) {
@@ -94,34 +95,21 @@ loops_status build_batch(const loops_csr* As, const int64_t* Ns, int32_t count, 
       cost.push_back((double)(nnz + (j - i)) * (double)N);
       i = j;
     }
-    // BCSR blocks (positions in the block order, most tiles first)
-    const Canon& cn = p->canon;
-    std::vector<int64_t> tiles_in_order;
-    for (int64_t q = 0; q < p->dev.bcsr.n_rb; ++q) {
-      // the order array sorts blocks by tile count, descending and stable
-      tiles_in_order.push_back(0);
-    }
-    if (p->dev.bcsr.n_rb) {
-      std::vector<int32_t> order((size_t)p->dev.bcsr.n_rb);
-      for (int64_t q = 0; q < p->dev.bcsr.n_rb; ++q) order[(size_t)q] = (int32_t)q;
-      std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
-        return cn.rb_ptr[(size_t)x + 1] - cn.rb_ptr[(size_t)x] > cn.rb_ptr[(size_t)y + 1] - cn.rb_ptr[(size_t)y];
-      });
-      for (int64_t q = 0; q < p->dev.bcsr.n_rb; ++q)
-        tiles_in_order[(size_t)q] = cn.rb_ptr[(size_t)order[(size_t)q] + 1] - cn.rb_ptr[(size_t)order[(size_t)q]];
-    }
+    // BCSR units (most tiles first)
+    const BcsrDev& bd = p->dev.bcsr;
     if (dtype == LOOPS_F32) {
-      for (int64_t q = 0; q < p->dev.bcsr.n_rb; q += per_round) {
-        const int32_t cnt = (int32_t)std::min<int64_t>(per_round, p->dev.bcsr.n_rb - q);
+      for (int64_t q = 0; q < bd.n_units; q += per_round) {
+        const int32_t cnt = (int32_t)std::min<int64_t>(per_round, bd.n_units - q);
         tasks.push_back({m, 1, q, cnt, 0});
-        cost.push_back((double)tiles_in_order[(size_t)q] * br * (double)N);
+        cost.push_back((double)bd.h_unit_tiles[(size_t)q] * br * (double)N);
       }
     } else {
-      for (int64_t q = 0; q < p->dev.bcsr.n_rb; ++q) {
+      for (int64_t q = 0; q < bd.n_units; ++q) {
         tasks.push_back({m, 2, q, 1, 0});
-        cost.push_back((double)tiles_in_order[(size_t)q] * br * (double)N);
+        cost.push_back((double)bd.h_unit_tiles[(size_t)q] * br * (double)N);
       }
     }
+    for (int64_t sidx = 0; sidx < bd.n_split; ++sidx) bsplits.push_back(make_int2(m, (int)sidx));
     for (int64_t sidx = 0; sidx < c.n_split; ++sidx) splits.push_back(make_int2(m, (int)sidx));
   }
   if (st) { destroy_batch(b); return st; }
@@ -133,6 +121,7 @@ loops_status build_batch(const loops_csr* As, const int64_t* Ns, int32_t count, 
   for (size_t i = 0; i < idx.size(); ++i) sorted[i] = tasks[(size_t)idx[i]];
   b->n_tasks = (int64_t)sorted.size();
   b->n_splits = (int64_t)splits.size();
+  b->n_bsplits = (int64_t)bsplits.size();
   b->smem_per_warp = dtype == LOOPS_F32 ? 0 : (int)(((16 * (max_N + 8) * 2) + 127) / 128 * 128);
   b->grid = batched_grid_blocks(dtype, br, b->smem_per_warp);
   // descriptors (static parts now; B/C pointers per call)
@@ -144,10 +133,14 @@ loops_status build_batch(const loops_csr* As, const int64_t* Ns, int32_t count, 
   if (e == cudaSuccess && b->n_splits) e = cudaMalloc((void**)&b->d_splits, sizeof(int2) * (size_t)b->n_splits);
   if (e == cudaSuccess && b->n_splits)
     e = cudaMemcpy(b->d_splits, splits.data(), sizeof(int2) * (size_t)b->n_splits, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && b->n_bsplits) e = cudaMalloc((void**)&b->d_bsplits, sizeof(int2) * (size_t)b->n_bsplits);
+  if (e == cudaSuccess && b->n_bsplits)
+    e = cudaMemcpy(b->d_bsplits, bsplits.data(), sizeof(int2) * (size_t)b->n_bsplits, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_copied, cudaEventDisableTiming);
   if (e != cudaSuccess) { st = cuda_status(e, "batched plan setup"); destroy_batch(b); return st; }
-  b->device_bytes = (int64_t)(sizeof(BatchDesc) * count + sizeof(BatchTask) * b->n_tasks + sizeof(int2) * b->n_splits);
+  b->device_bytes = (int64_t)(sizeof(BatchDesc) * count + sizeof(BatchTask) * b->n_tasks +
+                              sizeof(int2) * (b->n_splits + b->n_bsplits));
   for (int32_t m = 0; m < count; ++m) {
     const loops_plan_s* p = b->subs[(size_t)m];
     BatchDesc& d = b->h_desc[m];
@@ -160,7 +153,14 @@ loops_status build_batch(const loops_csr* As, const int64_t* Ns, int32_t count, 
     d.rb_ptr = p->dev.bcsr.rb_ptr;
     d.tile_col = p->dev.bcsr.tile_col;
     d.tile_val = p->dev.bcsr.tile_val;
-    d.order = p->dev.bcsr.order;
+    d.unit_block = p->dev.bcsr.unit_block;
+    d.unit_t0 = p->dev.bcsr.unit_t0;
+    d.unit_t1 = p->dev.bcsr.unit_t1;
+    d.unit_slot = p->dev.bcsr.unit_slot;
+    d.bscratch = p->dev.bcsr.scratch;
+    d.bsplit_block = p->dev.bcsr.split_block;
+    d.bsplit_slot_ptr = p->dev.bcsr.split_slot_ptr;
+    d.br = p->br;
     d.scratch = p->dev.csr.scratch;
     d.split_row = p->dev.csr.split_row;
     d.split_slot_ptr = p->dev.csr.split_slot_ptr;
@@ -181,6 +181,8 @@ cudaError_t run_batch(BatchState* b, cudaStream_t s) {
   L.n_tasks = b->n_tasks;
   L.splits = b->d_splits;
   L.n_splits = b->n_splits;
+  L.bsplits = b->d_bsplits;
+  L.n_bsplits = b->n_bsplits;
   L.grid = b->grid;
   L.smem_per_warp = b->smem_per_warp;
   return launch_batched(b->dtype, b->br, L, s);
@@ -351,6 +353,7 @@ loops_status loops_plan_batched(const loops_csr* As, const int64_t* Ns, int32_t 
   p->ev_fork = p->ev_join = nullptr;
   p->stage_B = p->stage_C = nullptr;
   p->stage_B_bytes = p->stage_C_bytes = 0;
+  p->pipe = nullptr;
   p->n_subnormal = 0;
   p->nnz_bcsr = 0;
   p->timing = false;

@@ -1,7 +1,8 @@
 // BCSR-part SpMM: the outer-product tile kernel of Algorithms 2 and 3, on tensor cores.
 //
 // A row block of B_r rows holds tiles (B_r x 1 columns of A, one per distinct column) padded
-// to a multiple of the MMA K. One K-group of tiles against the matching K gathered rows of B
+// to a multiple of the MMA K. Kernels run over work units (a block, or a K-aligned range of a
+// block with very many tiles, whose partial sums a last kernel adds in a fixed order). One K-group of tiles against the matching K gathered rows of B
 // is one MMA: the paper's sum of rank-1 updates (fmopa) of a B_r x 1 tile with a 1 x N row
 // of B becomes a B_r x K by K x 8 product. Accumulators stay in registers for the whole row
 // block and are stored once (C = A.B overwrites C).
@@ -26,8 +27,12 @@ struct BcsrKArgs {
   const int64_t* rb_ptr;
   const int32_t* tile_col;
   const void* tile_val;
-  const int32_t* order;
-  int64_t n_rb;
+  const int32_t* unit_block;
+  const int64_t* unit_t0;
+  const int64_t* unit_t1;
+  const int32_t* unit_slot;
+  int64_t n_units;
+  void* scratch;           // partial sums of units of split blocks: [slot][B_r][N]
   const void* B;
   int64_t ldb;
   void* C;
@@ -81,10 +86,12 @@ __global__ void __launch_bounds__(WARPS * 32) bcsr_hmma(BcsrKArgs a) {
   __shared__ __align__(8) uint64_t bar[kStages];
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
-  const int32_t b = a.order[blockIdx.x];
+  const int64_t u = blockIdx.x;
+  const int32_t b = a.unit_block[u];
   const int64_t rb = a.rb_id[b];
-  const int64_t t0 = a.rb_ptr[b];
-  const int n_groups = (int)((a.rb_ptr[b + 1] - t0) / 16);
+  const int64_t t0 = a.unit_t0[u];
+  const int n_groups = (int)((a.unit_t1[u] - t0) / 16);
+  const int32_t slot = a.unit_slot[u];
   const int64_t n0 = (int64_t)blockIdx.y * CT;
   const int width = (int)(a.N - n0 < (int64_t)CT ? a.N - n0 : (int64_t)CT);  // valid columns in this tile
   const T* Bp = reinterpret_cast<const T*>(a.B);
@@ -183,6 +190,20 @@ __global__ void __launch_bounds__(WARPS * 32) bcsr_hmma(BcsrKArgs a) {
   const int q = lane >> 2, t = lane & 3;
   float* C = reinterpret_cast<float*>(a.C);
   const bool vec2 = ((a.ldc & 1) == 0) && (((uintptr_t)a.C & 7) == 0);
+  if (slot >= 0) {  // one unit of a split block: unscaled partial sums
+    float* P = reinterpret_cast<float*>(a.scratch) + (int64_t)slot * 16 * a.N;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      const int64_t n = n0 + (warp * NF + f) * 8 + 2 * t;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        float* pp = P + (int64_t)(q + 8 * h) * a.N + n;
+        if (n < a.N) pp[0] = acc[f][2 * h];
+        if (n + 1 < a.N) pp[1] = acc[f][2 * h + 1];
+      }
+    }
+    return;
+  }
 #pragma unroll
   for (int f = 0; f < NF; ++f) {
     const int64_t n = n0 + (warp * NF + f) * 8 + 2 * t;
@@ -210,7 +231,7 @@ __global__ void __launch_bounds__(WARPS * 32) bcsr_hmma(BcsrKArgs a) {
 template <class T, int WARPS, int NF>
 cudaError_t launch_hmma_cfg(const BcsrKArgs& a, bool bulk, cudaStream_t s) {
   constexpr int CT = WARPS * 8 * NF;
-  dim3 grid((unsigned)a.n_rb, (unsigned)((a.N + CT - 1) / CT));
+  dim3 grid((unsigned)a.n_units, (unsigned)((a.N + CT - 1) / CT));
   if (bulk) bcsr_hmma<T, WARPS, NF, true><<<grid, WARPS * 32, 0, s>>>(a);
   else bcsr_hmma<T, WARPS, NF, false><<<grid, WARPS * 32, 0, s>>>(a);
   return cudaGetLastError();
@@ -241,13 +262,14 @@ __global__ void __launch_bounds__(128) bcsr_dmma(BcsrKArgs a) {
   const int lane = threadIdx.x & 31;
   const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t n_ct = (a.N + 16 * NP - 1) / (16 * NP);
-  if (wid >= a.n_rb * n_ct) return;
-  const int64_t bi = wid / n_ct;
+  if (wid >= a.n_units * n_ct) return;
+  const int64_t u = wid / n_ct;
   const int64_t n0 = (wid % n_ct) * (16 * NP);
-  const int32_t b = a.order[bi];
+  const int32_t b = a.unit_block[u];
   const int64_t rb = a.rb_id[b];
-  const int64_t t0 = a.rb_ptr[b];
-  const int n_groups = (int)((a.rb_ptr[b + 1] - t0) / 4);
+  const int64_t t0 = a.unit_t0[u];
+  const int n_groups = (int)((a.unit_t1[u] - t0) / 4);
+  const int32_t slot = a.unit_slot[u];
   const int q = lane >> 2, t = lane & 3;
   const double* Av = reinterpret_cast<const double*>(a.tile_val) + t0 * 8;
   const double* Bp = reinterpret_cast<const double*>(a.B);
@@ -279,6 +301,18 @@ __global__ void __launch_bounds__(128) bcsr_dmma(BcsrKArgs a) {
       dmma884(acc[p][1], av, b1);
     }
   }
+  if (slot >= 0) {  // one unit of a split block: partial sums of its 8 rows
+    double* prow = reinterpret_cast<double*>(a.scratch) + ((int64_t)slot * 8 + q) * a.N;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      const int64_t n = n0 + 16 * p + 4 * t;
+      const double o[4] = {acc[p][0][0], acc[p][1][0], acc[p][0][1], acc[p][1][1]};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (n + i < a.N) prow[n + i] = o[i];
+    }
+    return;
+  }
   const int64_t row = rb * 8 + q;
   if (row >= a.n_rows) return;
   double* crow = reinterpret_cast<double*>(a.C) + row * a.ldc;
@@ -303,7 +337,7 @@ cudaError_t launch_dmma(const BcsrKArgs& a, cudaStream_t s) {
   auto go = [&](auto np_tag) {
     constexpr int NP = decltype(np_tag)::value;
     const int64_t n_ct = (a.N + 16 * NP - 1) / (16 * NP);
-    const int64_t warps = a.n_rb * n_ct;
+    const int64_t warps = a.n_units * n_ct;
     bcsr_dmma<NP><<<(unsigned)((warps + 3) / 4), 128, 0, s>>>(a);
     return cudaGetLastError();
   };
@@ -322,12 +356,13 @@ __global__ void __launch_bounds__(256) bcsr_ffma(BcsrKArgs a) {
   const int sub = lane & (G - 1);
   const int64_t gid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
   const int64_t n_ct = (a.N + G * VE - 1) / (G * VE);
-  if (gid >= a.n_rb * n_ct) return;
-  const int64_t bi = gid / n_ct;
+  if (gid >= a.n_units * n_ct) return;
+  const int64_t u = gid / n_ct;
   const int64_t n = (gid % n_ct) * (G * VE) + (int64_t)sub * VE;
-  const int32_t b = a.order[bi];
+  const int32_t b = a.unit_block[u];
   const int64_t rb = a.rb_id[b];
-  const int64_t t0 = a.rb_ptr[b], t1 = a.rb_ptr[b + 1];
+  const int64_t t0 = a.unit_t0[u], t1 = a.unit_t1[u];
+  const int32_t slot = a.unit_slot[u];
   const float* Av = reinterpret_cast<const float*>(a.tile_val);
   const float* Bp = reinterpret_cast<const float*>(a.B);
   float acc[BR][VE];
@@ -361,6 +396,14 @@ __global__ void __launch_bounds__(256) bcsr_ffma(BcsrKArgs a) {
       for (int e = 0; e < VE; ++e) acc[r][e] = fmaf(av[r], bv[e], acc[r][e]);
   }
   if (!colok) return;
+  if (slot >= 0) {  // one unit of a split block: partial sums of its BR rows
+    float* P = reinterpret_cast<float*>(a.scratch) + (int64_t)slot * BR * a.N;
+#pragma unroll
+    for (int r = 0; r < BR; ++r)
+#pragma unroll
+      for (int e = 0; e < VE; ++e) P[(int64_t)r * a.N + n + e] = acc[r][e];
+    return;
+  }
   float* C = reinterpret_cast<float*>(a.C);
 #pragma unroll
   for (int r = 0; r < BR; ++r) {
@@ -384,7 +427,7 @@ cudaError_t launch_ffma_br(const BcsrKArgs& a, cudaStream_t s) {
     constexpr bool V = decltype(v_tag)::value;
     constexpr int VE = V ? 4 : 1;
     const int64_t n_ct = (a.N + G * VE - 1) / (G * VE);
-    const int64_t threads = a.n_rb * n_ct * G;
+    const int64_t threads = a.n_units * n_ct * G;
     bcsr_ffma<BR, G, V><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(a);
     return cudaGetLastError();
   };
@@ -398,6 +441,32 @@ cudaError_t launch_ffma_br(const BcsrKArgs& a, cudaStream_t s) {
   return go(std::integral_constant<int, 32>(), std::true_type());
 }
 
+// Blocks cut into several units: C rows = scale * sum of the units' partials, in slot order.
+template <class TAcc, class TC, bool SCALED>
+__global__ void __launch_bounds__(256) bcsr_split_reduce(const int32_t* __restrict__ split_block,
+                                                         const int32_t* __restrict__ slot_ptr, int32_t br,
+                                                         BcsrKArgs a) {
+  const int64_t sidx = blockIdx.x;
+  const int32_t b = split_block[sidx];
+  const int64_t rb = a.rb_id[b];
+  const int32_t s0 = slot_ptr[sidx], s1 = slot_ptr[sidx + 1];
+  const TAcc* P = reinterpret_cast<const TAcc*>(a.scratch);
+  const int64_t total = (int64_t)br * a.N;
+  for (int64_t i = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.y * blockDim.x) {
+    const int64_t r = i / a.N, n = i - r * a.N;
+    const int64_t row = rb * br + r;
+    if (row >= a.n_rows) continue;
+    TAcc acc = TAcc(0);
+    for (int32_t q = s0; q < s1; ++q) acc += P[((int64_t)q * br + r) * a.N + n];
+    if (SCALED) {
+      const float sc = a.col_scale ? a.col_scale[n] * a.inv_scale_f : a.inv_scale_f;
+      reinterpret_cast<TC*>(a.C)[row * a.ldc + n] = (TC)(acc * sc);
+    } else {
+      reinterpret_cast<TC*>(a.C)[row * a.ldc + n] = (TC)acc;
+    }
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_bcsr(const loops_plan_s* p, const BcsrDev& d, const DenseArgs& da, cudaStream_t s) {
@@ -407,8 +476,12 @@ cudaError_t launch_bcsr(const loops_plan_s* p, const BcsrDev& d, const DenseArgs
   a.rb_ptr = d.rb_ptr;
   a.tile_col = d.tile_col;
   a.tile_val = d.tile_val;
-  a.order = d.order;
-  a.n_rb = d.n_rb;
+  a.unit_block = d.unit_block;
+  a.unit_t0 = d.unit_t0;
+  a.unit_t1 = d.unit_t1;
+  a.unit_slot = d.unit_slot;
+  a.n_units = d.n_units;
+  a.scratch = d.scratch;
   a.B = da.B;
   a.ldb = da.ldb;
   a.C = da.C;
@@ -419,13 +492,27 @@ cudaError_t launch_bcsr(const loops_plan_s* p, const BcsrDev& d, const DenseArgs
   a.N = da.N;
   a.n_rows = da.n_rows;
   a.err = p->d_error;
+  cudaError_t e = cudaErrorInvalidValue;
   switch (p->dtype) {
-    case LOOPS_F64: return launch_dmma(a, s);
-    case LOOPS_F32: return p->br == 8 ? launch_ffma_br<8>(a, s) : launch_ffma_br<16>(a, s);
-    case LOOPS_F16: return launch_hmma<__half>(a, s);
-    case LOOPS_BF16: return launch_hmma<__nv_bfloat16>(a, s);
+    case LOOPS_F64: e = launch_dmma(a, s); break;
+    case LOOPS_F32: e = p->br == 8 ? launch_ffma_br<8>(a, s) : launch_ffma_br<16>(a, s); break;
+    case LOOPS_F16: e = launch_hmma<__half>(a, s); break;
+    case LOOPS_BF16: e = launch_hmma<__nv_bfloat16>(a, s); break;
   }
-  return cudaErrorInvalidValue;
+  if (e != cudaSuccess || d.n_split == 0) return e;
+  dim3 grid((unsigned)d.n_split, (unsigned)std::min<int64_t>((p->br * a.N + 255) / 256, 64));
+  switch (p->dtype) {
+    case LOOPS_F64:
+      bcsr_split_reduce<double, double, false><<<grid, 256, 0, s>>>(d.split_block, d.split_slot_ptr, p->br, a);
+      break;
+    case LOOPS_F32:
+      bcsr_split_reduce<float, float, false><<<grid, 256, 0, s>>>(d.split_block, d.split_slot_ptr, p->br, a);
+      break;
+    default:
+      bcsr_split_reduce<float, float, true><<<grid, 256, 0, s>>>(d.split_block, d.split_slot_ptr, p->br, a);
+      break;
+  }
+  return cudaGetLastError();
 }
 
 }  // namespace loops

@@ -85,8 +85,23 @@ loops_status resolve_block_rows(loops_dtype dtype, const loops_plan_opts& o, int
   return LOOPS_OK;
 }
 
+void destroy_pipe(HostPipe* h) {
+  if (!h) return;
+  for (int i = 0; i < 2; ++i) {
+    if (h->B[i]) cudaFree(h->B[i]);
+    if (h->C[i]) cudaFree(h->C[i]);
+    cudaEvent_t evs[] = {h->in_done[i], h->compute_done[i], h->out_done[i]};
+    for (cudaEvent_t ev : evs)
+      if (ev) cudaEventDestroy(ev);
+  }
+  if (h->s_in) cudaStreamDestroy(h->s_in);
+  if (h->s_out) cudaStreamDestroy(h->s_out);
+  delete h;
+}
+
 void destroy_plan(loops_plan_s* p) {
   if (!p) return;
+  if (p->pipe) destroy_pipe(p->pipe);
   if (p->batch) destroy_batch(p->batch);
   if (p->transposed) destroy_plan(p->transposed);
   free_part(p->dev);
@@ -125,6 +140,7 @@ loops_status make_plan(const loops_csr* A, const double* vals, int64_t N, loops_
   p->ev_fork = p->ev_join = nullptr;
   p->stage_B = p->stage_C = nullptr;
   p->stage_B_bytes = p->stage_C_bytes = 0;
+  p->pipe = nullptr;
   p->timing = false;
   for (auto& ev : p->tev) ev = nullptr;
   p->batch = nullptr;
@@ -585,6 +601,69 @@ loops_status loops_spmm_host(loops_plan_t p, const void* B_host, int64_t ldb, vo
                           (size_t)p->n_rows, cudaMemcpyDeviceToHost, s);
   if (e != cudaSuccess) return cuda_status(e, "device-to-host copy");
   return cuda_status(cudaStreamSynchronize(s), "synchronize");
+}
+
+loops_status loops_spmm_host_async(loops_plan_t p, const void* B_host, int64_t ldb, void* C_host, int64_t ldc,
+                                   loops_stream_t stream) {
+  clear_error();
+  loops_status st = check_single(p);
+  if (st) return st;
+  if ((st = check_dense(B_host, p->n_cols, p->N, ldb, "B"))) return st;
+  if ((st = check_dense(C_host, p->n_rows, p->N, ldc, "C"))) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t eb = dense_elem_bytes(p->dtype), ec = out_elem_bytes(p->dtype);
+  const int64_t need_B = p->n_cols * p->N * eb, need_C = p->n_rows * p->N * ec;
+  cudaError_t e = cudaSuccess;
+  if (!p->pipe) {
+    HostPipe* h = new (std::nothrow) HostPipe();
+    if (!h) { set_error("host allocation failed"); return LOOPS_ERR_OOM; }
+    e = cudaStreamCreateWithFlags(&h->s_in, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->s_out, cudaStreamNonBlocking);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+      e = cudaEventCreateWithFlags(&h->in_done[i], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->compute_done[i], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->out_done[i], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaMalloc(&h->B[i], (size_t)std::max<int64_t>(need_B, 16));
+      if (e == cudaSuccess) e = cudaMalloc(&h->C[i], (size_t)std::max<int64_t>(need_C, 16));
+    }
+    if (e != cudaSuccess) { destroy_pipe(h); return cuda_status(e, "host pipeline setup"); }
+    h->B_bytes = need_B;
+    h->C_bytes = need_C;
+    p->pipe = h;
+  }
+  HostPipe* h = p->pipe;
+  const int i = h->next;
+  h->next ^= 1;
+  // copy in: after the call that last used this buffer set has finished reading it
+  if (h->used[i]) e = cudaStreamWaitEvent(h->s_in, h->compute_done[i], 0);
+  if (e == cudaSuccess && need_B) {
+    if (ldb == p->N)
+      e = cudaMemcpyAsync(h->B[i], B_host, (size_t)need_B, cudaMemcpyHostToDevice, h->s_in);
+    else
+      e = cudaMemcpy2DAsync(h->B[i], (size_t)(p->N * eb), B_host, (size_t)(ldb * eb), (size_t)(p->N * eb),
+                            (size_t)p->n_cols, cudaMemcpyHostToDevice, h->s_in);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(h->in_done[i], h->s_in);
+  // compute on the caller's stream once B is in and the previous copy-out of this C set is done
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->in_done[i], 0);
+  if (e == cudaSuccess && h->used[i]) e = cudaStreamWaitEvent(s, h->out_done[i], 0);
+  if (e != cudaSuccess) return cuda_status(e, "host pipeline");
+  if ((st = run_spmm(p, h->B[i], p->N, nullptr, h->C[i], p->N, s))) return st;
+  e = cudaEventRecord(h->compute_done[i], s);
+  // copy out on its own stream; the caller's stream then waits for it, so synchronising the
+  // caller's stream completes this call (the next call's copy-in overlaps this copy-out)
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->s_out, h->compute_done[i], 0);
+  if (e == cudaSuccess && need_C) {
+    if (ldc == p->N)
+      e = cudaMemcpyAsync(C_host, h->C[i], (size_t)need_C, cudaMemcpyDeviceToHost, h->s_out);
+    else
+      e = cudaMemcpy2DAsync(C_host, (size_t)(ldc * ec), h->C[i], (size_t)(p->N * ec), (size_t)(p->N * ec),
+                            (size_t)p->n_rows, cudaMemcpyDeviceToHost, h->s_out);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(h->out_done[i], h->s_out);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->out_done[i], 0);
+  h->used[i] = true;
+  return cuda_status(e, "host pipeline");
 }
 
 loops_status loops_spmm_backward(loops_plan_t p, const void* dC, int64_t lddc, const void* B, int64_t ldb,

@@ -13,6 +13,15 @@
 #include "device_common.cuh"
 #include "loops_internal.h"
 
+// Tuning knobs of the memory-bound (non-FP64) CSR kernel: B-row loads kept in flight per
+// lane, and the minimum resident blocks per SM the register allocation must allow.
+#ifndef LOOPS_CSR_UNROLL
+#define LOOPS_CSR_UNROLL 4
+#endif
+#ifndef LOOPS_CSR_MIN_BLOCKS
+#define LOOPS_CSR_MIN_BLOCKS 4
+#endif
+
 namespace loops {
 
 namespace {
@@ -51,7 +60,7 @@ __device__ __forceinline__ float out_scale<TrBF16>(const CsrKArgs& a, int64_t n)
 
 // Vector path: N % VE == 0, B/C/ld aligned for 16-byte B loads and vector C stores.
 template <class Tr, int G, int VPL, int U>
-__global__ void __launch_bounds__(256) csr_spmm_vec(CsrKArgs a) {
+__global__ void __launch_bounds__(256, LOOPS_CSR_MIN_BLOCKS) csr_spmm_vec(CsrKArgs a) {
   using TB = typename Tr::TB;
   using TAcc = typename Tr::TAcc;
   using TC = typename Tr::TC;
@@ -250,7 +259,7 @@ cudaError_t launch_vec_g(const CsrKArgs& a, cudaStream_t s) {
   // F64 is bound by the FP64 pipe: one entry at a time, so no FMA is ever spent on a padded
   // slot (a predicated-off DFMA still occupies the pipe) and registers stay low for occupancy.
   // The other formats are bound by memory: U loads in flight per lane.
-  constexpr int U = std::is_same<Tr, TrF64>::value ? 1 : ((G >= 8) ? 8 : 4);
+  constexpr int U = std::is_same<Tr, TrF64>::value ? 1 : ((G >= 8) ? LOOPS_CSR_UNROLL : 4);
   csr_spmm_vec<Tr, G, VPL, U><<<grid, 256, 0, s>>>(a);
   return cudaGetLastError();
 }

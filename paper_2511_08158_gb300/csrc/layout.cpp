@@ -180,16 +180,51 @@ loops_status upload_part(loops_plan_s* p, int64_t N) {
       for (int32_t r = 0; r < c.br; ++r)
         fv[(size_t)frag_index(p->dtype, t, r, c.br)] = c.tile_val[(size_t)(t * c.br + r)];
     encode_values(fv.data(), fv.size(), p->dtype, enc);
-    std::vector<int32_t> order((size_t)n_rb);
-    for (int64_t b = 0; b < n_rb; ++b) order[(size_t)b] = (int32_t)b;
-    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
-      return c.rb_ptr[(size_t)a + 1] - c.rb_ptr[(size_t)a] > c.rb_ptr[(size_t)b + 1] - c.rb_ptr[(size_t)b];
-    });
+    // work units: blocks with more than kBcsrSplitTiles tiles are cut (a multiple of the K)
+    struct Unit { int32_t b; int64_t t0, t1; int32_t slot; };
+    std::vector<Unit> units;
+    std::vector<int32_t> split_block, split_slot_ptr;
+    int64_t n_bslots = 0;
+    for (int64_t b = 0; b < n_rb; ++b) {
+      const int64_t t0 = c.rb_ptr[(size_t)b], t1 = c.rb_ptr[(size_t)b + 1];
+      if (t1 - t0 > kBcsrSplitTiles) {
+        split_block.push_back((int32_t)b);
+        split_slot_ptr.push_back((int32_t)n_bslots);
+        for (int64_t t = t0; t < t1; t += kBcsrSplitTiles)
+          units.push_back({(int32_t)b, t, std::min(t + kBcsrSplitTiles, t1), (int32_t)n_bslots++});
+      } else {
+        units.push_back({(int32_t)b, t0, t1, -1});
+      }
+    }
+    split_slot_ptr.push_back((int32_t)n_bslots);
+    std::stable_sort(units.begin(), units.end(), [](const Unit& x, const Unit& y) { return x.t1 - x.t0 > y.t1 - y.t0; });
+    std::vector<int32_t> ub(units.size()), us(units.size());
+    std::vector<int64_t> u0(units.size()), u1(units.size());
+    d.bcsr.h_unit_tiles.resize(units.size());
+    for (size_t i = 0; i < units.size(); ++i) {
+      ub[i] = units[i].b;
+      u0[i] = units[i].t0;
+      u1[i] = units[i].t1;
+      us[i] = units[i].slot;
+      d.bcsr.h_unit_tiles[i] = units[i].t1 - units[i].t0;
+    }
+    d.bcsr.n_units = (int64_t)units.size();
+    d.bcsr.n_split = (int64_t)split_block.size();
+    d.bcsr.n_slots = n_bslots;
     if ((st = dev_upload(&d.bcsr.rb_id, c.rb_ids.data(), (size_t)n_rb, bytes))) return st;
     if ((st = dev_upload(&d.bcsr.rb_ptr, c.rb_ptr.data(), (size_t)n_rb + 1, bytes))) return st;
     if ((st = dev_upload(&d.bcsr.tile_col, c.tile_col.data(), (size_t)n_t, bytes))) return st;
     if ((st = dev_upload((uint8_t**)&d.bcsr.tile_val, enc.data(), enc.size(), bytes))) return st;
-    if ((st = dev_upload(&d.bcsr.order, order.data(), order.size(), bytes))) return st;
+    if ((st = dev_upload(&d.bcsr.unit_block, ub.data(), ub.size(), bytes))) return st;
+    if ((st = dev_upload(&d.bcsr.unit_t0, u0.data(), u0.size(), bytes))) return st;
+    if ((st = dev_upload(&d.bcsr.unit_t1, u1.data(), u1.size(), bytes))) return st;
+    if ((st = dev_upload(&d.bcsr.unit_slot, us.data(), us.size(), bytes))) return st;
+    if (n_bslots) {
+      if ((st = dev_upload(&d.bcsr.split_block, split_block.data(), split_block.size(), bytes))) return st;
+      if ((st = dev_upload(&d.bcsr.split_slot_ptr, split_slot_ptr.data(), split_slot_ptr.size(), bytes))) return st;
+      if ((st = dev_upload((uint8_t**)&d.bcsr.scratch, (const uint8_t*)nullptr,
+                           (size_t)(n_bslots * c.br * std::max<int64_t>(N, 1) * acc_bytes), bytes))) return st;
+    }
   }
   return LOOPS_OK;
 }
@@ -197,7 +232,9 @@ loops_status upload_part(loops_plan_s* p, int64_t N) {
 void free_part(PartDev& d) {
   void* ptrs[] = {d.csr.item_row, d.csr.item_ptr, d.csr.col, d.csr.val, d.csr.split_row,
                   d.csr.split_slot_ptr, d.csr.scratch, d.bcsr.rb_id, d.bcsr.rb_ptr,
-                  d.bcsr.tile_col, d.bcsr.tile_val, d.bcsr.order};
+                  d.bcsr.tile_col, d.bcsr.tile_val, d.bcsr.unit_block, d.bcsr.unit_t0,
+                  d.bcsr.unit_t1, d.bcsr.unit_slot, d.bcsr.split_block, d.bcsr.split_slot_ptr,
+                  d.bcsr.scratch};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   d = PartDev();

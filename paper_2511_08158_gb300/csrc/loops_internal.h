@@ -96,13 +96,26 @@ struct CsrDev {
 
 // BCSR part: block b has tiles [rb_ptr[b], rb_ptr[b+1]) (a multiple of k_pad), global row
 // block id rb_id[b]. tile_val is stored in the MMA fragment order of the dtype's kernel.
+// Work units (longest first) cover a block's tiles [unit_t0, unit_t1); a block with more than
+// kBcsrSplitTiles tiles is cut into several units whose partial sums (B_r x N accumulators,
+// slot unit_slot) are added in slot order by a second kernel; unit_slot -1 writes C directly.
+constexpr int64_t kBcsrSplitTiles = 256;
 struct BcsrDev {
   int64_t n_rb = 0, n_tiles = 0;
   int32_t* rb_id = nullptr;
   int64_t* rb_ptr = nullptr;
   int32_t* tile_col = nullptr;
   void* tile_val = nullptr;
-  int32_t* order = nullptr;            // processing order of blocks (most tiles first)
+  int64_t n_units = 0;
+  int32_t* unit_block = nullptr;
+  int64_t* unit_t0 = nullptr;
+  int64_t* unit_t1 = nullptr;
+  int32_t* unit_slot = nullptr;
+  int64_t n_split = 0, n_slots = 0;
+  int32_t* split_block = nullptr;      // block index of each block cut into units
+  int32_t* split_slot_ptr = nullptr;   // size n_split + 1
+  void* scratch = nullptr;             // n_slots x B_r x N accumulators
+  std::vector<int64_t> h_unit_tiles;   // tiles per unit (host, for batched task costs)
 };
 
 struct PartDev {
@@ -142,7 +155,14 @@ struct BatchDesc {
   const int64_t* rb_ptr;
   const int32_t* tile_col;
   const void* tile_val;
-  const int32_t* order;
+  const int32_t* unit_block;
+  const int64_t* unit_t0;
+  const int64_t* unit_t1;
+  const int32_t* unit_slot;
+  void* bscratch;
+  const int32_t* bsplit_block;
+  const int32_t* bsplit_slot_ptr;
+  int32_t br;
   void* scratch;
   const int32_t* split_row;
   const int32_t* split_slot_ptr;
@@ -155,7 +175,7 @@ struct BatchDesc {
 };
 
 // One task of the persistent batched kernel: kind 0 CSR items [first, first + count) of
-// matrix m, kind 1 F32 row blocks (positions in the block order), kind 2 one F16/BF16 block.
+// matrix m, kind 1 F32 BCSR units [first, first + count), kind 2 one F16/BF16 BCSR unit.
 struct BatchTask {
   int32_t m;
   int32_t kind;
@@ -170,11 +190,26 @@ struct BatchLaunch {
   int64_t n_tasks;
   const int2* splits;                  // (matrix, split row) pairs
   int64_t n_splits;
+  const int2* bsplits;                 // (matrix, split block) pairs
+  int64_t n_bsplits;
   int grid;
   int smem_per_warp;
 };
 
 struct BatchState;
+
+// Double-buffered host pipeline of loops_spmm_host_async.
+struct HostPipe {
+  void* B[2] = {nullptr, nullptr};
+  void* C[2] = {nullptr, nullptr};
+  int64_t B_bytes = 0, C_bytes = 0;
+  cudaStream_t s_in = nullptr, s_out = nullptr;
+  cudaEvent_t in_done[2] = {nullptr, nullptr}, compute_done[2] = {nullptr, nullptr},
+              out_done[2] = {nullptr, nullptr};
+  bool used[2] = {false, false};
+  int next = 0;
+};
+void destroy_pipe(HostPipe* h);
 
 }  // namespace loops
 
@@ -200,6 +235,7 @@ struct loops_plan_s {
   void* stage_B;                       // loops_spmm_host staging buffers
   void* stage_C;
   int64_t stage_B_bytes, stage_C_bytes;
+  loops::HostPipe* pipe;               // loops_spmm_host_async state (lazily created)
   int64_t n_subnormal;
   int64_t nnz_bcsr;
   cudaEvent_t tev[4];                  // optional caller-owned timing events (may be null)

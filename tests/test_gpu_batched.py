@@ -109,3 +109,16 @@ def test_batched_rejects_unsupported_n(lp):
         lp.BatchedPlan([A], [6], "f32", tau=2.0)
     with pytest.raises(lp.LoopsError):
         lp.BatchedPlan([A], [32], "f64", tau=2.0)
+
+
+def test_batched_blocks_cut_into_units(lp):
+    rng = np.random.default_rng(11)
+    mats = []
+    for m, N in enumerate((16, 32, 64)):
+        n = 800
+        rows = np.concatenate([np.repeat(np.arange(32, 48), 400), rng.integers(0, n, 2000)])
+        cols = np.concatenate([rng.integers(0, 600, 16 * 400), rng.integers(0, n, 2000)])
+        mats.append((W.csr_from_coo(n, n, rows, cols, rng.standard_normal(rows.size)), N))
+    for fmt in ("f32", "bf16"):
+        _, _, _, _, errs = _run(lp, mats, fmt, 0.0)
+        assert max(errs) <= TOL[fmt], errs

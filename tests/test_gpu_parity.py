@@ -169,3 +169,31 @@ def test_contiguous_paper_split(lp):
         plan = lp.Plan(A, 32, "f64", contiguous_split=True, r_boundary=rb)
         C = plan.spmm(to_device(torch, Bg, "f64")).cpu().numpy()
         assert rel_l2(C, oracle.spmm(A_r, B_eff)) <= TOL["f64"]
+
+
+@pytest.mark.parametrize("fmt", FMTS)
+def test_blocks_cut_into_units(lp, fmt):
+    # a row block whose rows touch ~700 distinct columns: more tiles than one work unit takes,
+    # so the block is cut into units whose partial sums are added in order
+    n = 1000
+    rng = np.random.default_rng(3)
+    rows = np.concatenate([np.repeat(np.arange(16, 32), 500), rng.integers(0, n, 3000)])
+    cols = np.concatenate([rng.integers(0, 700, 16 * 500), rng.integers(0, n, 3000)])
+    A = W.csr_from_coo(n, n, rows, cols, rng.standard_normal(rows.size))
+    B = W.dense_normal(n, 40, 4)
+    for tau in (0.0, 1.5):
+        C, ref, plan = run_case(lp, A, B, fmt, tau)
+        assert rel_l2(C, ref) <= TOL[fmt]
+        assert plan.info()["n_tiles"] > 256
+
+
+def test_spmm_host_async_pipeline(lp):
+    A, _ = W.uniform_rows(3000, 12, 16, seed=2)
+    plan = lp.Plan(A, 16, "f64", tau=2.0)
+    Bs = [torch.as_tensor(W.dense_normal(3000, 16, 30 + k)).pin_memory() for k in range(5)]
+    Cs = [torch.full((3000, 16), float("nan"), dtype=torch.float64).pin_memory() for _ in range(5)]
+    for B, C in zip(Bs, Cs):
+        plan.spmm_host_async(B, C)
+    torch.cuda.synchronize()
+    for B, C in zip(Bs, Cs):
+        assert rel_l2(C.numpy(), oracle.spmm(A, B.numpy())) <= TOL["f64"]
