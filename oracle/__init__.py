@@ -69,11 +69,11 @@ def _load():
                                             _f64p, _f64p]
             L.oracle_partition_sizes.argtypes = [ctypes.c_int64, _i64p, _i32p, ctypes.c_int64,
                                                  ctypes.c_int64, ctypes.c_double, ctypes.c_int,
-                                                 ctypes.c_int64, _i64p]
+                                                 ctypes.c_int64, ctypes.c_int64, _i64p]
             L.oracle_partition_fill.argtypes = [ctypes.c_int64, _i64p, _i32p, _f64p, ctypes.c_int64,
                                                 ctypes.c_int64, ctypes.c_double, ctypes.c_int,
-                                                ctypes.c_int64, _i32p, _i64p, _i32p, _f64p, _i32p,
-                                                _i64p, _i32p, _f64p]
+                                                ctypes.c_int64, ctypes.c_int64, _i32p, _i64p, _i32p, _f64p,
+                                                _i32p, _i64p, _i32p, _f64p]
             for f in (L.oracle_partition_sizes, L.oracle_partition_fill):
                 f.restype = ctypes.c_int
     return _lib
@@ -225,17 +225,18 @@ def default_block_rows(fmt: str) -> int:
 
 
 def partition(A, fmt: str = "f64", block_rows: int | None = None, k_pad: int = 1,
-              tau: float = 2.0, contiguous: bool = False, r_boundary: int = 0) -> dict:
+              tau: float = 2.0, contiguous: bool = False, r_boundary: int = 0, tile_min: int = 0) -> dict:
     """Algorithm 1 with the structural split (see ``loops_oracle.c``). Returns the canonical
     partition: csr_rows, csr_ptr, csr_col, csr_val, rb_ids, rb_ptr, tile_col, tile_val
     (tile_val shaped [n_tiles, B_r]); values rounded once into ``fmt`` after the plan scale
-    s_A (returned as 'scale', values are stored as round(s_A * a))."""
+    s_A (returned as 'scale', values are stored as round(s_A * a)). tile_min > 1 keeps only
+    tiles with at least tile_min stored entries in BCSR blocks; the rest go to the CSR part."""
     L = _load()
     br = default_block_rows(fmt) if block_rows is None else int(block_rows)
     rp, ci, v = _csr_arrays(A)
     sz = np.zeros(4, dtype=np.int64)
     L.oracle_partition_sizes(A.n_rows, _p(rp, _i64p), _p(ci, _i32p), br, int(k_pad), float(tau),
-                             int(contiguous), int(r_boundary), _p(sz, _i64p))
+                             int(contiguous), int(r_boundary), int(tile_min), _p(sz, _i64p))
     n_csr, nnz_csr, n_rb, n_t = (int(x) for x in sz)
     out = dict(
         csr_rows=np.zeros(n_csr, np.int32), csr_ptr=np.zeros(n_csr + 1, np.int64),
@@ -243,7 +244,7 @@ def partition(A, fmt: str = "f64", block_rows: int | None = None, k_pad: int = 1
         rb_ids=np.zeros(n_rb, np.int32), rb_ptr=np.zeros(n_rb + 1, np.int64),
         tile_col=np.zeros(n_t, np.int32), tile_val=np.zeros(n_t * br, np.float64))
     L.oracle_partition_fill(A.n_rows, _p(rp, _i64p), _p(ci, _i32p), _p(v, _f64p), br, int(k_pad),
-                            float(tau), int(contiguous), int(r_boundary),
+                            float(tau), int(contiguous), int(r_boundary), int(tile_min),
                             _p(out["csr_rows"], _i32p), _p(out["csr_ptr"], _i64p),
                             _p(out["csr_col"], _i32p), _p(out["csr_val"], _f64p),
                             _p(out["rb_ids"], _i32p), _p(out["rb_ptr"], _i64p),
@@ -284,17 +285,21 @@ def expand_partition(part: dict, n_rows: int, n_cols: int) -> np.ndarray:
 def spmm_partitioned(part: dict, n_rows: int, B: np.ndarray) -> np.ndarray:
     """C computed part by part from a partition (CSR rows by the inner product, BCSR blocks
     by rank-1 tile updates acc += a_tile (B_r x 1) * B[col, :], Algorithm 2), with values
-    divided back by the plan scale. Used to pin the partition invariant."""
+    divided back by the plan scale; a row present in both parts gets both contributions. Rows
+    covered by neither part stay NaN, so a coverage gap shows. Used to pin the partition
+    invariant."""
     B = np.asarray(B, dtype=np.float64)
     N = B.shape[1]
     br = part["block_rows"]
     s = part["scale"]
-    C = np.full((n_rows, N), np.nan)
+    C = np.zeros((n_rows, N))
+    covered = np.zeros(n_rows, dtype=bool)
     for x, i in enumerate(part["csr_rows"]):
         acc = np.zeros(N)
         for k in range(part["csr_ptr"][x], part["csr_ptr"][x + 1]):
             acc += (part["csr_val"][k] / s) * B[part["csr_col"][k]]
-        C[i] = acc
+        C[i] += acc
+        covered[i] = True
     for x, b in enumerate(part["rb_ids"]):
         acc = np.zeros((br, N))
         for t in range(part["rb_ptr"][x], part["rb_ptr"][x + 1]):
@@ -304,5 +309,7 @@ def spmm_partitioned(part: dict, n_rows: int, B: np.ndarray) -> np.ndarray:
             acc += np.outer(part["tile_val"][t] / s, B[c])
         r0 = int(b) * br
         r1 = min(r0 + br, n_rows)
-        C[r0:r1] = acc[: r1 - r0]
+        C[r0:r1] += acc[: r1 - r0]
+        covered[r0:r1] = True
+    C[~covered] = np.nan
     return C

@@ -154,93 +154,130 @@ static int64_t oracle_block_kinds(int64_t n_rows, const int64_t* row_ptr, const 
   return n_blocks;
 }
 
+/* One pass of Algorithm 1 over the row blocks. With out_sizes it only counts; otherwise it
+ * fills the arrays. tile_min > 1 keeps in a BCSR block only the tiles holding at least
+ * tile_min stored entries; the entries of the other tiles become CSR-part entries of their
+ * rows (in input order), and a block left with no tile is entirely CSR. */
+static int oracle_partition_run(int64_t n_rows, const int64_t* row_ptr, const int32_t* col_idx,
+                                const double* vals, int64_t block_rows, int64_t k_pad, double tau,
+                                int contiguous, int64_t r_boundary, int64_t tile_min, int64_t* out_sizes,
+                                int32_t* csr_rows, int64_t* csr_ptr, int32_t* csr_col, double* csr_val,
+                                int32_t* rb_ids, int64_t* rb_ptr, int32_t* tile_col, double* tile_val) {
+  const int fill = out_sizes == NULL;
+  const int64_t n_blocks = (n_rows + block_rows - 1) / block_rows;
+  unsigned char* kind = (unsigned char*)malloc((size_t)(n_blocks > 0 ? n_blocks : 1));
+  oracle_block_kinds(n_rows, row_ptr, col_idx, block_rows, tau, contiguous, r_boundary, kind);
+  int64_t rc = 0, kc = 0, rbc = 0, tc = 0;
+  if (fill) { csr_ptr[0] = 0; rb_ptr[0] = 0; }
+  for (int64_t b = 0; b < n_blocks; ++b) {
+    const int64_t i0 = b * block_rows;
+    const int64_t i1 = (i0 + block_rows < n_rows) ? i0 + block_rows : n_rows;
+    const int64_t m = row_ptr[i1] - row_ptr[i0];
+    unsigned char* moved = (unsigned char*)calloc((size_t)(m > 0 ? m : 1), 1);
+    int64_t n_keep = 0;
+    oracle_entry* e = NULL;
+    if (kind[b]) {
+      /* Step 2: group the block's entries into B_r x 1 tiles keyed by column */
+      e = (oracle_entry*)malloc((size_t)(m > 0 ? m : 1) * sizeof(oracle_entry));
+      int64_t x = 0;
+      for (int64_t i = i0; i < i1; ++i)
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) { e[x].col = col_idx[k]; e[x].r = (int32_t)(i - i0); e[x].k = k; ++x; }
+      qsort(e, (size_t)m, sizeof(oracle_entry), oracle_entry_cmp);
+      for (int64_t y = 0; y < m;) {
+        int64_t z = y;
+        while (z < m && e[z].col == e[y].col) ++z;
+        if (tile_min > 1 && z - y < tile_min) {
+          for (int64_t w = y; w < z; ++w) moved[e[w].k - row_ptr[i0]] = 1;
+        } else {
+          ++n_keep;
+        }
+        y = z;
+      }
+      if (n_keep == 0) {            /* nothing left for BCSR: the whole block is CSR */
+        for (int64_t w = 0; w < m; ++w) moved[w] = 0;
+      }
+    }
+    if (!kind[b] || n_keep == 0) {
+      /* Step 1: copy the rows into the CSR part, preserving their structure */
+      for (int64_t i = i0; i < i1; ++i) {
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+          if (fill) { csr_col[kc] = col_idx[k]; csr_val[kc] = vals[k]; }
+          ++kc;
+        }
+        if (fill) { csr_rows[rc] = (int32_t)i; csr_ptr[rc + 1] = kc; }
+        ++rc;
+      }
+    } else {
+      /* entries of dropped tiles: CSR-part rows, entries in input order */
+      for (int64_t i = i0; i < i1; ++i) {
+        int64_t any = 0;
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+          if (!moved[k - row_ptr[i0]]) continue;
+          if (fill) { csr_col[kc] = col_idx[k]; csr_val[kc] = vals[k]; }
+          ++kc;
+          any = 1;
+        }
+        if (any) {
+          if (fill) { csr_rows[rc] = (int32_t)i; csr_ptr[rc + 1] = kc; }
+          ++rc;
+        }
+      }
+      /* kept tiles, ascending by column, duplicates summed in input order, then padding */
+      const int64_t t_begin = tc;
+      int32_t last_col = 0;
+      for (int64_t y = 0; y < m; ++y) {
+        if (moved[e[y].k - row_ptr[i0]]) continue;
+        if (tc == t_begin || e[y].col != last_col) {
+          last_col = e[y].col;
+          if (fill) {
+            tile_col[tc] = e[y].col;
+            for (int64_t r = 0; r < block_rows; ++r) tile_val[tc * block_rows + r] = 0.0;
+          }
+          ++tc;
+        }
+        if (fill) tile_val[(tc - 1) * block_rows + e[y].r] += vals[e[y].k];
+      }
+      const int64_t t_real = tc - t_begin;
+      const int64_t t_pad = (t_real + k_pad - 1) / k_pad * k_pad;
+      for (int64_t p = t_real; p < t_pad; ++p) {
+        if (fill) {
+          tile_col[tc] = -1;
+          for (int64_t r = 0; r < block_rows; ++r) tile_val[tc * block_rows + r] = 0.0;
+        }
+        ++tc;
+      }
+      if (fill) { rb_ids[rbc] = (int32_t)b; rb_ptr[rbc + 1] = tc; }
+      ++rbc;
+    }
+    free(e);
+    free(moved);
+  }
+  free(kind);
+  if (!fill) { out_sizes[0] = rc; out_sizes[1] = kc; out_sizes[2] = rbc; out_sizes[3] = tc; }
+  return 0;
+}
+
 /* out[0] = CSR-part rows, out[1] = CSR-part nnz, out[2] = BCSR row blocks, out[3] = BCSR tiles
  * (padding included). Returns 0. */
 int oracle_partition_sizes(int64_t n_rows, const int64_t* row_ptr, const int32_t* col_idx,
                            int64_t block_rows, int64_t k_pad, double tau, int contiguous,
-                           int64_t r_boundary, int64_t* out) {
-  const int64_t n_blocks = (n_rows + block_rows - 1) / block_rows;
-  unsigned char* kind = (unsigned char*)malloc((size_t)(n_blocks > 0 ? n_blocks : 1));
-  oracle_block_kinds(n_rows, row_ptr, col_idx, block_rows, tau, contiguous, r_boundary, kind);
-  int64_t n_csr = 0, nnz_csr = 0, n_rb = 0, n_tiles = 0;
-  for (int64_t b = 0; b < n_blocks; ++b) {
-    const int64_t i0 = b * block_rows;
-    const int64_t i1 = (i0 + block_rows < n_rows) ? i0 + block_rows : n_rows;
-    if (!kind[b]) { n_csr += i1 - i0; nnz_csr += row_ptr[i1] - row_ptr[i0]; continue; }
-    ++n_rb;
-    const int64_t m = row_ptr[i1] - row_ptr[i0];
-    oracle_entry* e = (oracle_entry*)malloc((size_t)(m > 0 ? m : 1) * sizeof(oracle_entry));
-    int64_t x = 0;
-    for (int64_t i = i0; i < i1; ++i)
-      for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) { e[x].col = col_idx[k]; e[x].r = (int32_t)(i - i0); e[x].k = k; ++x; }
-    qsort(e, (size_t)m, sizeof(oracle_entry), oracle_entry_cmp);
-    int64_t t = 0;
-    for (int64_t y = 0; y < m; ++y) if (y == 0 || e[y].col != e[y - 1].col) ++t;
-    free(e);
-    n_tiles += (t + k_pad - 1) / k_pad * k_pad;
-  }
-  free(kind);
-  out[0] = n_csr; out[1] = nnz_csr; out[2] = n_rb; out[3] = n_tiles;
-  return 0;
+                           int64_t r_boundary, int64_t tile_min, int64_t* out) {
+  return oracle_partition_run(n_rows, row_ptr, col_idx, NULL, block_rows, k_pad, tau, contiguous, r_boundary,
+                              tile_min, out, NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL);
 }
 
 /* Fill the canonical partition. Arrays sized by oracle_partition_sizes:
  *   csr_rows[n_csr], csr_ptr[n_csr + 1], csr_col[nnz_csr], csr_val[nnz_csr]
  *   rb_ids[n_rb], rb_ptr[n_rb + 1], tile_col[n_tiles], tile_val[n_tiles * block_rows]
  * tile_val[t * B_r + r] holds the value of row (rb_id * B_r + r) in tile t (Algorithm 1 offset
- * (i mod B_r) * B_c + (j mod B_c) with B_c = 1). Values are the f64 sums of the input values. */
+ * (i mod B_r) * B_c + (j mod B_c) with B_c = 1). Values are the f64 sums of the input values.
+ * With tile_min > 1 a CSR-part row may also lie in a BCSR block (its remaining entries). */
 int oracle_partition_fill(int64_t n_rows, const int64_t* row_ptr, const int32_t* col_idx,
                           const double* vals, int64_t block_rows, int64_t k_pad, double tau,
-                          int contiguous, int64_t r_boundary, int32_t* csr_rows, int64_t* csr_ptr,
-                          int32_t* csr_col, double* csr_val, int32_t* rb_ids, int64_t* rb_ptr,
-                          int32_t* tile_col, double* tile_val) {
-  const int64_t n_blocks = (n_rows + block_rows - 1) / block_rows;
-  unsigned char* kind = (unsigned char*)malloc((size_t)(n_blocks > 0 ? n_blocks : 1));
-  oracle_block_kinds(n_rows, row_ptr, col_idx, block_rows, tau, contiguous, r_boundary, kind);
-  int64_t rc = 0, kc = 0, rbc = 0, tc = 0;
-  csr_ptr[0] = 0;
-  rb_ptr[0] = 0;
-  for (int64_t b = 0; b < n_blocks; ++b) {
-    const int64_t i0 = b * block_rows;
-    const int64_t i1 = (i0 + block_rows < n_rows) ? i0 + block_rows : n_rows;
-    if (!kind[b]) {
-      /* Step 1: copy the rows into the CSR part, preserving their structure. */
-      for (int64_t i = i0; i < i1; ++i) {
-        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) { csr_col[kc] = col_idx[k]; csr_val[kc] = vals[k]; ++kc; }
-        csr_rows[rc] = (int32_t)i;
-        csr_ptr[rc + 1] = kc;
-        ++rc;
-      }
-      continue;
-    }
-    /* Step 2: group the block's entries into B_r x 1 tiles keyed by column. */
-    const int64_t m = row_ptr[i1] - row_ptr[i0];
-    oracle_entry* e = (oracle_entry*)malloc((size_t)(m > 0 ? m : 1) * sizeof(oracle_entry));
-    int64_t x = 0;
-    for (int64_t i = i0; i < i1; ++i)
-      for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) { e[x].col = col_idx[k]; e[x].r = (int32_t)(i - i0); e[x].k = k; ++x; }
-    qsort(e, (size_t)m, sizeof(oracle_entry), oracle_entry_cmp);
-    const int64_t t_begin = tc;
-    for (int64_t y = 0; y < m; ++y) {
-      if (y == 0 || e[y].col != e[y - 1].col) {
-        tile_col[tc] = e[y].col;
-        for (int64_t r = 0; r < block_rows; ++r) tile_val[tc * block_rows + r] = 0.0;
-        ++tc;
-      }
-      tile_val[(tc - 1) * block_rows + e[y].r] += vals[e[y].k];
-    }
-    free(e);
-    const int64_t t_real = tc - t_begin;
-    const int64_t t_pad = (t_real + k_pad - 1) / k_pad * k_pad;
-    for (int64_t p = t_real; p < t_pad; ++p) {
-      tile_col[tc] = -1;
-      for (int64_t r = 0; r < block_rows; ++r) tile_val[tc * block_rows + r] = 0.0;
-      ++tc;
-    }
-    rb_ids[rbc] = (int32_t)b;
-    rb_ptr[rbc + 1] = tc;
-    ++rbc;
-  }
-  free(kind);
-  return 0;
+                          int contiguous, int64_t r_boundary, int64_t tile_min, int32_t* csr_rows,
+                          int64_t* csr_ptr, int32_t* csr_col, double* csr_val, int32_t* rb_ids,
+                          int64_t* rb_ptr, int32_t* tile_col, double* tile_val) {
+  return oracle_partition_run(n_rows, row_ptr, col_idx, vals, block_rows, k_pad, tau, contiguous, r_boundary,
+                              tile_min, NULL, csr_rows, csr_ptr, csr_col, csr_val, rb_ids, rb_ptr, tile_col,
+                              tile_val);
 }

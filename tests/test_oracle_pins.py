@@ -187,24 +187,41 @@ def test_partition_hand_worked_example(golden_dir):
     part = oracle.partition(A, "f64", block_rows=c["block_rows"], k_pad=c["k_pad"], contiguous=True,
                             r_boundary=c["r_boundary"])
     _check_case(part, c)
+    c = g["tile_split"]
+    part = oracle.partition(A, "f64", block_rows=c["block_rows"], k_pad=c["k_pad"], tau=c["tau"],
+                            tile_min=c["tile_min"])
+    _check_case(part, c)
 
 
 @pytest.mark.parametrize("tau", [0.0, 1.0, 1.5, 2.0, 4.0, math.inf])
 @pytest.mark.parametrize("br,kpad", [(8, 4), (16, 16), (16, 1)])
-def test_partition_invariant_exact(tau, br, kpad):
+@pytest.mark.parametrize("tile_min", [0, 2, 3])
+def test_partition_invariant_exact(tau, br, kpad, tile_min):
     # any split: expanding the partition gives A back, and C from the parts equals C (exact)
     A = _int_csr(45, 40, 0.12, int(br + kpad), duplicates=True, unsorted=True, explicit_zeros=True)
     B = _int_dense(40, 5, 3)
-    part = oracle.partition(A, "f64", block_rows=br, k_pad=kpad, tau=tau)
+    part = oracle.partition(A, "f64", block_rows=br, k_pad=kpad, tau=tau, tile_min=tile_min)
     assert np.array_equal(oracle.expand_partition(part, A.n_rows, A.n_cols), A.to_dense())
     assert np.array_equal(oracle.spmm_partitioned(part, A.n_rows, B), oracle.spmm(A, B))
-    # structure: every row is in exactly one part; tiles per block are a multiple of k_pad
+    # structure: every row is covered; without the tile split each row is in exactly one
+    # part; kept tiles hold at least tile_min entries; tiles per block are a multiple of k_pad
     rows = set(int(r) for r in part["csr_rows"])
     for b in part["rb_ids"]:
         blk = set(range(int(b) * br, min(int(b) * br + br, A.n_rows)))
-        assert not (rows & blk)
+        if tile_min <= 1:
+            assert not (rows & blk)
         rows |= blk
     assert rows == set(range(A.n_rows))
+    if tile_min > 1:
+        D = A.to_dense()
+        for x, b in enumerate(part["rb_ids"]):
+            for t in range(part["rb_ptr"][x], part["rb_ptr"][x + 1]):
+                c = part["tile_col"][t]
+                if c >= 0:
+                    r0 = int(b) * br
+                    stored = sum(int(np.sum(A.col_idx[A.row_ptr[i]:A.row_ptr[i + 1]] == c))
+                                 for i in range(r0, min(r0 + br, A.n_rows)))
+                    assert stored >= tile_min
     assert np.all(np.diff(part["rb_ptr"]) % kpad == 0)
     if tau == math.inf:
         assert part["rb_ids"].size == 0
