@@ -280,8 +280,9 @@ def run_loops(args):
     plan = lp.Plan(A, N, "f64", tau=-1.0)           # autotuned split
     plan_s = time.perf_counter() - t0
     info = plan.info()
-    variants = {"csr_only": math.inf, "hybrid_tau2": 2.0, "bcsr_only": 0.0}
-    vplans = {k: lp.Plan(A, N, "f64", tau=t) for k, t in variants.items()}
+    variants = {"csr_only": (math.inf, 0), "hybrid_tau2": (2.0, 0), "hybrid_tau2_tile_split": (2.0, 2),
+                "bcsr_only": (0.0, 0)}
+    vplans = {k: lp.Plan(A, N, "f64", tau=t, tile_min=tm) for k, (t, tm) in variants.items()}
 
     # main timed region: K steps, barrier + synchronize on both sides
     sampler = ClockSampler(local)
@@ -310,7 +311,8 @@ def run_loops(args):
     for k, p in vplans.items():
         s, c, b = time_plan(torch, p, Bd, Cd, max(10, args.steps // 2), 3, flush)
         inf_ = p.info()
-        var_out[k] = {"tau": variants[k], "gflops": flops / (statistics.mean(s) * 1e-3) / 1e9,
+        var_out[k] = {"tau": variants[k][0], "tile_min": variants[k][1],
+                      "gflops": flops / (statistics.mean(s) * 1e-3) / 1e9,
                       "ms_per_step": statistics.mean(s), "bcsr_row_blocks": inf_["n_row_blocks"],
                       "bcsr_tiles": inf_["n_tiles"], "csr_ms": statistics.mean(c), "bcsr_ms": statistics.mean(b)}
     # restore the main plan's output for the parity check below
@@ -382,6 +384,7 @@ def run_loops(args):
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Laplacian + dense blocks, N(0,1) B)",
             "config": dict(config(N), parallelism=f"replicas{world}", tau_autotuned=info["tau"],
+                           tile_min_autotuned=info["tile_min"],
                            bcsr_row_blocks=info["n_row_blocks"], bcsr_tiles=info["n_tiles"],
                            plan_build_s=plan_s),
             "roofline": roofline, "hbm": hbm, "variants": var_out,

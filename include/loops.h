@@ -78,8 +78,16 @@ typedef struct {
  *      F16/BF16 need 16, F32 accepts 8 or 16.
  * contiguous_split: paper mode (Eq. 1, Algorithm 1): rows [0, r_boundary) rounded up to a
  *      multiple of B_r form the CSR part and every later row block is BCSR; tau ignored.
+ *      r_boundary < 0 derives it from Eq. 1: the all-CSR and all-BCSR plans are timed on the
+ *      plan's stream (synchronised), each part's throughput is TP = rows / time, and
+ *      r_boundary / TP_csr = (n_rows - r_boundary) / TP_bcsr balances the two parts' times.
  * want_backward: also build the transposed plan and keep A's pattern so that
- *      loops_spmm_backward works. */
+ *      loops_spmm_backward works.
+ * tile_min: tile-level split inside BCSR blocks (the dense/sparse-region idea the paper cites,
+ *      Sec. 5): tiles holding fewer than tile_min stored entries leave the block, and their
+ *      entries join the CSR part, whose rows then add to the C rows the BCSR part wrote
+ *      (after it, in a fixed order). 0 or 1: off; -1: the autotuner (tau < 0) also tries 2.
+ *      Not available together with want_backward or in batched plans. */
 typedef struct {
   double tau;
   int32_t block_rows;
@@ -87,7 +95,8 @@ typedef struct {
   int64_t r_boundary;
   int32_t want_backward;
   int32_t split_len;      /* CSR rows longer than this are split in segments; 0 = default */
-  int32_t reserved[6];
+  int32_t tile_min;
+  int32_t reserved[5];
 } loops_plan_opts;
 
 typedef struct loops_plan_s* loops_plan_t;
@@ -106,6 +115,8 @@ typedef struct {
   int64_t n_split_rows, n_segments;
   int64_t n_subnormal_vals;/* stored 16-bit A values that are subnormal */
   int64_t device_bytes;    /* device memory owned by the plan */
+  int64_t r_boundary;      /* paper mode: the boundary used (Eq. 1 when derived); else -1 */
+  int64_t tile_min;        /* tile-level split threshold in effect (0: off) */
 } loops_plan_info;
 
 /* Canonical partition (host arrays, malloc'ed by the library; release with
@@ -139,7 +150,8 @@ const char* loops_status_str(loops_status status);
 /* Thread-local message of the last failing call on this thread ("" if none). */
 const char* loops_last_error(void);
 
-/* Fill *opts with defaults: tau = 2.0, block_rows = 0, no contiguous split, no backward. */
+/* Fill *opts with defaults: tau = 2.0, block_rows = 0, no contiguous split, no backward,
+ * tile_min = -1 (tile split only considered when autotuning). */
 void loops_plan_opts_default(loops_plan_opts* opts);
 
 /* Host-only partition of A (Algorithm 1 with the structural split) -- no GPU needed.

@@ -52,7 +52,7 @@ class _Opts(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_double), ("block_rows", ctypes.c_int32),
                 ("contiguous_split", ctypes.c_int32), ("r_boundary", ctypes.c_int64),
                 ("want_backward", ctypes.c_int32), ("split_len", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("tile_min", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class _Info(ctypes.Structure):
@@ -62,7 +62,8 @@ class _Info(ctypes.Structure):
                 ("scale", ctypes.c_double), ("n_csr_rows", ctypes.c_int64), ("nnz_csr", ctypes.c_int64),
                 ("n_row_blocks", ctypes.c_int64), ("n_tiles", ctypes.c_int64), ("nnz_bcsr", ctypes.c_int64),
                 ("n_split_rows", ctypes.c_int64), ("n_segments", ctypes.c_int64),
-                ("n_subnormal_vals", ctypes.c_int64), ("device_bytes", ctypes.c_int64)]
+                ("n_subnormal_vals", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+                ("r_boundary", ctypes.c_int64), ("tile_min", ctypes.c_int64)]
 
 
 class _Part(ctypes.Structure):
@@ -151,9 +152,12 @@ def _csr_struct(A):
     return s, (rp, ci, v)
 
 
-def _opts(tau=2.0, block_rows=0, contiguous_split=False, r_boundary=0, want_backward=False, split_len=0):
+def _opts(tau=2.0, block_rows=0, contiguous_split=False, r_boundary=0, want_backward=False, split_len=0,
+          tile_min=None):
     o = _Opts()
     load().loops_plan_opts_default(ctypes.byref(o))
+    if tile_min is not None:
+        o.tile_min = int(tile_min)
     o.tau = float(tau)
     o.block_rows = int(block_rows)
     o.contiguous_split = int(bool(contiguous_split))
@@ -178,11 +182,11 @@ def _part_to_dict(p: _Part) -> dict:
 
 
 def partition_host(A, dtype: str = "f64", tau: float = 2.0, block_rows: int = 0, contiguous_split: bool = False,
-                   r_boundary: int = 0) -> dict:
+                   r_boundary: int = 0, tile_min: int = 0) -> dict:
     """Host-only LOOPS partition (no GPU), canonical arrays as numpy."""
     L = load()
     cs, keep = _csr_struct(A)
-    o = _opts(tau, block_rows, contiguous_split, r_boundary)
+    o = _opts(tau, block_rows, contiguous_split, r_boundary, tile_min=tile_min)
     part = _Part()
     _check(L.loops_partition_host(ctypes.byref(cs), _DT[dtype], ctypes.byref(o), ctypes.byref(part)))
     try:
@@ -211,7 +215,7 @@ class Plan:
 
     def __init__(self, A, N: int, dtype: str = "f64", tau: float = 2.0, block_rows: int = 0,
                  want_backward: bool = False, contiguous_split: bool = False, r_boundary: int = 0,
-                 split_len: int = 0, stream=None):
+                 split_len: int = 0, tile_min=None, stream=None):
         L = load()
         self._L = L
         self.dtype = _DT[dtype]
@@ -220,7 +224,7 @@ class Plan:
         self.n_rows, self.n_cols = int(A.n_rows), int(A.n_cols)
         self.nnz = int(np.asarray(A.row_ptr)[-1]) if len(A.row_ptr) else 0
         cs, keep = _csr_struct(A)
-        o = _opts(tau, block_rows, contiguous_split, r_boundary, want_backward, split_len)
+        o = _opts(tau, block_rows, contiguous_split, r_boundary, want_backward, split_len, tile_min)
         h = ctypes.c_void_p()
         s = _stream_handle(stream) if _torch().cuda.is_available() else ctypes.c_void_p(0)
         _check(L.loops_plan(ctypes.byref(cs), self.N, self.dtype, ctypes.byref(o), s, ctypes.byref(h)))

@@ -9,14 +9,20 @@
 //   BCSR task  (kind 1): F32 units [first, first + count) (a unit is a row block, or a K-aligned
 //              range of a block with very many tiles), one group of G lanes per unit,
 //              register-blocked outer product.
-//   BCSR task  (kind 2): one F16/BF16 unit per warp: the 16 B rows of each K-group are staged
-//              in the warp's own shared-memory slice and fed to mma.sync m16n8k16.
+//   BCSR task  (kind 2): one F16/BF16 unit per warp, in 64-column chunks: the 16 B-row pieces
+//              of each K-group are staged in the warp's own shared-memory slice and fed to
+//              mma.sync m16n8k16.
 // Rows split in segments and blocks cut into units get small follow-up launches that add
 // their partial sums in a fixed order.
 #include <type_traits>
 
 #include "device_common.cuh"
 #include "loops_internal.h"
+
+// Minimum resident blocks per SM for the persistent kernel (register cap; tuning knob).
+#ifndef LOOPS_BATCHED_MIN_BLOCKS
+#define LOOPS_BATCHED_MIN_BLOCKS 3
+#endif
 
 namespace loops {
 
@@ -153,8 +159,12 @@ __device__ __forceinline__ void ffma_block(const BatchDesc& d, int64_t u, int su
   }
 }
 
-// One F16/BF16 row block for the whole warp; sB is the warp's shared-memory slice holding the
-// 16 gathered B rows of the current K-group (row stride N + 8 elements).
+// One F16/BF16 BCSR unit for the whole warp, in column chunks of up to 64: sB is the warp's
+// shared-memory slice holding the 16 gathered B-row pieces of the current K-group and chunk
+// (row stride 72 elements, conflict-free for ldmatrix).
+constexpr int kHChunk = 64;
+constexpr int kHStride = kHChunk + 8;
+
 template <class T>
 __device__ __forceinline__ void hmma_block(const BatchDesc& d, int64_t u, T* sB, int lane) {
   constexpr bool kBF16 = sizeof(T) == 2 && !std::is_same<T, __half>::value;
@@ -164,80 +174,82 @@ __device__ __forceinline__ void hmma_block(const BatchDesc& d, int64_t u, T* sB,
   const int n_groups = (int)((d.unit_t1[u] - t0) / 16);
   const int32_t slot = d.unit_slot[u];
   const int N = (int)d.N;
-  const int RS = N + 8;
-  const int NF = N / 8;
   const T* Bp = reinterpret_cast<const T*>(d.B);
   const uint4* Af = reinterpret_cast<const uint4*>(d.tile_val) + (t0 / 16) * 32;
-  float acc[16][4];
+  const int q = lane >> 2, t = lane & 3;
+  for (int c0 = 0; c0 < N; c0 += kHChunk) {
+    const int NC = min(kHChunk, N - c0);   // columns of this chunk (a multiple of 8)
+    const int NF = NC / 8;
+    const int vec_per_row = NC / 8;        // 16-byte vectors per staged row piece
+    float acc[8][4];
 #pragma unroll
-  for (int f = 0; f < 16; ++f)
+    for (int f = 0; f < 8; ++f)
 #pragma unroll
-    for (int i = 0; i < 4; ++i) acc[f][i] = 0.f;
-  const int vec_per_row = N / 8;  // 16-byte vectors per staged row
-  for (int g = 0; g < n_groups; ++g) {
-    __syncwarp();
-    for (int i = lane; i < 16 * vec_per_row; i += 32) {
-      const int k = i / vec_per_row, q = i % vec_per_row;
-      const int32_t c = __ldg(d.tile_col + t0 + g * 16 + k);
-      const uint4 v = c >= 0 ? ldg16(Bp + (int64_t)c * d.ldb + q * 8) : make_uint4(0, 0, 0, 0);
-      *reinterpret_cast<uint4*>(sB + k * RS + q * 8) = v;
-    }
-    __syncwarp();
-    const uint4 af = __ldg(Af + (int64_t)g * 32 + lane);
-    const int mi = lane >> 3, r = lane & 7;
+      for (int i = 0; i < 4; ++i) acc[f][i] = 0.f;
+    for (int g = 0; g < n_groups; ++g) {
+      __syncwarp();
+      for (int i = lane; i < 16 * vec_per_row; i += 32) {
+        const int k = i / vec_per_row, qv = i % vec_per_row;
+        const int32_t c = __ldg(d.tile_col + t0 + g * 16 + k);
+        const uint4 v = c >= 0 ? ldg16(Bp + (int64_t)c * d.ldb + c0 + qv * 8) : make_uint4(0, 0, 0, 0);
+        *reinterpret_cast<uint4*>(sB + k * kHStride + qv * 8) = v;
+      }
+      __syncwarp();
+      const uint4 af = __ldg(Af + (int64_t)g * 32 + lane);
+      const int mi = lane >> 3, r = lane & 7;
 #pragma unroll
-    for (int f = 0; f < 16; f += 2) {
-      if (f >= NF) break;
-      if (f + 1 < NF) {
-        const uint32_t addr = smem_addr(sB + (r + 8 * (mi & 1)) * RS + f * 8 + 8 * (mi >> 1));
-        uint32_t b0, b1, b2, b3;
-        asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
-                     : "=r"(b0), "=r"(b1), "=r"(b2), "=r"(b3) : "r"(addr));
-        mma16816_b(acc[f], af, b0, b1, kBF16);
-        mma16816_b(acc[f + 1], af, b2, b3, kBF16);
-      } else {
-        const uint32_t addr = smem_addr(sB + (r + 8 * (mi & 1)) * RS + f * 8);
-        uint32_t b0, b1;
-        asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];"
-                     : "=r"(b0), "=r"(b1) : "r"(addr));
-        mma16816_b(acc[f], af, b0, b1, kBF16);
+      for (int f = 0; f < 8; f += 2) {
+        if (f >= NF) break;
+        if (f + 1 < NF) {
+          const uint32_t addr = smem_addr(sB + (r + 8 * (mi & 1)) * kHStride + f * 8 + 8 * (mi >> 1));
+          uint32_t b0, b1, b2, b3;
+          asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                       : "=r"(b0), "=r"(b1), "=r"(b2), "=r"(b3) : "r"(addr));
+          mma16816_b(acc[f], af, b0, b1, kBF16);
+          mma16816_b(acc[f + 1], af, b2, b3, kBF16);
+        } else {
+          const uint32_t addr = smem_addr(sB + (r + 8 * (mi & 1)) * kHStride + f * 8);
+          uint32_t b0, b1;
+          asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];"
+                       : "=r"(b0), "=r"(b1) : "r"(addr));
+          mma16816_b(acc[f], af, b0, b1, kBF16);
+        }
       }
     }
-  }
-  const int q = lane >> 2, t = lane & 3;
-  if (slot >= 0) {  // unit of a split block: unscaled partial sums
-    float* P = reinterpret_cast<float*>(d.bscratch) + (int64_t)slot * 16 * d.N;
+    if (slot >= 0) {  // unit of a split block: unscaled partial sums
+      float* P = reinterpret_cast<float*>(d.bscratch) + (int64_t)slot * 16 * d.N;
 #pragma unroll
-    for (int f = 0; f < 16; ++f) {
+      for (int f = 0; f < 8; ++f) {
+        if (f >= NF) break;
+        const int64_t n = c0 + f * 8 + 2 * t;
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+          *reinterpret_cast<float2*>(P + (int64_t)(q + 8 * h) * d.N + n) = make_float2(acc[f][2 * h], acc[f][2 * h + 1]);
+      }
+      continue;
+    }
+    float* C = reinterpret_cast<float*>(d.C);
+#pragma unroll
+    for (int f = 0; f < 8; ++f) {
       if (f >= NF) break;
-      const int64_t n = f * 8 + 2 * t;
+      const int64_t n = c0 + f * 8 + 2 * t;
+      float s0 = d.inv_scale, s1 = d.inv_scale;
+      if (d.col_scale) {
+        s0 *= d.col_scale[n];
+        s1 *= d.col_scale[n + 1];
+      }
 #pragma unroll
-      for (int h = 0; h < 2; ++h)
-        *reinterpret_cast<float2*>(P + (int64_t)(q + 8 * h) * d.N + n) = make_float2(acc[f][2 * h], acc[f][2 * h + 1]);
-    }
-    return;
-  }
-  float* C = reinterpret_cast<float*>(d.C);
-#pragma unroll
-  for (int f = 0; f < 16; ++f) {
-    if (f >= NF) break;
-    const int64_t n = f * 8 + 2 * t;
-    float s0 = d.inv_scale, s1 = d.inv_scale;
-    if (d.col_scale) {
-      s0 *= d.col_scale[n];
-      s1 *= d.col_scale[n + 1];
-    }
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int64_t row = rb * 16 + q + 8 * h;
-      if (row < d.n_rows)
-        *reinterpret_cast<float2*>(C + row * d.ldc + n) = make_float2(acc[f][2 * h] * s0, acc[f][2 * h + 1] * s1);
+      for (int h = 0; h < 2; ++h) {
+        const int64_t row = rb * 16 + q + 8 * h;
+        if (row < d.n_rows)
+          *reinterpret_cast<float2*>(C + row * d.ldc + n) = make_float2(acc[f][2 * h] * s0, acc[f][2 * h + 1] * s1);
+      }
     }
   }
 }
 
 template <class Tr, int BR>
-__global__ void __launch_bounds__(256) batched_persistent(const BatchDesc* __restrict__ descs,
+__global__ void __launch_bounds__(256, LOOPS_BATCHED_MIN_BLOCKS) batched_persistent(const BatchDesc* __restrict__ descs,
                                                           const BatchTask* __restrict__ tasks, int64_t n_tasks,
                                                           int smem_per_warp) {
   extern __shared__ __align__(128) unsigned char smem[];

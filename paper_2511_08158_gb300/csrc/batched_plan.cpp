@@ -63,7 +63,6 @@ loops_status build_batch(const loops_csr* As, const int64_t* Ns, int32_t count, 
   std::vector<BatchTask> tasks;
   std::vector<double> cost;
   std::vector<int2> splits, bsplits;
-  int64_t max_N = 8;
   std::vector<double> vals;
   for (int32_t m = 0; m < count && !st; ++m) {
     const int64_t N = Ns[m];
@@ -73,7 +72,6 @@ loops_status build_batch(const loops_csr* As, const int64_t* Ns, int32_t count, 
       st = LOOPS_ERR_UNSUPPORTED;
       break;
     }
-    max_N = std::max(max_N, N);
     if ((st = validate_csr(&As[m]))) break;
     read_vals_f64(&As[m], vals);
     loops_plan_s* p = nullptr;
@@ -122,7 +120,7 @@ loops_status build_batch(const loops_csr* As, const int64_t* Ns, int32_t count, 
   b->n_tasks = (int64_t)sorted.size();
   b->n_splits = (int64_t)splits.size();
   b->n_bsplits = (int64_t)bsplits.size();
-  b->smem_per_warp = dtype == LOOPS_F32 ? 0 : (int)(((16 * (max_N + 8) * 2) + 127) / 128 * 128);
+  b->smem_per_warp = dtype == LOOPS_F32 ? 0 : (16 * (64 + 8) * 2 + 127) / 128 * 128;  // one 64-column chunk
   b->grid = batched_grid_blocks(dtype, br, b->smem_per_warp);
   // descriptors (static parts now; B/C pointers per call)
   cudaError_t e = cudaMallocHost((void**)&b->h_desc, sizeof(BatchDesc) * (size_t)std::max(count, 1));
@@ -256,6 +254,11 @@ loops_status loops_plan_batched(const loops_csr* As, const int64_t* Ns, int32_t 
   loops_plan_opts_default(&o);
   if (opts) o = *opts;
   if (std::isnan(o.tau)) { set_error("tau is NaN"); return LOOPS_ERR_INVALID_ARG; }
+  if (o.tile_min > 1) {
+    set_error("the tile-level split is not available in batched plans");
+    return LOOPS_ERR_UNSUPPORTED;
+  }
+  o.tile_min = 0;
   o.want_backward = 0;
   o.contiguous_split = 0;
   int32_t br;
@@ -346,6 +349,7 @@ loops_status loops_plan_batched(const loops_csr* As, const int64_t* Ns, int32_t 
   p->tau = best->tau;
   p->scale = 1.0;
   p->split_len = 0;
+  p->tile_min = 0;
   p->opts = o;
   p->transposed = nullptr;
   p->d_error = nullptr;

@@ -16,7 +16,8 @@ void clear_error() { g_last_error.clear(); }
 
 loops_status export_part(const loops_plan_s* p, loops_partition* out);
 loops_status autotune_tau(const loops_csr* A, const double* vals, int64_t N, loops_dtype dtype,
-                          int32_t br, int32_t split_len, cudaStream_t s, double* tau_out);
+                          int32_t br, int32_t split_len, bool try_tile_split, cudaStream_t s, double* tau_out,
+                          int32_t* tile_min_out);
 
 loops_status cuda_status(cudaError_t e, const char* what) {
   if (e == cudaSuccess) return LOOPS_OK;
@@ -134,6 +135,7 @@ loops_status make_plan(const loops_csr* A, const double* vals, int64_t N, loops_
   p->tau = tau;
   p->opts = o;
   p->split_len = o.split_len > 0 ? o.split_len : 512;
+  p->tile_min = o.tile_min > 1 ? o.tile_min : 0;
   p->transposed = nullptr;
   p->d_error = nullptr;
   p->side = nullptr;
@@ -145,7 +147,8 @@ loops_status make_plan(const loops_csr* A, const double* vals, int64_t N, loops_
   for (auto& ev : p->tev) ev = nullptr;
   p->batch = nullptr;
   p->other_bytes = 0;
-  loops_status st = build_canon(A, vals, dtype, br, tau, o.contiguous_split != 0, o.r_boundary, p->canon);
+  loops_status st = build_canon(A, vals, dtype, br, tau, o.contiguous_split != 0, o.r_boundary, p->tile_min,
+                                p->canon);
   if (st) { destroy_plan(p); return st; }
   p->scale = p->canon.scale;
   p->n_subnormal = 0;
@@ -247,24 +250,31 @@ static loops_status run_spmm(loops_plan_s* p, const void* B, int64_t ldb, const 
   const bool tm = p->timing;
   auto rec = [&](int i, cudaStream_t st) { return tm ? cudaEventRecord(p->tev[i], st) : cudaSuccess; };
   cudaError_t e = cudaSuccess;
+  const bool has_acc = p->dev.csr_acc.n_items > 0;
   if (has_csr && has_bcsr) {
     e = cudaEventRecord(p->ev_fork, s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(p->side, p->ev_fork, 0);
     if (e == cudaSuccess) e = rec(2, p->side);
     if (e == cudaSuccess) e = launch_bcsr(p, p->dev.bcsr, a, p->side);
-    if (e == cudaSuccess) e = rec(3, p->side);
+    if (e == cudaSuccess && !has_acc) e = rec(3, p->side);
     if (e == cudaSuccess) e = rec(0, s);
-    if (e == cudaSuccess) e = launch_csr(p, p->dev.csr, a, s);
+    if (e == cudaSuccess) e = launch_csr(p, p->dev.csr, a, false, s);
     if (e == cudaSuccess) e = rec(1, s);
     if (e == cudaSuccess) e = cudaEventRecord(p->ev_join, p->side);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->ev_join, 0);
   } else {
     if (e == cudaSuccess) e = rec(2, s);
     if (e == cudaSuccess && has_bcsr) e = launch_bcsr(p, p->dev.bcsr, a, s);
-    if (e == cudaSuccess) e = rec(3, s);
+    if (e == cudaSuccess && !has_acc) e = rec(3, s);
     if (e == cudaSuccess) e = rec(0, s);
-    if (e == cudaSuccess && has_csr) e = launch_csr(p, p->dev.csr, a, s);
+    if (e == cudaSuccess && has_csr) e = launch_csr(p, p->dev.csr, a, false, s);
     if (e == cudaSuccess) e = rec(1, s);
+  }
+  // tile-level split: rows of BCSR blocks add their moved entries after the BCSR part wrote
+  // them (the BCSR timing window then ends after this pass)
+  if (e == cudaSuccess && has_acc) {
+    e = launch_csr(p, p->dev.csr_acc, a, true, s);
+    if (e == cudaSuccess) e = rec(3, s);
   }
   return cuda_status(e, "SpMM launch");
 }
@@ -279,9 +289,15 @@ static cudaError_t fill_finite(void* p, int64_t bytes, cudaStream_t s) {
 // thresholds on synthetic B and keeps the fastest. Candidates that give the same row-block
 // split as an earlier one are skipped.
 loops_status autotune_tau(const loops_csr* A, const double* vals, int64_t N, loops_dtype dtype, int32_t br,
-                          int32_t split_len, cudaStream_t s, double* tau_out) {
-  static const double cands[] = {INFINITY, 8.0, 4.0, 3.0, 2.0, 1.5, 1.25, 0.0};
+                          int32_t split_len, bool try_tile_split, cudaStream_t s, double* tau_out,
+                          int32_t* tile_min_out) {
+  struct Cand { double tau; int32_t tile_min; };
+  std::vector<Cand> cands;
+  for (double t : {(double)INFINITY, 8.0, 4.0, 3.0, 2.0, 1.5, 1.25, 0.0}) cands.push_back({t, 0});
+  if (try_tile_split)  // tile-level split: dense tiles (>= 2 entries) on the BCSR kernel only
+    for (double t : {4.0, 2.0, 1.25}) cands.push_back({t, 2});
   *tau_out = 2.0;
+  *tile_min_out = 0;
   if (A->nnz == 0 || N == 0 || A->n_rows == 0) return LOOPS_OK;
   const int64_t eb = dense_elem_bytes(dtype), ec = out_elem_bytes(dtype);
   void *dB = nullptr, *dC = nullptr;
@@ -293,15 +309,17 @@ loops_status autotune_tau(const loops_csr* A, const double* vals, int64_t N, loo
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   loops_status st = cuda_status(e, "autotune setup");
   double best = INFINITY;
-  std::vector<int64_t> seen;
+  std::vector<std::pair<int64_t, int64_t>> seen;
   loops_plan_opts o;
   loops_plan_opts_default(&o);
   o.split_len = split_len;
-  for (double tau : cands) {
+  for (const Cand& cand : cands) {
     if (st) break;
+    const double tau = cand.tau;
+    o.tile_min = cand.tile_min;
     loops_plan_s* p = nullptr;
     if ((st = make_plan(A, vals, N, dtype, o, br, tau, false, &p))) break;
-    const int64_t key = (int64_t)p->canon.rb_ids.size();
+    const std::pair<int64_t, int64_t> key((int64_t)p->canon.rb_ids.size(), (int64_t)p->canon.tile_col.size());
     if (std::find(seen.begin(), seen.end(), key) != seen.end()) { destroy_plan(p); continue; }
     seen.push_back(key);
     float best_ms = INFINITY;
@@ -317,13 +335,63 @@ loops_status autotune_tau(const loops_csr* A, const double* vals, int64_t N, loo
       best_ms = std::min(best_ms, ms);
     }
     destroy_plan(p);
-    if (!st && best_ms < best) { best = best_ms; *tau_out = tau; }
+    if (!st && best_ms < best) { best = best_ms; *tau_out = tau; *tile_min_out = cand.tile_min; }
   }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   if (dB) cudaFree(dB);
   if (dC) cudaFree(dC);
   return st;
+}
+
+// Paper mode with the boundary from Eq. 1: time the pure CSR plan (the paper's pure vector-unit
+// configuration) and the pure BCSR plan (rows from 0 on in BCSR) on synthetic B, take each
+// part's throughput TP = rows / time, and choose r_b so that the two parts, running side by
+// side, take the same time: r_b / TP_csr = (n_rows - r_b) / TP_bcsr.
+loops_status model_boundary(const loops_csr* A, const double* vals, int64_t N, loops_dtype dtype, int32_t br,
+                            int32_t split_len, cudaStream_t s, int64_t* rb_out) {
+  *rb_out = A->n_rows;
+  if (A->nnz == 0 || N == 0 || A->n_rows == 0) return LOOPS_OK;
+  const int64_t eb = dense_elem_bytes(dtype), ec = out_elem_bytes(dtype);
+  void *dB = nullptr, *dC = nullptr;
+  cudaError_t e = cudaMalloc(&dB, (size_t)std::max<int64_t>(A->n_cols * N * eb, 16));
+  if (e == cudaSuccess) e = cudaMalloc(&dC, (size_t)std::max<int64_t>(A->n_rows * N * ec, 16));
+  if (e == cudaSuccess) e = fill_finite(dB, A->n_cols * N * eb, s);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  loops_status st = cuda_status(e, "model setup");
+  float t[2] = {INFINITY, INFINITY};
+  for (int which = 0; which < 2 && !st; ++which) {
+    loops_plan_opts o;
+    loops_plan_opts_default(&o);
+    o.split_len = split_len;
+    o.contiguous_split = which;          // 0: tau = inf (all CSR); 1: r_b = 0 (all BCSR)
+    o.r_boundary = 0;
+    loops_plan_s* p = nullptr;
+    if ((st = make_plan(A, vals, N, dtype, o, br, INFINITY, false, &p))) break;
+    for (int it = 0; it < 7 && !st; ++it) {
+      if (it >= 2) cudaEventRecord(e0, s);
+      st = run_spmm(p, dB, N, nullptr, dC, N, s);
+      if (it >= 2) {
+        cudaEventRecord(e1, s);
+        if (!st) st = cuda_status(cudaEventSynchronize(e1), "model timing");
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        t[which] = std::min(t[which], ms);
+      }
+    }
+    destroy_plan(p);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (dB) cudaFree(dB);
+  if (dC) cudaFree(dC);
+  if (st) return st;
+  const double tp_csr = (double)A->n_rows / std::max((double)t[0], 1e-9);
+  const double tp_bcsr = (double)A->n_rows / std::max((double)t[1], 1e-9);
+  *rb_out = (int64_t)std::llround((double)A->n_rows * tp_csr / (tp_csr + tp_bcsr));
+  return LOOPS_OK;
 }
 
 }  // namespace loops
@@ -354,6 +422,7 @@ void loops_plan_opts_default(loops_plan_opts* o) {
   if (!o) return;
   std::memset(o, 0, sizeof(*o));
   o->tau = 2.0;
+  o->tile_min = -1;
 }
 
 loops_status loops_partition_host(const loops_csr* A, loops_dtype dtype, const loops_plan_opts* opts,
@@ -373,7 +442,9 @@ loops_status loops_partition_host(const loops_csr* A, loops_dtype dtype, const l
   std::vector<double> vals;
   read_vals_f64(A, vals);
   Canon c;
-  if ((st = build_canon(A, vals.data(), dtype, br, o.tau, o.contiguous_split != 0, o.r_boundary, c))) return st;
+  if ((st = build_canon(A, vals.data(), dtype, br, o.tau, o.contiguous_split != 0, o.r_boundary,
+                        o.tile_min > 1 ? o.tile_min : 0, c)))
+    return st;
   fill_partition(c, out);
   return LOOPS_OK;
 }
@@ -403,11 +474,23 @@ loops_status loops_plan(const loops_csr* A, int64_t N, loops_dtype dtype, const 
   int32_t br;
   if ((st = resolve_block_rows(dtype, o, &br))) return st;
   if (o.split_len < 0) { set_error("split_len < 0"); return LOOPS_ERR_INVALID_ARG; }
+  if (o.want_backward && o.tile_min > 1) {
+    set_error("the tile-level split is not available with want_backward");
+    return LOOPS_ERR_UNSUPPORTED;
+  }
   std::vector<double> vals;
   read_vals_f64(A, vals);
   double tau = o.tau;
   if (tau < 0.0 && !o.contiguous_split) {
-    if ((st = autotune_tau(A, vals.data(), N, dtype, br, o.split_len, (cudaStream_t)stream, &tau))) return st;
+    int32_t tmin = o.tile_min;
+    if ((st = autotune_tau(A, vals.data(), N, dtype, br, o.split_len, tmin < 0 && !o.want_backward,
+                           (cudaStream_t)stream, &tau, &tmin)))
+      return st;
+    o.tile_min = tmin;
+  }
+  if (o.contiguous_split && o.r_boundary < 0) {
+    if ((st = model_boundary(A, vals.data(), N, dtype, br, o.split_len, (cudaStream_t)stream, &o.r_boundary)))
+      return st;
   }
   loops_plan_s* p = nullptr;
   if ((st = make_plan(A, vals.data(), N, dtype, o, br, tau, false, &p))) return st;
@@ -474,6 +557,8 @@ loops_status loops_plan_info_get(loops_plan_t p, loops_plan_info* out) {
   out->n_segments = p->dev.csr.n_slots;
   out->n_subnormal_vals = p->n_subnormal;
   out->device_bytes = p->dev.device_bytes + p->other_bytes + p->vmap.bytes;
+  out->r_boundary = p->opts.contiguous_split ? p->opts.r_boundary : -1;
+  out->tile_min = p->tile_min;
   if (p->transposed)
     out->device_bytes += p->transposed->dev.device_bytes + p->transposed->other_bytes + p->transposed->vmap.bytes;
   return LOOPS_OK;

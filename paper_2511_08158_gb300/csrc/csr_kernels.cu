@@ -21,6 +21,9 @@
 #ifndef LOOPS_CSR_MIN_BLOCKS
 #define LOOPS_CSR_MIN_BLOCKS 4
 #endif
+#ifndef LOOPS_CSR_LANE_VECTORS
+#define LOOPS_CSR_LANE_VECTORS 1
+#endif
 
 namespace loops {
 
@@ -41,6 +44,7 @@ struct CsrKArgs {
   float inv_scale_f;
   double inv_scale_d;
   int64_t N;
+  int accumulate;        // add to C (rows a BCSR part wrote first) instead of overwriting it
 };
 
 template <class Tr>
@@ -59,8 +63,13 @@ __device__ __forceinline__ float out_scale<TrBF16>(const CsrKArgs& a, int64_t n)
 }
 
 // Vector path: N % VE == 0, B/C/ld aligned for 16-byte B loads and vector C stores.
+// FP64: 8 resident blocks (at most 32 registers) keep enough warps in flight to feed the FP64
+// pipe; the other formats use the tuning knob.
+template <class Tr>
+constexpr int csr_min_blocks() { return std::is_same<Tr, TrF64>::value ? 8 : LOOPS_CSR_MIN_BLOCKS; }
+
 template <class Tr, int G, int VPL, int U>
-__global__ void __launch_bounds__(256, LOOPS_CSR_MIN_BLOCKS) csr_spmm_vec(CsrKArgs a) {
+__global__ void __launch_bounds__(256, csr_min_blocks<Tr>()) csr_spmm_vec(CsrKArgs a) {
   using TB = typename Tr::TB;
   using TAcc = typename Tr::TAcc;
   using TC = typename Tr::TC;
@@ -158,6 +167,10 @@ __global__ void __launch_bounds__(256, LOOPS_CSR_MIN_BLOCKS) csr_spmm_vec(CsrKAr
 #pragma unroll
       for (int e = 0; e < VE; ++e)
         o[e] = Tr::kScaled ? (TC)(acc[p][e] * out_scale<Tr>(a, coff[p] + e)) : (TC)acc[p][e];
+      if (a.accumulate) {
+#pragma unroll
+        for (int e = 0; e < VE; ++e) o[e] += crow[coff[p] + e];
+      }
       // VE outputs are 16 (F64/F32) or 32 (16-bit inputs, f32 outputs) bytes
 #pragma unroll
       for (int q = 0; q < (int)(VE * sizeof(TC) / 16); ++q)
@@ -218,7 +231,9 @@ __global__ void __launch_bounds__(256) csr_spmm_scalar(CsrKArgs a) {
   }
   if (!colok) return;
   if (row >= 0) {
-    reinterpret_cast<TC*>(a.C)[(int64_t)row * a.ldc + n] = Tr::kScaled ? (TC)(acc * out_scale<Tr>(a, n)) : (TC)acc;
+    TC* cp = reinterpret_cast<TC*>(a.C) + (int64_t)row * a.ldc + n;
+    const TC v = Tr::kScaled ? (TC)(acc * out_scale<Tr>(a, n)) : (TC)acc;
+    *cp = a.accumulate ? *cp + v : v;
   } else {
     reinterpret_cast<TAcc*>(a.scratch)[(int64_t)(-1 - row) * a.N + n] = acc;
   }
@@ -239,7 +254,9 @@ __global__ void __launch_bounds__(256) split_reduce(const int32_t* __restrict__ 
   for (int64_t n = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; n < a.N; n += (int64_t)gridDim.y * blockDim.x) {
     TAcc acc = TAcc(0);
     for (int32_t q = s0; q < s1; ++q) acc += sc[(int64_t)q * a.N + n];
-    reinterpret_cast<TC*>(a.C)[(int64_t)row * a.ldc + n] = Tr::kScaled ? (TC)(acc * out_scale<Tr>(a, n)) : (TC)acc;
+    TC* cp = reinterpret_cast<TC*>(a.C) + (int64_t)row * a.ldc + n;
+    const TC v = Tr::kScaled ? (TC)(acc * out_scale<Tr>(a, n)) : (TC)acc;
+    *cp = a.accumulate ? *cp + v : v;
   }
 }
 
@@ -265,8 +282,10 @@ cudaError_t launch_vec_g(const CsrKArgs& a, cudaStream_t s) {
 }
 
 template <class Tr>
-cudaError_t launch_csr_t(const loops_plan_s* p, const CsrDev& d, const DenseArgs& da, cudaStream_t s) {
+cudaError_t launch_csr_t(const loops_plan_s* p, const CsrDev& d, const DenseArgs& da, bool accumulate,
+                         cudaStream_t s) {
   CsrKArgs a;
+  a.accumulate = accumulate ? 1 : 0;
   a.item_row = d.item_row;
   a.item_ptr = d.item_ptr;
   a.col = d.col;
@@ -290,14 +309,18 @@ cudaError_t launch_csr_t(const loops_plan_s* p, const CsrDev& d, const DenseArgs
   if (a.n_items > 0) {
     if (vec) {
       const int64_t nvec = a.N / VE;
-      const int G = next_pow2(nvec);
-      const bool two = nvec > 32;
+      // lanes per item: the 16-byte vectors of a row, LOOPS_CSR_LANE_VECTORS per lane (more
+      // vectors per lane: fewer shuffles per byte and more loads in flight per lane)
+      constexpr int LV = LOOPS_CSR_LANE_VECTORS;
+      const int64_t nv = std::is_same<Tr, TrF64>::value ? nvec : (nvec + LV - 1) / LV;
+      const int G = next_pow2(nv);
+      const bool two = std::is_same<Tr, TrF64>::value ? nvec > 32 : (LV > 1 && nvec > 1) || nvec > 32;
       switch (G) {
-        case 1: e = launch_vec_g<Tr, 1, 1>(a, s); break;
-        case 2: e = launch_vec_g<Tr, 2, 1>(a, s); break;
-        case 4: e = launch_vec_g<Tr, 4, 1>(a, s); break;
-        case 8: e = launch_vec_g<Tr, 8, 1>(a, s); break;
-        case 16: e = launch_vec_g<Tr, 16, 1>(a, s); break;
+        case 1: e = two ? launch_vec_g<Tr, 1, 2>(a, s) : launch_vec_g<Tr, 1, 1>(a, s); break;
+        case 2: e = two ? launch_vec_g<Tr, 2, 2>(a, s) : launch_vec_g<Tr, 2, 1>(a, s); break;
+        case 4: e = two ? launch_vec_g<Tr, 4, 2>(a, s) : launch_vec_g<Tr, 4, 1>(a, s); break;
+        case 8: e = two ? launch_vec_g<Tr, 8, 2>(a, s) : launch_vec_g<Tr, 8, 1>(a, s); break;
+        case 16: e = two ? launch_vec_g<Tr, 16, 2>(a, s) : launch_vec_g<Tr, 16, 1>(a, s); break;
         default: e = two ? launch_vec_g<Tr, 32, 2>(a, s) : launch_vec_g<Tr, 32, 1>(a, s); break;
       }
     } else {
@@ -560,12 +583,13 @@ cudaError_t launch_set_values(const loops_plan_s* p, const void* vals, loops_dty
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_csr(const loops_plan_s* p, const CsrDev& d, const DenseArgs& a, cudaStream_t s) {
+cudaError_t launch_csr(const loops_plan_s* p, const CsrDev& d, const DenseArgs& a, bool accumulate,
+                       cudaStream_t s) {
   switch (p->dtype) {
-    case LOOPS_F64: return launch_csr_t<TrF64>(p, d, a, s);
-    case LOOPS_F32: return launch_csr_t<TrF32>(p, d, a, s);
-    case LOOPS_F16: return launch_csr_t<TrF16>(p, d, a, s);
-    case LOOPS_BF16: return launch_csr_t<TrBF16>(p, d, a, s);
+    case LOOPS_F64: return launch_csr_t<TrF64>(p, d, a, accumulate, s);
+    case LOOPS_F32: return launch_csr_t<TrF32>(p, d, a, accumulate, s);
+    case LOOPS_F16: return launch_csr_t<TrF16>(p, d, a, accumulate, s);
+    case LOOPS_BF16: return launch_csr_t<TrBF16>(p, d, a, accumulate, s);
   }
   return cudaErrorInvalidValue;
 }

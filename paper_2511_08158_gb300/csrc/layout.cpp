@@ -113,60 +113,75 @@ loops_status upload_part(loops_plan_s* p, int64_t N) {
   loops_status st;
   const int acc_bytes = p->dtype == LOOPS_F64 ? 8 : 4;
 
-  // ---- CSR work items
-  struct It { int32_t row; int64_t beg, end; int bucket; };
-  std::vector<It> items;
-  const int64_t n_csr = (int64_t)c.csr_rows.size();
-  items.reserve((size_t)n_csr);
-  const int64_t L = std::max<int64_t>(p->split_len, 1);
-  int64_t n_slots = 0;
-  for (int64_t x = 0; x < n_csr; ++x) {
-    const int64_t b = c.csr_ptr[(size_t)x], e = c.csr_ptr[(size_t)x + 1];
-    const int64_t len = e - b;
-    if (len > L) {
-      d.csr.h_split_row.push_back(c.csr_rows[(size_t)x]);
-      d.csr.h_split_slot_ptr.push_back((int32_t)n_slots);
-      for (int64_t s = b; s < e; s += L) {
-        items.push_back({(int32_t)(-1 - n_slots), s, std::min(s + L, e), 63});
-        ++n_slots;
-      }
-    } else {
-      items.push_back({c.csr_rows[(size_t)x], b, e, bucket_of(len)});
-    }
+  // ---- CSR work items: rows inside BCSR blocks (tile-level split) go to csr_acc
+  std::vector<uint8_t> in_bcsr;
+  if (!c.rb_ids.empty()) {
+    in_bcsr.assign((size_t)std::max<int64_t>(p->n_rows, 1), 0);
+    for (int32_t b : c.rb_ids)
+      for (int64_t i = (int64_t)b * c.br; i < std::min<int64_t>((int64_t)b * c.br + c.br, p->n_rows); ++i)
+        in_bcsr[(size_t)i] = 1;
   }
-  d.csr.h_split_slot_ptr.push_back((int32_t)n_slots);
-  std::stable_sort(items.begin(), items.end(), [](const It& a, const It& b) { return a.bucket > b.bucket; });
-  d.csr.n_items = (int64_t)items.size();
-  d.csr.n_split = (int64_t)d.csr.h_split_row.size();
-  d.csr.n_slots = n_slots;
-  d.csr.h_item_row.resize(items.size());
-  d.csr.h_item_ptr.resize(items.size() + 1);
-  d.csr.nnz = (int64_t)c.csr_col.size();
-  std::vector<int32_t> col((size_t)d.csr.nnz);
-  std::vector<double> val((size_t)d.csr.nnz);
-  int64_t pos = 0;
-  d.csr.h_item_ptr[0] = 0;
-  for (size_t i = 0; i < items.size(); ++i) {
-    d.csr.h_item_row[i] = items[i].row;
-    for (int64_t k = items[i].beg; k < items[i].end; ++k) {
-      col[(size_t)pos] = c.csr_col[(size_t)k];
-      val[(size_t)pos] = c.csr_val[(size_t)k];
-      ++pos;
-    }
-    d.csr.h_item_ptr[i + 1] = pos;
-  }
-  std::vector<uint8_t> enc;
-  encode_values(val.data(), val.size(), p->dtype, enc);
   int64_t& bytes = d.device_bytes;
-  if ((st = dev_upload(&d.csr.item_row, d.csr.h_item_row.data(), items.size(), bytes))) return st;
-  if ((st = dev_upload(&d.csr.item_ptr, d.csr.h_item_ptr.data(), items.size() + 1, bytes))) return st;
-  if ((st = dev_upload(&d.csr.col, col.data(), col.size(), bytes))) return st;
-  if ((st = dev_upload((uint8_t**)&d.csr.val, enc.data(), enc.size(), bytes))) return st;
-  if (d.csr.n_split) {
-    if ((st = dev_upload(&d.csr.split_row, d.csr.h_split_row.data(), d.csr.h_split_row.size(), bytes))) return st;
-    if ((st = dev_upload(&d.csr.split_slot_ptr, d.csr.h_split_slot_ptr.data(), d.csr.h_split_slot_ptr.size(), bytes))) return st;
-    if ((st = dev_upload((uint8_t**)&d.csr.scratch, (const uint8_t*)nullptr,
-                         (size_t)(n_slots * std::max<int64_t>(N, 1) * acc_bytes), bytes))) return st;
+  std::vector<uint8_t> enc;
+  for (int which = 0; which < 2; ++which) {
+    CsrDev& cd = which == 0 ? d.csr : d.csr_acc;
+    struct It { int32_t row; int64_t beg, end; int bucket; };
+    std::vector<It> items;
+    const int64_t n_csr = (int64_t)c.csr_rows.size();
+    const int64_t L = std::max<int64_t>(p->split_len, 1);
+    int64_t n_slots = 0;
+    for (int64_t x = 0; x < n_csr; ++x) {
+      const int32_t row = c.csr_rows[(size_t)x];
+      const int mixed = in_bcsr.empty() ? 0 : in_bcsr[(size_t)row];
+      if (mixed != which) continue;
+      const int64_t b = c.csr_ptr[(size_t)x], e = c.csr_ptr[(size_t)x + 1];
+      const int64_t len = e - b;
+      if (len > L) {
+        cd.h_split_row.push_back(row);
+        cd.h_split_slot_ptr.push_back((int32_t)n_slots);
+        for (int64_t s0 = b; s0 < e; s0 += L) {
+          items.push_back({(int32_t)(-1 - n_slots), s0, std::min(s0 + L, e), 63});
+          ++n_slots;
+        }
+      } else {
+        items.push_back({row, b, e, bucket_of(len)});
+      }
+    }
+    cd.h_split_slot_ptr.push_back((int32_t)n_slots);
+    std::stable_sort(items.begin(), items.end(), [](const It& a, const It& b) { return a.bucket > b.bucket; });
+    cd.n_items = (int64_t)items.size();
+    cd.n_split = (int64_t)cd.h_split_row.size();
+    cd.n_slots = n_slots;
+    cd.h_item_row.resize(items.size());
+    cd.h_item_ptr.resize(items.size() + 1);
+    int64_t total = 0;
+    for (auto& it : items) total += it.end - it.beg;
+    cd.nnz = total;
+    std::vector<int32_t> col((size_t)total);
+    std::vector<double> val((size_t)total);
+    int64_t pos = 0;
+    cd.h_item_ptr[0] = 0;
+    for (size_t i = 0; i < items.size(); ++i) {
+      cd.h_item_row[i] = items[i].row;
+      for (int64_t k = items[i].beg; k < items[i].end; ++k) {
+        col[(size_t)pos] = c.csr_col[(size_t)k];
+        val[(size_t)pos] = c.csr_val[(size_t)k];
+        ++pos;
+      }
+      cd.h_item_ptr[i + 1] = pos;
+    }
+    if (items.empty()) continue;
+    encode_values(val.data(), val.size(), p->dtype, enc);
+    if ((st = dev_upload(&cd.item_row, cd.h_item_row.data(), items.size(), bytes))) return st;
+    if ((st = dev_upload(&cd.item_ptr, cd.h_item_ptr.data(), items.size() + 1, bytes))) return st;
+    if ((st = dev_upload(&cd.col, col.data(), col.size(), bytes))) return st;
+    if ((st = dev_upload((uint8_t**)&cd.val, enc.data(), enc.size(), bytes))) return st;
+    if (cd.n_split) {
+      if ((st = dev_upload(&cd.split_row, cd.h_split_row.data(), cd.h_split_row.size(), bytes))) return st;
+      if ((st = dev_upload(&cd.split_slot_ptr, cd.h_split_slot_ptr.data(), cd.h_split_slot_ptr.size(), bytes))) return st;
+      if ((st = dev_upload((uint8_t**)&cd.scratch, (const uint8_t*)nullptr,
+                           (size_t)(n_slots * std::max<int64_t>(N, 1) * acc_bytes), bytes))) return st;
+    }
   }
 
   // ---- BCSR part
@@ -231,7 +246,9 @@ loops_status upload_part(loops_plan_s* p, int64_t N) {
 
 void free_part(PartDev& d) {
   void* ptrs[] = {d.csr.item_row, d.csr.item_ptr, d.csr.col, d.csr.val, d.csr.split_row,
-                  d.csr.split_slot_ptr, d.csr.scratch, d.bcsr.rb_id, d.bcsr.rb_ptr,
+                  d.csr.split_slot_ptr, d.csr.scratch, d.csr_acc.item_row, d.csr_acc.item_ptr,
+                  d.csr_acc.col, d.csr_acc.val, d.csr_acc.split_row, d.csr_acc.split_slot_ptr,
+                  d.csr_acc.scratch, d.bcsr.rb_id, d.bcsr.rb_ptr,
                   d.bcsr.tile_col, d.bcsr.tile_val, d.bcsr.unit_block, d.bcsr.unit_t0,
                   d.bcsr.unit_t1, d.bcsr.unit_slot, d.bcsr.split_block, d.bcsr.split_slot_ptr,
                   d.bcsr.scratch};
@@ -319,34 +336,46 @@ loops_status export_part(const loops_plan_s* p, loops_partition* out) {
   const PartDev& d = p->dev;
   const int es = p->dtype == LOOPS_F64 ? 8 : p->dtype == LOOPS_F32 ? 4 : 2;
   loops_status st;
-  std::vector<int32_t> item_row, col, split_row, split_slot;
-  std::vector<int64_t> item_ptr;
-  std::vector<uint8_t> val;
-  if ((st = dev_download(item_row, d.csr.item_row, (size_t)d.csr.n_items))) return st;
-  if ((st = dev_download(item_ptr, d.csr.item_ptr, (size_t)(d.csr.n_items ? d.csr.n_items + 1 : 0)))) return st;
-  if ((st = dev_download(col, d.csr.col, (size_t)d.csr.nnz))) return st;
-  if ((st = dev_download(val, (const uint8_t*)d.csr.val, (size_t)(d.csr.nnz * es)))) return st;
-  if ((st = dev_download(split_row, d.csr.split_row, (size_t)d.csr.n_split))) return st;
-  if ((st = dev_download(split_slot, d.csr.split_slot_ptr, (size_t)(d.csr.n_split ? d.csr.n_split + 1 : 0)))) return st;
-  // slot -> split row index
-  std::vector<int32_t> slot_owner((size_t)d.csr.n_slots, -1);
-  for (int64_t s = 0; s < d.csr.n_split; ++s)
-    for (int32_t q = split_slot[(size_t)s]; q < split_slot[(size_t)s + 1]; ++q) slot_owner[(size_t)q] = (int32_t)s;
-  struct Row { int32_t row; std::vector<std::pair<int64_t, int64_t>> segs; };  // (slot or -1, item)
+  // rows of both CSR item sets, each with its entries (column, value) in segment order
+  struct Row { int32_t row; std::vector<std::pair<int32_t, double>> ents; };
   std::vector<Row> rows;
-  std::vector<int64_t> split_pos((size_t)d.csr.n_split, -1);
-  for (int64_t i = 0; i < d.csr.n_items; ++i) {
-    const int32_t r = item_row[(size_t)i];
-    if (r >= 0) {
-      rows.push_back({r, {{-1, i}}});
-    } else {
-      const int32_t slot = -1 - r;
-      const int32_t s = slot_owner[(size_t)slot];
-      if (split_pos[(size_t)s] < 0) {
-        split_pos[(size_t)s] = (int64_t)rows.size();
-        rows.push_back({split_row[(size_t)s], {}});
+  int64_t nnz_csr = 0;
+  for (const CsrDev* cd : {&d.csr, &d.csr_acc}) {
+    std::vector<int32_t> item_row, col, split_row, split_slot;
+    std::vector<int64_t> item_ptr;
+    std::vector<uint8_t> val;
+    if ((st = dev_download(item_row, cd->item_row, (size_t)cd->n_items))) return st;
+    if ((st = dev_download(item_ptr, cd->item_ptr, (size_t)(cd->n_items ? cd->n_items + 1 : 0)))) return st;
+    if ((st = dev_download(col, cd->col, (size_t)cd->nnz))) return st;
+    if ((st = dev_download(val, (const uint8_t*)cd->val, (size_t)(cd->nnz * es)))) return st;
+    if ((st = dev_download(split_row, cd->split_row, (size_t)cd->n_split))) return st;
+    if ((st = dev_download(split_slot, cd->split_slot_ptr, (size_t)(cd->n_split ? cd->n_split + 1 : 0)))) return st;
+    nnz_csr += cd->nnz;
+    // slot -> split row index
+    std::vector<int32_t> slot_owner((size_t)cd->n_slots, -1);
+    for (int64_t sidx = 0; sidx < cd->n_split; ++sidx)
+      for (int32_t q = split_slot[(size_t)sidx]; q < split_slot[(size_t)sidx + 1]; ++q)
+        slot_owner[(size_t)q] = (int32_t)sidx;
+    std::vector<std::vector<std::pair<int64_t, int64_t>>> split_segs((size_t)cd->n_split);  // (slot, item)
+    auto add_item = [&](Row& r, int64_t i) {
+      for (int64_t e = item_ptr[(size_t)i]; e < item_ptr[(size_t)i + 1]; ++e)
+        r.ents.push_back({col[(size_t)e], decode_value(&val[(size_t)(e * es)], p->dtype)});
+    };
+    for (int64_t i = 0; i < cd->n_items; ++i) {
+      const int32_t r = item_row[(size_t)i];
+      if (r >= 0) {
+        rows.push_back({r, {}});
+        add_item(rows.back(), i);
+      } else {
+        const int32_t slot = -1 - r;
+        split_segs[(size_t)slot_owner[(size_t)slot]].push_back({slot, i});
       }
-      rows[(size_t)split_pos[(size_t)s]].segs.push_back({slot, i});
+    }
+    for (int64_t sidx = 0; sidx < cd->n_split; ++sidx) {
+      auto segs = split_segs[(size_t)sidx];
+      std::sort(segs.begin(), segs.end());
+      rows.push_back({split_row[(size_t)sidx], {}});
+      for (auto& sg : segs) add_item(rows.back(), sg.second);
     }
   }
   std::sort(rows.begin(), rows.end(), [](const Row& a, const Row& b) { return a.row < b.row; });
@@ -356,23 +385,19 @@ loops_status export_part(const loops_plan_s* p, loops_partition* out) {
   out->k_pad = p->kpad;
   out->scale = p->scale;
   out->n_csr_rows = (int64_t)rows.size();
-  out->nnz_csr = d.csr.nnz;
+  out->nnz_csr = nnz_csr;
   out->csr_rows = (int32_t*)std::malloc(sizeof(int32_t) * (rows.size() + 1));
   out->csr_ptr = (int64_t*)std::malloc(sizeof(int64_t) * (rows.size() + 1));
-  out->csr_col = (int32_t*)std::malloc(sizeof(int32_t) * (size_t)(d.csr.nnz + 1));
-  out->csr_val = (double*)std::malloc(sizeof(double) * (size_t)(d.csr.nnz + 1));
+  out->csr_col = (int32_t*)std::malloc(sizeof(int32_t) * (size_t)(nnz_csr + 1));
+  out->csr_val = (double*)std::malloc(sizeof(double) * (size_t)(nnz_csr + 1));
   int64_t k = 0;
   out->csr_ptr[0] = 0;
   for (size_t x = 0; x < rows.size(); ++x) {
-    auto segs = rows[x].segs;
-    std::sort(segs.begin(), segs.end());
     out->csr_rows[x] = rows[x].row;
-    for (auto& sg : segs) {
-      for (int64_t e = item_ptr[(size_t)sg.second]; e < item_ptr[(size_t)sg.second + 1]; ++e) {
-        out->csr_col[k] = col[(size_t)e];
-        out->csr_val[k] = decode_value(&val[(size_t)(e * es)], p->dtype);
-        ++k;
-      }
+    for (auto& en : rows[x].ents) {
+      out->csr_col[k] = en.first;
+      out->csr_val[k] = en.second;
+      ++k;
     }
     out->csr_ptr[x + 1] = k;
   }

@@ -69,7 +69,7 @@ void read_vals_f64(const loops_csr* A, std::vector<double>& out);
 
 // Algorithm 1 with the structural split (see partition.cpp).
 loops_status build_canon(const loops_csr* A, const double* vals, loops_dtype dtype, int32_t br,
-                         double tau, bool contiguous, int64_t r_boundary, Canon& out);
+                         double tau, bool contiguous, int64_t r_boundary, int32_t tile_min, Canon& out);
 
 // Round raw f64 values into the dtype after scaling (used by build_canon and updates).
 double round_store(double v, double scale, loops_dtype d);
@@ -118,8 +118,11 @@ struct BcsrDev {
   std::vector<int64_t> h_unit_tiles;   // tiles per unit (host, for batched task costs)
 };
 
+// csr: rows that no BCSR block covers (written); csr_acc: rows of BCSR blocks whose sparse tiles
+// moved to the CSR part (tile-level split), added to C after the BCSR part has written it.
 struct PartDev {
   CsrDev csr;
+  CsrDev csr_acc;
   BcsrDev bcsr;
   int64_t device_bytes = 0;
 };
@@ -222,6 +225,7 @@ struct loops_plan_s {
   double tau;
   double scale;
   int32_t split_len;
+  int32_t tile_min;                    // tile-level split threshold in effect (0: off)
   loops_plan_opts opts;
   loops::Canon canon;                  // host copy (canonical order)
   loops::PartDev dev;
@@ -269,7 +273,8 @@ struct DenseArgs {
   int64_t n_rows;           // rows of C (bounds for BCSR tails)
 };
 
-cudaError_t launch_csr(const loops_plan_s* p, const CsrDev& d, const DenseArgs& a, cudaStream_t s);
+cudaError_t launch_csr(const loops_plan_s* p, const CsrDev& d, const DenseArgs& a, bool accumulate,
+                       cudaStream_t s);
 cudaError_t launch_bcsr(const loops_plan_s* p, const BcsrDev& d, const DenseArgs& a, cudaStream_t s);
 cudaError_t launch_sddmm(const loops_plan_s* p, const void* dC, int64_t lddc, const void* B,
                          int64_t ldb, void* dvals, cudaStream_t s);

@@ -172,10 +172,25 @@ struct Chunk {  // partition of a contiguous range of row blocks
 
 void partition_blocks(const loops_csr* A, const double* vals, loops_dtype dtype, int32_t br,
                       int32_t kpad, double scale, double tau, bool contiguous, int64_t rb_first,
-                      int64_t b0, int64_t b1, Chunk& out) {
+                      int32_t tile_min, int64_t b0, int64_t b1, Chunk& out) {
   const int64_t* rp = A->row_ptr;
   const int32_t* ci = A->col_idx;
   std::vector<Ent> ents;
+  std::vector<uint8_t> moved;
+  auto csr_row = [&](int64_t i, bool only_moved, int64_t i0) {
+    int64_t len = 0;
+    for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+      if (only_moved && !moved[(size_t)(k - rp[i0])]) continue;
+      out.csr_col.push_back(ci[k]);
+      out.csr_val.push_back(round_store(vals[k], scale, dtype));
+      out.csr_src.push_back(k);
+      ++len;
+    }
+    if (!only_moved || len > 0) {
+      out.csr_rows.push_back((int32_t)i);
+      out.csr_len.push_back(len);
+    }
+  };
   for (int64_t b = b0; b < b1; ++b) {
     const int64_t i0 = b * br;
     const int64_t i1 = std::min<int64_t>(i0 + br, A->n_rows);
@@ -205,22 +220,34 @@ void partition_blocks(const loops_csr* A, const double* vals, loops_dtype dtype,
       // block density nnz_rb / u compared with tau, without a division
       bcsr = (double)nnz_rb >= tau * (double)u;
     }
-    if (!bcsr) {
-      for (int64_t i = i0; i < i1; ++i) {
-        out.csr_rows.push_back((int32_t)i);
-        out.csr_len.push_back(rp[i + 1] - rp[i]);
-        for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
-          out.csr_col.push_back(ci[k]);
-          out.csr_val.push_back(round_store(vals[k], scale, dtype));
-          out.csr_src.push_back(k);
+    // tile-level split: tiles with fewer than tile_min stored entries leave the block
+    moved.assign((size_t)std::max<int64_t>(nnz_rb, 1), 0);
+    int64_t n_keep = 0;
+    if (bcsr) {
+      for (size_t y = 0; y < ents.size();) {
+        size_t z = y;
+        while (z < ents.size() && ents[z].col == ents[y].col) ++z;
+        if (tile_min > 1 && (int64_t)(z - y) < tile_min) {
+          for (size_t w = y; w < z; ++w) moved[(size_t)(ents[w].k - rp[i0])] = 1;
+        } else {
+          ++n_keep;
         }
+        y = z;
       }
+    }
+    if (!bcsr || n_keep == 0) {
+      for (int64_t i = i0; i < i1; ++i) csr_row(i, false, i0);
       continue;
     }
-    // tiles keyed by column, ascending; duplicates of (row, col) summed in input order
+    if (tile_min > 1)
+      for (int64_t i = i0; i < i1; ++i) csr_row(i, true, i0);  // the moved entries, input order
+    // kept tiles keyed by column, ascending; duplicates of (row, col) summed in input order
     const int64_t t_begin = (int64_t)out.tile_col.size();
+    int32_t last_col = 0;
     for (size_t x = 0; x < ents.size(); ++x) {
-      if (x == 0 || ents[x].col != ents[x - 1].col) {
+      if (moved[(size_t)(ents[x].k - rp[i0])]) continue;
+      if ((int64_t)out.tile_col.size() == t_begin || ents[x].col != last_col) {
+        last_col = ents[x].col;
         out.tile_col.push_back(ents[x].col);
         out.tile_val.resize(out.tile_val.size() + br, 0.0);
       }
@@ -248,7 +275,7 @@ void partition_blocks(const loops_csr* A, const double* vals, loops_dtype dtype,
 }  // namespace
 
 loops_status build_canon(const loops_csr* A, const double* vals, loops_dtype dtype, int32_t br,
-                         double tau, bool contiguous, int64_t r_boundary, Canon& out) {
+                         double tau, bool contiguous, int64_t r_boundary, int32_t tile_min, Canon& out) {
   out = Canon();
   out.n_rows = A->n_rows;
   out.n_cols = A->n_cols;
@@ -268,7 +295,7 @@ loops_status build_canon(const loops_csr* A, const double* vals, loops_dtype dty
     const int64_t b0 = std::min<int64_t>(n_blocks, t * per);
     const int64_t b1 = std::min<int64_t>(n_blocks, b0 + per);
     auto job = [&, t, b0, b1]() {
-      partition_blocks(A, vals, dtype, br, out.kpad, out.scale, tau, contiguous, rb_first, b0, b1,
+      partition_blocks(A, vals, dtype, br, out.kpad, out.scale, tau, contiguous, rb_first, tile_min, b0, b1,
                        chunks[(size_t)t]);
     };
     if (n_thr == 1) job(); else thr.emplace_back(job);

@@ -52,14 +52,15 @@ CASES = [
 @pytest.mark.parametrize("case", range(len(CASES)))
 @pytest.mark.parametrize("dtype", ["f64", "f32", "f16", "bf16"])
 @pytest.mark.parametrize("tau", [0.0, 1.0, 1.5, 2.5, math.inf])
-def test_partition_host_matches_oracle(loops_lib, case, dtype, tau):
+@pytest.mark.parametrize("tile_min", [0, 2, 3])
+def test_partition_host_matches_oracle(loops_lib, case, dtype, tau, tile_min):
     c = CASES[case]
     A = W.random_csr(c["n"], c["m"], c["d"], 100 + case, duplicates=c["dup"], unsorted=c["uns"],
                      explicit_zeros=c["zeros"])
     A.vals = A.vals * 10.0 ** np.random.default_rng(case).integers(-7, 3, A.vals.size)
     kpad = {"f64": 4, "f32": 1, "f16": 16, "bf16": 16}[dtype]
-    lib = loops_lib.partition_host(A, dtype, tau=tau)
-    ora = oracle.partition(A, dtype, k_pad=kpad, tau=tau)
+    lib = loops_lib.partition_host(A, dtype, tau=tau, tile_min=tile_min)
+    ora = oracle.partition(A, dtype, k_pad=kpad, tau=tau, tile_min=tile_min)
     assert lib["k_pad"] == kpad and lib["block_rows"] == oracle.default_block_rows(dtype)
     _compare(lib, ora)
 

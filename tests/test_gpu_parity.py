@@ -197,3 +197,53 @@ def test_spmm_host_async_pipeline(lp):
     torch.cuda.synchronize()
     for B, C in zip(Bs, Cs):
         assert rel_l2(C.numpy(), oracle.spmm(A, B.numpy())) <= TOL["f64"]
+
+
+@pytest.mark.parametrize("fmt", ["f64", "bf16"])
+def test_paper_mode_boundary_from_eq1(lp, fmt):
+    # contiguous split with r_b derived from Eq. 1 (timed pure-CSR and pure-BCSR throughputs)
+    A, B = W.laplacian_blocks(grid=64, n_blocks=128, block=8, seed=5, N=32)
+    A_r, Bg, s, B_eff = rounded_inputs(A, B, fmt)
+    plan = lp.Plan(A, 32, fmt, contiguous_split=True, r_boundary=-1)
+    info = plan.info()
+    assert 0 <= info["r_boundary"] <= A.n_rows
+    cs = torch.as_tensor(s, dtype=torch.float32).cuda() if s is not None else None
+    C = plan.spmm(to_device(torch, Bg, fmt), col_scale=cs).double().cpu().numpy()
+    assert rel_l2(C, oracle.spmm(A_r, B_eff)) <= TOL[fmt]
+    # the split is the contiguous one at that boundary (rounded up to B_r)
+    ex = plan.export()
+    ora = oracle.partition(A, fmt, k_pad={"f64": 4}.get(fmt, 16), contiguous=True, r_boundary=info["r_boundary"])
+    assert np.array_equal(ex["rb_ids"], ora["rb_ids"]) and np.array_equal(ex["csr_rows"], ora["csr_rows"])
+
+
+@pytest.mark.parametrize("fmt", FMTS)
+@pytest.mark.parametrize("tile_min", [2, 3])
+def test_tile_level_split(lp, fmt, tile_min):
+    # sparse tiles of BCSR blocks move to the CSR part, which adds them after the BCSR part
+    kpad = {"f64": 4, "f32": 1, "f16": 16, "bf16": 16}[fmt]
+    A, B = W.laplacian_blocks(grid=64, n_blocks=96, block=8, seed=9, N=40)
+    R = W.random_csr(301, 220, 0.05, 11, duplicates=True, unsorted=True, explicit_zeros=True)
+    for M, Bm in ((A, B), (R, W.dense_normal(220, 40, 3))):
+        for tau in (0.0, 1.5):
+            C, ref, plan = run_case(lp, M, Bm, fmt, tau, split_len=8)
+            assert rel_l2(C, ref) <= TOL[fmt]
+            plan2 = lp.Plan(M, 40, fmt, tau=tau, tile_min=tile_min, split_len=8)
+            assert plan2.info()["tile_min"] == tile_min
+            A_r, Bg, s, B_eff = rounded_inputs(M, Bm, fmt)
+            cs = torch.as_tensor(s, dtype=torch.float32).cuda() if s is not None else None
+            C2 = plan2.spmm(to_device(torch, Bg, fmt), col_scale=cs).double().cpu().numpy()
+            assert rel_l2(C2, ref) <= TOL[fmt]
+            ex = plan2.export()
+            ora = oracle.partition(M, fmt, k_pad=kpad, tau=tau, tile_min=tile_min)
+            for k in ("csr_rows", "csr_ptr", "csr_col", "rb_ids", "rb_ptr", "tile_col"):
+                assert np.array_equal(ex[k], ora[k]), k
+            assert np.array_equal(ex["tile_val"].view(np.uint64), ora["tile_val"].view(np.uint64))
+
+
+def test_tile_level_split_integers_bit_exact(lp):
+    A = W.random_csr(150, 140, 0.1, 3, integer_values=True, duplicates=True, unsorted=True)
+    B = np.random.default_rng(4).integers(-4, 5, size=(140, 64)).astype(np.float64)
+    for fmt in FMTS:
+        plan = lp.Plan(A, 64, fmt, tau=0.0, tile_min=2)
+        C = plan.spmm(to_device(torch, B, fmt)).double().cpu().numpy()
+        assert np.array_equal(C, oracle.spmm(A, B))
