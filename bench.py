@@ -155,9 +155,24 @@ def traffic_for(kernel_key: str):
     return d["dram_bytes_per_launch"] if sha == d["source_sha256"] else None
 
 
-def cpu_baseline(A, B, budget_s: float = 12.0):
-    """The oracle as it stands, single-threaded, on the full workload, repeated for about
-    `budget_s` seconds. Returns (GFLOP/s, C_oracle, reps)."""
+def host_cores() -> int:
+    """Host threads available to this process."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_spmm_on(A, B, threads: int):
+    """The oracle's row loop on `threads` host threads (bit-identical to one thread)."""
+    import oracle
+
+    return oracle.spmm(A, B) if threads == 1 else oracle.spmm_threads(A, B, threads)
+
+
+def cpu_baseline(A, B, threads: int = 1, budget_s: float = 12.0):
+    """The oracle as it stands on the full workload, on `threads` host threads, repeated for
+    about `budget_s` seconds. Returns (GFLOP/s, C_oracle, reps, seconds)."""
     import oracle
 
     oracle.build()
@@ -165,7 +180,7 @@ def cpu_baseline(A, B, budget_s: float = 12.0):
     reps, t_tot, C = 0, 0.0, None
     while reps < 1 or (t_tot < budget_s and reps < 200):
         t0 = time.perf_counter()
-        C = oracle.spmm(A, B)
+        C = oracle_spmm_on(A, B, threads)
         t_tot += time.perf_counter() - t0
         reps += 1
     return flops * reps / t_tot / 1e9, C, reps, t_tot
@@ -180,12 +195,13 @@ def run_reference(args):
     oracle.build()
     A, B = workload(args.N)
     flops = 2.0 * A.nnz * args.N
+    threads = host_cores()
     for _ in range(args.warmup):
-        oracle.spmm(A, B)
+        oracle_spmm_on(A, B, threads)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle.spmm(A, B)
+        oracle_spmm_on(A, B, threads)
         times.append(time.perf_counter() - t0)
     t = sum(times) / len(times)
     v = flops / t / 1e9
@@ -193,10 +209,35 @@ def run_reference(args):
             "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)", "config": config(args.N),
             "impl": "reference",
-            "cpu_baseline": {"value": v, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
-                             "sample": "full workload per step (single-threaded C oracle, FP64)"},
+            "cpu_baseline": {"value": v, "unit": "GFLOP/s", "cores": threads, "kind": "oracle",
+                             "sample": f"full workload per step (FP64 C oracle, rows split over "
+                                       f"{threads} host threads)"},
             "e2e": {"value": v, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def plan_build_compare(torch, lp, A, N, fmt, tau, reps=3):
+    """Wall time of building the same plan (fixed tau, no autotuning) on the host from host
+    arrays (loops_plan) and on the GPU from device-resident arrays (loops_plan_device), best of
+    `reps`; and whether the two partitions are identical."""
+    Ad = W.CSR(A.n_rows, A.n_cols, torch.as_tensor(A.row_ptr).cuda(), torch.as_tensor(A.col_idx).cuda(),
+               torch.as_tensor(A.vals).cuda())
+    out = {"tau": tau, "dtype": fmt}
+    plans = {}
+    for key, dev in (("host_s", False), ("device_s", True)):
+        best = math.inf
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            pl = lp.Plan(Ad if dev else A, N, fmt, tau=tau, build_on_device=dev)
+            torch.cuda.synchronize()
+            best = min(best, time.perf_counter() - t0)
+            plans[key] = pl
+        out[key] = best
+    ea, eb = plans["host_s"].export(), plans["device_s"].export()
+    out["identical"] = bool(all(np.array_equal(np.asarray(ea[k]), np.asarray(eb[k])) for k in ea))
+    out["speedup"] = out["host_s"] / out["device_s"]
+    return out
 
 
 def max_over_ranks(torch, x: float, world: int, device) -> float:
@@ -283,6 +324,7 @@ def run_loops(args):
     variants = {"csr_only": (math.inf, 0), "hybrid_tau2": (2.0, 0), "hybrid_tau2_tile_split": (2.0, 2),
                 "bcsr_only": (0.0, 0)}
     vplans = {k: lp.Plan(A, N, "f64", tau=t, tile_min=tm) for k, (t, tm) in variants.items()}
+    build_cmp = plan_build_compare(torch, lp, A, N, "f64", 2.0) if rank == 0 else None
 
     # main timed region: K steps, barrier + synchronize on both sides
     sampler = ClockSampler(local)
@@ -356,11 +398,13 @@ def run_loops(args):
         # pipelined call: step k+1's copy in overlaps step k's copy out
         for _ in range(2):
             plan.spmm_host_async(Bh, Ch)
+        plan.host_flush()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(k_e2e):
             plan.spmm_host_async(Bh, Ch)
+        plan.host_flush()
         e1.record(stream)
         torch.cuda.synchronize()
         t_e2e = e0.elapsed_time(e1) / k_e2e
@@ -375,9 +419,14 @@ def run_loops(args):
     cpu = None
     rel = None
     if world == 1:
-        v_cpu, C_ref, reps, t_tot = cpu_baseline(A, B)
-        cpu = {"value": v_cpu, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
-               "sample": f"full workload x {reps} runs ({t_tot:.1f} s, single-threaded FP64 C oracle)"}
+        threads = host_cores()
+        v_cpu, C_ref, reps, t_tot = cpu_baseline(A, B, threads, budget_s=6.0)
+        v_one, _, reps1, t_one = cpu_baseline(A, B, 1, budget_s=8.0)
+        cpu = {"value": v_cpu, "unit": "GFLOP/s", "cores": threads, "kind": "oracle",
+               "sample": f"full workload x {reps} runs ({t_tot:.1f} s, FP64 C oracle, rows split over "
+                         f"{threads} host threads)",
+               "single_thread": {"value": v_one, "cores": 1, "sample": f"full workload x {reps1} runs "
+                                                                       f"({t_one:.1f} s)"}}
         C = Cd.cpu().numpy()
         rel = float(np.linalg.norm(C - C_ref) / np.linalg.norm(C_ref))
     line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
@@ -387,6 +436,7 @@ def run_loops(args):
                            tile_min_autotuned=info["tile_min"],
                            bcsr_row_blocks=info["n_row_blocks"], bcsr_tiles=info["n_tiles"],
                            plan_build_s=plan_s),
+            "plan_build": build_cmp,
             "roofline": roofline, "hbm": hbm, "variants": var_out,
             "rel_l2_vs_oracle": rel, "rel_l2_tol": TOL_F64,
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
@@ -509,6 +559,7 @@ def run_other(args):
         ms = statistics.mean(st)
         res[name] = {"tau": inf["tau"], "gflops": flops / (ms * 1e-3) / 1e9, "ms_per_step": ms,
                      "bcsr_row_blocks": inf["n_row_blocks"], "nnz_bcsr": inf["nnz_bcsr"]}
+    build_cmp = plan_build_compare(torch, lp, A, N, fmt, 2.0)
     p = plans["autotuned"]
     inf = p.info()
     step, csr, bcsr = time_plan(torch, p, Bd, Cd, args.steps, args.warmup, flush) if sc is None else (
@@ -528,7 +579,7 @@ def run_other(args):
                          "frac": ach / hbm_peak, "traffic": None, "peak_source": hbm_src},
                hbm={"alg_bytes_per_step": alg, "achieved_gbs": alg / (ms * 1e-3) / 1e9,
                     "frac_of_measured": alg / (ms * 1e-3) / 1e9 / hbm_peak},
-               variants=res, part_ms={"csr": csr_ms, "bcsr": bcsr_ms},
+               variants=res, part_ms={"csr": csr_ms, "bcsr": bcsr_ms}, plan_build=build_cmp,
                gpu_launches=launches_per_step(inf) * args.steps)
     if wl == "gcn":
         dYd = torch.as_tensor(dY, dtype=torch.float32).cuda()

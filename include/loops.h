@@ -170,6 +170,24 @@ void loops_partition_free(loops_partition* part);
 loops_status loops_plan(const loops_csr* A, int64_t N, loops_dtype dtype,
                         const loops_plan_opts* opts, loops_stream_t stream, loops_plan_t* out);
 
+/* Build the same plan as loops_plan from a matrix whose CSR arrays are in DEVICE memory,
+ * with every step of the conversion run on the GPU on `stream`: validation, row-block
+ * analysis (nnz_rb, distinct columns), the split (Sec. 3.1, Algorithm 1 with the structural
+ * or the contiguous Eq. 1 boundary, and the tile-level split), and the packing of both parts
+ * (stable radix sorts by (row block, column), so tiles come out in ascending column order
+ * and duplicates are summed in input order). The plan equals loops_plan's on the same
+ * matrix bit for bit (loops_plan_export) and runs on the same kernels. For re-planning when
+ * the pattern changes between calls (dynamic graphs, Sec. 4.5): the matrix never travels to
+ * the host. The paper builds its format on the CPU; this on-device build has no counterpart
+ * there. Arguments as loops_plan, except: A->row_ptr, A->col_idx and A->vals are device
+ * pointers, borrowed for the call. Validation errors are those of loops_plan (the first bad
+ * row or entry is reported). The call synchronises `stream` (it reads back a few totals);
+ * with tau < 0 it autotunes exactly as loops_plan does. Plans built here (unless they use the
+ * tile-level split) also accept loops_plan_set_values without want_backward;
+ * loops_plan_update_values refreshes them through the same device maps. */
+loops_status loops_plan_device(const loops_csr* A, int64_t N, loops_dtype dtype,
+                               const loops_plan_opts* opts, loops_stream_t stream, loops_plan_t* out);
+
 /* Release a plan and its device memory (synchronises the device first). NULL is a no-op. */
 loops_status loops_plan_destroy(loops_plan_t plan);
 
@@ -186,7 +204,8 @@ loops_status loops_plan_update_values(loops_plan_t plan, const void* vals, loops
                                       loops_stream_t stream);
 
 /* Replace A's values from a DEVICE array (nnz values of vals_dtype, F64 or F32, in A's input
- * order; same pattern) for a plan built with want_backward: both parts and the transposed
+ * order; same pattern) for a plan built with want_backward (or by loops_plan_device without
+ * the tile-level split): both parts and the transposed
  * plan are refreshed by a kernel on `stream` (stored value = round(s_A * sum of the entries
  * of a slot, in input order), exactly as the host packer rounds). Stream-ordered; used by
  * the autograd path so that C = A(vals) . B follows the current values. */
@@ -211,13 +230,18 @@ loops_status loops_spmm_host(loops_plan_t plan, const void* B_host, int64_t ldb,
                              int64_t ldc, loops_stream_t stream);
 
 /* Pipelined end-to-end SpMM with HOST buffers, for a sequence of calls: like loops_spmm_host,
- * but it does not wait. Two plan-owned staging sets alternate between calls, and the copy of
- * the next call's B to the device runs on an internal stream while this call's C comes back on
- * another, so consecutive calls overlap their transfers. Each call's C_host is complete once
- * `stream` has been synchronised; B_host and C_host must stay valid and unchanged until then.
- * Calls on one plan must use the same `stream`. */
+ * but it does not wait. Two plan-owned staging sets alternate between calls; B comes in on one
+ * internal stream and C goes back on another, so the copy-in of call k+1 and the SpMM of call
+ * k+1 (on `stream`) overlap the copy-out of call k. The C_host of every call made so far is
+ * complete once loops_spmm_host_flush(plan, stream) has been called and `stream` has then been
+ * synchronised; B_host and C_host must stay valid and unchanged until then. Calls on one plan
+ * must use the same `stream`. */
 loops_status loops_spmm_host_async(loops_plan_t plan, const void* B_host, int64_t ldb, void* C_host,
                                    int64_t ldc, loops_stream_t stream);
+
+/* Make `stream` wait for the copy-out of the last loops_spmm_host_async call on this plan
+ * (stream-ordered, no host wait). */
+loops_status loops_spmm_host_flush(loops_plan_t plan, loops_stream_t stream);
 
 /* Backward of C = A . B for a plan built with want_backward:
  *   dB = A^T . dC  (transposed hybrid SpMM; dB device, n_cols x N, lddb; NULL to skip)

@@ -33,7 +33,7 @@ EXPORTED = ["loops_version", "loops_status_str", "loops_last_error", "loops_plan
             "loops_spmm_scaled", "loops_spmm_host", "loops_spmm_backward", "loops_cast_scaled",
             "loops_plan_check", "loops_plan_set_timing_events", "loops_plan_set_values",
             "loops_csr_spmm_noalloc", "loops_plan_batched", "loops_spmm_batched", "loops_plan_batched_info",
-            "loops_spmm_host_async"]
+            "loops_spmm_host_async", "loops_spmm_host_flush", "loops_plan_device"]
 
 
 class LoopsError(RuntimeError):
@@ -103,6 +103,8 @@ def load():
     L.loops_partition_free.argtypes = [ctypes.POINTER(_Part)]
     L.loops_partition_free.restype = None
     L.loops_plan.argtypes = [ctypes.POINTER(_Csr), i64, ctypes.c_int, ctypes.POINTER(_Opts), vp, ctypes.POINTER(vp)]
+    L.loops_plan_device.argtypes = [ctypes.POINTER(_Csr), i64, ctypes.c_int, ctypes.POINTER(_Opts), vp,
+                                    ctypes.POINTER(vp)]
     L.loops_plan_destroy.argtypes = [vp]
     L.loops_plan_info_get.argtypes = [vp, ctypes.POINTER(_Info)]
     L.loops_plan_export.argtypes = [vp, ctypes.POINTER(_Part)]
@@ -111,6 +113,7 @@ def load():
     L.loops_spmm_scaled.argtypes = [vp, vp, i64, vp, vp, i64, vp]
     L.loops_spmm_host.argtypes = [vp, vp, i64, vp, i64, vp]
     L.loops_spmm_host_async.argtypes = [vp, vp, i64, vp, i64, vp]
+    L.loops_spmm_host_flush.argtypes = [vp, vp]
     L.loops_spmm_backward.argtypes = [vp, vp, i64, vp, i64, vp, i64, vp, vp]
     L.loops_cast_scaled.argtypes = [vp, i64, i64, i64, ctypes.c_int, vp, i64, vp, vp]
     L.loops_plan_check.argtypes = [vp, vp]
@@ -149,6 +152,25 @@ def _csr_struct(A):
         vd = F64
     s = _Csr(int(A.n_rows), int(A.n_cols), int(rp[-1]) if rp.size else 0, rp.ctypes.data, ci.ctypes.data,
              v.ctypes.data, vd)
+    return s, (rp, ci, v)
+
+
+def _csr_struct_device(A):
+    """A's CSR arrays as CUDA tensors (copied to the device if they are host arrays) ->
+    (_Csr with device pointers, keepalive)."""
+    torch = _torch()
+
+    def dev(x, dt):
+        t = x if isinstance(x, torch.Tensor) else torch.as_tensor(np.ascontiguousarray(x))
+        return t.to(device="cuda", dtype=dt).contiguous()
+
+    rp = dev(A.row_ptr, torch.int64)
+    ci = dev(A.col_idx, torch.int32)
+    v0 = A.vals
+    f32 = (v0.dtype == torch.float32) if isinstance(v0, torch.Tensor) else (np.asarray(v0).dtype == np.float32)
+    v = dev(v0, torch.float32 if f32 else torch.float64)
+    s = _Csr(int(A.n_rows), int(A.n_cols), int(ci.numel()), rp.data_ptr(), ci.data_ptr(), v.data_ptr(),
+             F32 if f32 else F64)
     return s, (rp, ci, v)
 
 
@@ -215,19 +237,26 @@ class Plan:
 
     def __init__(self, A, N: int, dtype: str = "f64", tau: float = 2.0, block_rows: int = 0,
                  want_backward: bool = False, contiguous_split: bool = False, r_boundary: int = 0,
-                 split_len: int = 0, tile_min=None, stream=None):
+                 split_len: int = 0, tile_min=None, stream=None, build_on_device: bool = False):
+        """build_on_device: run the whole conversion on the GPU (``loops_plan_device``); A's
+        arrays may then be CUDA tensors (host arrays are copied to the device first)."""
         L = load()
         self._L = L
         self.dtype = _DT[dtype]
         self.dtype_name = dtype
         self.N = int(N)
         self.n_rows, self.n_cols = int(A.n_rows), int(A.n_cols)
-        self.nnz = int(np.asarray(A.row_ptr)[-1]) if len(A.row_ptr) else 0
-        cs, keep = _csr_struct(A)
         o = _opts(tau, block_rows, contiguous_split, r_boundary, want_backward, split_len, tile_min)
         h = ctypes.c_void_p()
         s = _stream_handle(stream) if _torch().cuda.is_available() else ctypes.c_void_p(0)
-        _check(L.loops_plan(ctypes.byref(cs), self.N, self.dtype, ctypes.byref(o), s, ctypes.byref(h)))
+        if build_on_device:
+            cs, keep = _csr_struct_device(A)
+            self.nnz = int(cs.nnz)
+            _check(L.loops_plan_device(ctypes.byref(cs), self.N, self.dtype, ctypes.byref(o), s, ctypes.byref(h)))
+        else:
+            self.nnz = int(np.asarray(A.row_ptr)[-1]) if len(A.row_ptr) else 0
+            cs, keep = _csr_struct(A)
+            _check(L.loops_plan(ctypes.byref(cs), self.N, self.dtype, ctypes.byref(o), s, ctypes.byref(h)))
         self._h = h
 
     @property
@@ -322,11 +351,15 @@ class Plan:
         return C_host
 
     def spmm_host_async(self, B_host, C_host, stream=None):
-        """Pipelined end-to-end C = A . B with pinned host tensors; C_host is complete after the
-        stream is synchronised (consecutive calls overlap their transfers)."""
+        """Pipelined end-to-end C = A . B with pinned host tensors (consecutive calls overlap
+        their transfers); C_host is complete after host_flush() and a stream synchronisation."""
         _check(self._L.loops_spmm_host_async(self._h, B_host.data_ptr(), B_host.stride(0), C_host.data_ptr(),
                                              C_host.stride(0), _stream_handle(stream)))
         return C_host
+
+    def host_flush(self, stream=None):
+        """Make the stream wait for the last pipelined call's copy-out."""
+        _check(self._L.loops_spmm_host_flush(self._h, _stream_handle(stream)))
 
     def backward(self, dC, B, need_dB=True, need_dvals=True, stream=None):
         """(dB, dvals) = (A^T . dC, <dC[i_k], B[j_k]> per stored entry in input order)."""

@@ -1,5 +1,6 @@
 // C-ABI entry points of libloops.so (declared in include/loops.h).
 #include <algorithm>
+#include <functional>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -15,9 +16,11 @@ void set_error(const std::string& msg) { g_last_error = msg; }
 void clear_error() { g_last_error.clear(); }
 
 loops_status export_part(const loops_plan_s* p, loops_partition* out);
-loops_status autotune_tau(const loops_csr* A, const double* vals, int64_t N, loops_dtype dtype,
-                          int32_t br, int32_t split_len, bool try_tile_split, cudaStream_t s, double* tau_out,
-                          int32_t* tile_min_out);
+// Builds a candidate plan for the given options and threshold (host or device builder).
+using PlanBuilder = std::function<loops_status(const loops_plan_opts& o, double tau, loops_plan_s** out)>;
+loops_status autotune_tau(const PlanBuilder& build, int64_t n_rows, int64_t n_cols, int64_t nnz, int64_t N,
+                          loops_dtype dtype, int32_t split_len, bool try_tile_split, cudaStream_t s,
+                          double* tau_out, int32_t* tile_min_out);
 
 loops_status cuda_status(cudaError_t e, const char* what) {
   if (e == cudaSuccess) return LOOPS_OK;
@@ -119,16 +122,16 @@ void destroy_plan(loops_plan_s* p) {
 }
 
 // Builds a single (non-transposed) plan from validated input and f64 values.
-loops_status make_plan(const loops_csr* A, const double* vals, int64_t N, loops_dtype dtype,
-                       const loops_plan_opts& o, int32_t br, double tau, bool light, loops_plan_s** out) {
-  *out = nullptr;
+// A plan object with its fields set from the arguments and no device part yet.
+static loops_plan_s* new_plan(int64_t n_rows, int64_t n_cols, int64_t nnz, int64_t N, loops_dtype dtype,
+                              const loops_plan_opts& o, int32_t br, double tau) {
   loops_plan_s* p = new (std::nothrow) loops_plan_s();
-  if (!p) { set_error("host allocation failed"); return LOOPS_ERR_OOM; }
+  if (!p) { set_error("host allocation failed"); return nullptr; }
   p->magic = kPlanMagic;
   p->dtype = dtype;
-  p->n_rows = A->n_rows;
-  p->n_cols = A->n_cols;
-  p->nnz = A->nnz;
+  p->n_rows = n_rows;
+  p->n_cols = n_cols;
+  p->nnz = nnz;
   p->N = N;
   p->br = br;
   p->kpad = k_pad_for(dtype);
@@ -147,6 +150,32 @@ loops_status make_plan(const loops_csr* A, const double* vals, int64_t N, loops_
   for (auto& ev : p->tev) ev = nullptr;
   p->batch = nullptr;
   p->other_bytes = 0;
+  p->n_csr_rows = p->nnz_csr = p->n_rb = p->n_tiles = 0;
+  p->device_built = false;
+  p->has_vmap = false;
+  p->n_subnormal = 0;
+  p->nnz_bcsr = 0;
+  p->scale = 1.0;
+  return p;
+}
+
+// Error word, side stream and fork/join events of a plan that runs SpMM calls.
+static loops_status plan_runtime(loops_plan_s* p) {
+  cudaError_t e = cudaMalloc((void**)&p->d_error, sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMemset(p->d_error, 0, sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming);
+  if (e != cudaSuccess) return cuda_status(e, "plan setup");
+  p->other_bytes += sizeof(int32_t);
+  return LOOPS_OK;
+}
+
+loops_status make_plan(const loops_csr* A, const double* vals, int64_t N, loops_dtype dtype,
+                       const loops_plan_opts& o, int32_t br, double tau, bool light, loops_plan_s** out) {
+  *out = nullptr;
+  loops_plan_s* p = new_plan(A->n_rows, A->n_cols, A->nnz, N, dtype, o, br, tau);
+  if (!p) return LOOPS_ERR_OOM;
   loops_status st = build_canon(A, vals, dtype, br, tau, o.contiguous_split != 0, o.r_boundary, p->tile_min,
                                 p->canon);
   if (st) { destroy_plan(p); return st; }
@@ -159,18 +188,29 @@ loops_status make_plan(const loops_csr* A, const double* vals, int64_t N, loops_
   }
   p->nnz_bcsr = 0;
   for (uint8_t k : p->canon.src_kind) p->nnz_bcsr += k;
+  p->n_csr_rows = (int64_t)p->canon.csr_rows.size();
+  p->nnz_csr = (int64_t)p->canon.csr_col.size();
+  p->n_rb = (int64_t)p->canon.rb_ids.size();
+  p->n_tiles = (int64_t)p->canon.tile_col.size();
   if ((st = upload_part(p, N))) { destroy_plan(p); return st; }
-  if (light) {
-    *out = p;
-    return LOOPS_OK;
-  }
-  cudaError_t e = cudaMalloc((void**)&p->d_error, sizeof(int32_t));
-  if (e == cudaSuccess) e = cudaMemset(p->d_error, 0, sizeof(int32_t));
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming);
-  if (e != cudaSuccess) { st = cuda_status(e, "plan setup"); destroy_plan(p); return st; }
-  p->other_bytes += sizeof(int32_t);
+  if (!light && (st = plan_runtime(p))) { destroy_plan(p); return st; }
+  *out = p;
+  return LOOPS_OK;
+}
+
+// The same plan built on the device from a device-resident CSR matrix (plan_device.cu).
+static loops_status make_plan_device(const DevCsrIn& A, const int64_t* remap, double scale, int64_t N,
+                                     loops_dtype dtype, const loops_plan_opts& o, int32_t br, double tau,
+                                     bool want_maps, cudaStream_t s, loops_plan_s** out) {
+  *out = nullptr;
+  loops_plan_s* p = new_plan(A.n_rows, A.n_cols, A.nnz, N, dtype, o, br, tau);
+  if (!p) return LOOPS_ERR_OOM;
+  p->device_built = true;
+  p->scale = scale;
+  loops_status st = build_part_device(p, A, remap, N, tau, o.contiguous_split != 0, o.r_boundary,
+                                      want_maps && p->tile_min == 0, s);
+  if (!st) st = plan_runtime(p);
+  if (st) { destroy_plan(p); return st; }
   *out = p;
   return LOOPS_OK;
 }
@@ -288,9 +328,9 @@ static cudaError_t fill_finite(void* p, int64_t bytes, cudaStream_t s) {
 // Autotuner (replaces the paper's Eq. 2/Eq. 3 CPU model): times C = A.B for candidate split
 // thresholds on synthetic B and keeps the fastest. Candidates that give the same row-block
 // split as an earlier one are skipped.
-loops_status autotune_tau(const loops_csr* A, const double* vals, int64_t N, loops_dtype dtype, int32_t br,
-                          int32_t split_len, bool try_tile_split, cudaStream_t s, double* tau_out,
-                          int32_t* tile_min_out) {
+loops_status autotune_tau(const PlanBuilder& build, int64_t n_rows, int64_t n_cols, int64_t nnz, int64_t N,
+                          loops_dtype dtype, int32_t split_len, bool try_tile_split, cudaStream_t s,
+                          double* tau_out, int32_t* tile_min_out) {
   struct Cand { double tau; int32_t tile_min; };
   std::vector<Cand> cands;
   for (double t : {(double)INFINITY, 8.0, 4.0, 3.0, 2.0, 1.5, 1.25, 0.0}) cands.push_back({t, 0});
@@ -298,12 +338,12 @@ loops_status autotune_tau(const loops_csr* A, const double* vals, int64_t N, loo
     for (double t : {4.0, 2.0, 1.25}) cands.push_back({t, 2});
   *tau_out = 2.0;
   *tile_min_out = 0;
-  if (A->nnz == 0 || N == 0 || A->n_rows == 0) return LOOPS_OK;
+  if (nnz == 0 || N == 0 || n_rows == 0) return LOOPS_OK;
   const int64_t eb = dense_elem_bytes(dtype), ec = out_elem_bytes(dtype);
   void *dB = nullptr, *dC = nullptr;
-  cudaError_t e = cudaMalloc(&dB, (size_t)std::max<int64_t>(A->n_cols * N * eb, 16));
-  if (e == cudaSuccess) e = cudaMalloc(&dC, (size_t)std::max<int64_t>(A->n_rows * N * ec, 16));
-  if (e == cudaSuccess) e = fill_finite(dB, A->n_cols * N * eb, s);
+  cudaError_t e = cudaMalloc(&dB, (size_t)std::max<int64_t>(n_cols * N * eb, 16));
+  if (e == cudaSuccess) e = cudaMalloc(&dC, (size_t)std::max<int64_t>(n_rows * N * ec, 16));
+  if (e == cudaSuccess) e = fill_finite(dB, n_cols * N * eb, s);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
@@ -318,8 +358,8 @@ loops_status autotune_tau(const loops_csr* A, const double* vals, int64_t N, loo
     const double tau = cand.tau;
     o.tile_min = cand.tile_min;
     loops_plan_s* p = nullptr;
-    if ((st = make_plan(A, vals, N, dtype, o, br, tau, false, &p))) break;
-    const std::pair<int64_t, int64_t> key((int64_t)p->canon.rb_ids.size(), (int64_t)p->canon.tile_col.size());
+    if ((st = build(o, tau, &p))) break;
+    const std::pair<int64_t, int64_t> key(p->n_rb, p->n_tiles);
     if (std::find(seen.begin(), seen.end(), key) != seen.end()) { destroy_plan(p); continue; }
     seen.push_back(key);
     float best_ms = INFINITY;
@@ -348,15 +388,15 @@ loops_status autotune_tau(const loops_csr* A, const double* vals, int64_t N, loo
 // configuration) and the pure BCSR plan (rows from 0 on in BCSR) on synthetic B, take each
 // part's throughput TP = rows / time, and choose r_b so that the two parts, running side by
 // side, take the same time: r_b / TP_csr = (n_rows - r_b) / TP_bcsr.
-loops_status model_boundary(const loops_csr* A, const double* vals, int64_t N, loops_dtype dtype, int32_t br,
-                            int32_t split_len, cudaStream_t s, int64_t* rb_out) {
-  *rb_out = A->n_rows;
-  if (A->nnz == 0 || N == 0 || A->n_rows == 0) return LOOPS_OK;
+loops_status model_boundary(const PlanBuilder& build, int64_t n_rows, int64_t n_cols, int64_t nnz, int64_t N,
+                            loops_dtype dtype, int32_t split_len, cudaStream_t s, int64_t* rb_out) {
+  *rb_out = n_rows;
+  if (nnz == 0 || N == 0 || n_rows == 0) return LOOPS_OK;
   const int64_t eb = dense_elem_bytes(dtype), ec = out_elem_bytes(dtype);
   void *dB = nullptr, *dC = nullptr;
-  cudaError_t e = cudaMalloc(&dB, (size_t)std::max<int64_t>(A->n_cols * N * eb, 16));
-  if (e == cudaSuccess) e = cudaMalloc(&dC, (size_t)std::max<int64_t>(A->n_rows * N * ec, 16));
-  if (e == cudaSuccess) e = fill_finite(dB, A->n_cols * N * eb, s);
+  cudaError_t e = cudaMalloc(&dB, (size_t)std::max<int64_t>(n_cols * N * eb, 16));
+  if (e == cudaSuccess) e = cudaMalloc(&dC, (size_t)std::max<int64_t>(n_rows * N * ec, 16));
+  if (e == cudaSuccess) e = fill_finite(dB, n_cols * N * eb, s);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
@@ -369,7 +409,7 @@ loops_status model_boundary(const loops_csr* A, const double* vals, int64_t N, l
     o.contiguous_split = which;          // 0: tau = inf (all CSR); 1: r_b = 0 (all BCSR)
     o.r_boundary = 0;
     loops_plan_s* p = nullptr;
-    if ((st = make_plan(A, vals, N, dtype, o, br, INFINITY, false, &p))) break;
+    if ((st = build(o, INFINITY, &p))) break;
     for (int it = 0; it < 7 && !st; ++it) {
       if (it >= 2) cudaEventRecord(e0, s);
       st = run_spmm(p, dB, N, nullptr, dC, N, s);
@@ -388,9 +428,9 @@ loops_status model_boundary(const loops_csr* A, const double* vals, int64_t N, l
   if (dB) cudaFree(dB);
   if (dC) cudaFree(dC);
   if (st) return st;
-  const double tp_csr = (double)A->n_rows / std::max((double)t[0], 1e-9);
-  const double tp_bcsr = (double)A->n_rows / std::max((double)t[1], 1e-9);
-  *rb_out = (int64_t)std::llround((double)A->n_rows * tp_csr / (tp_csr + tp_bcsr));
+  const double tp_csr = (double)n_rows / std::max((double)t[0], 1e-9);
+  const double tp_bcsr = (double)n_rows / std::max((double)t[1], 1e-9);
+  *rb_out = (int64_t)std::llround((double)n_rows * tp_csr / (tp_csr + tp_bcsr));
   return LOOPS_OK;
 }
 
@@ -483,13 +523,20 @@ loops_status loops_plan(const loops_csr* A, int64_t N, loops_dtype dtype, const 
   double tau = o.tau;
   if (tau < 0.0 && !o.contiguous_split) {
     int32_t tmin = o.tile_min;
-    if ((st = autotune_tau(A, vals.data(), N, dtype, br, o.split_len, tmin < 0 && !o.want_backward,
-                           (cudaStream_t)stream, &tau, &tmin)))
+    const PlanBuilder host_build = [&](const loops_plan_opts& oc, double t, loops_plan_s** q) {
+      return make_plan(A, vals.data(), N, dtype, oc, br, t, false, q);
+    };
+    if ((st = autotune_tau(host_build, A->n_rows, A->n_cols, A->nnz, N, dtype, o.split_len,
+                           tmin < 0 && !o.want_backward, (cudaStream_t)stream, &tau, &tmin)))
       return st;
     o.tile_min = tmin;
   }
   if (o.contiguous_split && o.r_boundary < 0) {
-    if ((st = model_boundary(A, vals.data(), N, dtype, br, o.split_len, (cudaStream_t)stream, &o.r_boundary)))
+    const PlanBuilder host_build = [&](const loops_plan_opts& oc, double t, loops_plan_s** q) {
+      return make_plan(A, vals.data(), N, dtype, oc, br, t, false, q);
+    };
+    if ((st = model_boundary(host_build, A->n_rows, A->n_cols, A->nnz, N, dtype, o.split_len,
+                             (cudaStream_t)stream, &o.r_boundary)))
       return st;
   }
   loops_plan_s* p = nullptr;
@@ -517,7 +564,83 @@ loops_status loops_plan(const loops_csr* A, int64_t N, loops_dtype dtype, const 
     if ((st = build_sddmm(p, A))) { destroy_plan(p); return st; }
     if ((st = upload_value_maps(p, nullptr))) { destroy_plan(p); return st; }
     if ((st = upload_value_maps(pt, &p->t_perm))) { destroy_plan(p); return st; }
+    p->has_vmap = pt->has_vmap = true;
   }
+  *out = p;
+  return LOOPS_OK;
+}
+
+loops_status loops_plan_device(const loops_csr* A, int64_t N, loops_dtype dtype, const loops_plan_opts* opts,
+                               loops_stream_t stream, loops_plan_t* out) {
+  clear_error();
+  if (!out) { set_error("out is NULL"); return LOOPS_ERR_INVALID_ARG; }
+  *out = nullptr;
+  if (!A) { set_error("A is NULL"); return LOOPS_ERR_INVALID_ARG; }
+  if (!valid_dtype(dtype)) { set_error("bad dtype"); return LOOPS_ERR_INVALID_ARG; }
+  if (N < 0) { set_error("N < 0"); return LOOPS_ERR_INVALID_ARG; }
+  if (N > (1 << 20)) { set_error("N above 2^20 is not supported"); return LOOPS_ERR_UNSUPPORTED; }
+  loops_plan_opts o;
+  loops_plan_opts_default(&o);
+  if (opts) o = *opts;
+  if (std::isnan(o.tau)) { set_error("tau is NaN"); return LOOPS_ERR_INVALID_ARG; }
+  if (A->vals_dtype != LOOPS_F64 && A->vals_dtype != LOOPS_F32) {
+    set_error("A values must be LOOPS_F64 or LOOPS_F32 on input");
+    return LOOPS_ERR_UNSUPPORTED;
+  }
+  loops_status st;
+  int32_t br;
+  if ((st = resolve_block_rows(dtype, o, &br))) return st;
+  if (o.split_len < 0) { set_error("split_len < 0"); return LOOPS_ERR_INVALID_ARG; }
+  if (o.want_backward && o.tile_min > 1) {
+    set_error("the tile-level split is not available with want_backward");
+    return LOOPS_ERR_UNSUPPORTED;
+  }
+  const cudaStream_t s = (cudaStream_t)stream;
+  const DevCsrIn d{A->n_rows, A->n_cols, A->nnz, A->row_ptr, A->col_idx, A->vals, A->vals_dtype == LOOPS_F32};
+  double max_abs = 0.0;
+  if ((st = validate_csr_device(d, dtype, s, &max_abs))) return st;
+  const double scale = plan_scale_from_max(max_abs, dtype);
+  const PlanBuilder dev_build = [&](const loops_plan_opts& oc, double t, loops_plan_s** q) {
+    return make_plan_device(d, nullptr, scale, N, dtype, oc, br, t, false, s, q);
+  };
+  double tau = o.tau;
+  if (tau < 0.0 && !o.contiguous_split) {
+    int32_t tmin = o.tile_min;
+    if ((st = autotune_tau(dev_build, A->n_rows, A->n_cols, A->nnz, N, dtype, o.split_len,
+                           tmin < 0 && !o.want_backward, s, &tau, &tmin)))
+      return st;
+    o.tile_min = tmin;
+  }
+  if (o.contiguous_split && o.r_boundary < 0) {
+    if ((st = model_boundary(dev_build, A->n_rows, A->n_cols, A->nnz, N, dtype, o.split_len, s, &o.r_boundary)))
+      return st;
+  }
+  loops_plan_s* p = nullptr;
+  if ((st = make_plan_device(d, nullptr, scale, N, dtype, o, br, tau, true, s, &p))) return st;
+  if (o.want_backward) {
+    int64_t* trp = nullptr;
+    int32_t* tci = nullptr;
+    double* tv = nullptr;
+    int64_t* perm = nullptr;
+    st = transpose_device(d, &trp, &tci, &tv, &perm, s);
+    if (!st) {
+      const DevCsrIn dt{A->n_cols, A->n_rows, A->nnz, trp, tci, tv, 0};
+      loops_plan_opts ot = o;
+      ot.want_backward = 0;
+      ot.contiguous_split = 0;
+      loops_plan_s* pt = nullptr;
+      st = make_plan_device(dt, perm, scale, N, dtype, ot, br, tau, true, s, &pt);
+      p->transposed = pt;
+    }
+    if (!st) st = build_sddmm_device(p, d, s);
+    cudaStreamSynchronize(s);
+    void* tmp[] = {trp, tci, tv, perm};
+    for (void* q : tmp)
+      if (q) cudaFree(q);
+    if (st) { destroy_plan(p); return st; }
+  }
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) { destroy_plan(p); return cuda_status(e, "device plan build"); }
   *out = p;
   return LOOPS_OK;
 }
@@ -548,10 +671,10 @@ loops_status loops_plan_info_get(loops_plan_t p, loops_plan_info* out) {
   out->N = p->N;
   out->tau = p->tau;
   out->scale = p->scale;
-  out->n_csr_rows = (int64_t)p->canon.csr_rows.size();
-  out->nnz_csr = (int64_t)p->canon.csr_col.size();
-  out->n_row_blocks = (int64_t)p->canon.rb_ids.size();
-  out->n_tiles = (int64_t)p->canon.tile_col.size();
+  out->n_csr_rows = p->n_csr_rows;
+  out->nnz_csr = p->nnz_csr;
+  out->n_row_blocks = p->n_rb;
+  out->n_tiles = p->n_tiles;
   out->nnz_bcsr = p->nnz_bcsr;
   out->n_split_rows = p->dev.csr.n_split;
   out->n_segments = p->dev.csr.n_slots;
@@ -584,6 +707,22 @@ loops_status loops_plan_update_values(loops_plan_t p, const void* vals, loops_dt
   if (st) return st;
   if (!vals && p->nnz) { set_error("vals is NULL"); return LOOPS_ERR_INVALID_ARG; }
   if (vd != LOOPS_F64 && vd != LOOPS_F32) { set_error("vals must be F64 or F32"); return LOOPS_ERR_UNSUPPORTED; }
+  if (p->device_built) {  // no host copy of the partition: refresh through the device value maps
+    if (!p->has_vmap) {
+      set_error("values of a device-built plan with the tile-level split cannot be updated");
+      return LOOPS_ERR_UNSUPPORTED;
+    }
+    const size_t bytes = (size_t)p->nnz * (vd == LOOPS_F64 ? 8 : 4);
+    void* dv = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = bytes ? cudaMalloc(&dv, bytes) : cudaSuccess;
+    if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(dv, vals, bytes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = launch_set_values(p, dv, vd, s);
+    if (e == cudaSuccess && p->transposed) e = launch_set_values(p->transposed, dv, vd, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (dv) cudaFree(dv);
+    return cuda_status(e, "value update");
+  }
   std::vector<double> v((size_t)p->nnz);
   for (int64_t k = 0; k < p->nnz; ++k) v[(size_t)k] = vd == LOOPS_F64 ? ((const double*)vals)[k] : (double)((const float*)vals)[k];
   cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
@@ -614,15 +753,16 @@ loops_status loops_plan_set_values(loops_plan_t p, const void* vals, loops_dtype
   clear_error();
   loops_status st = check_single(p);
   if (st) return st;
-  if (!p->transposed) {
-    set_error("plan was built without want_backward (no device value maps)");
+  if (!p->has_vmap) {
+    set_error("plan has no device value maps (built on the host without want_backward, or with the "
+              "tile-level split)");
     return LOOPS_ERR_STATE;
   }
   if (vd != LOOPS_F64 && vd != LOOPS_F32) { set_error("vals must be F64 or F32"); return LOOPS_ERR_UNSUPPORTED; }
   if (!vals && p->nnz) { set_error("vals is NULL"); return LOOPS_ERR_INVALID_ARG; }
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = launch_set_values(p, vals, vd, s);
-  if (e == cudaSuccess) e = launch_set_values(p->transposed, vals, vd, s);
+  if (e == cudaSuccess && p->transposed) e = launch_set_values(p->transposed, vals, vd, s);
   return cuda_status(e, "value refresh launch");
 }
 
@@ -735,8 +875,8 @@ loops_status loops_spmm_host_async(loops_plan_t p, const void* B_host, int64_t l
   if (e != cudaSuccess) return cuda_status(e, "host pipeline");
   if ((st = run_spmm(p, h->B[i], p->N, nullptr, h->C[i], p->N, s))) return st;
   e = cudaEventRecord(h->compute_done[i], s);
-  // copy out on its own stream; the caller's stream then waits for it, so synchronising the
-  // caller's stream completes this call (the next call's copy-in overlaps this copy-out)
+  // copy out on its own stream: the next call's copy-in and SpMM overlap it; the caller's
+  // stream waits for it only in loops_spmm_host_flush (or when this C set is reused)
   if (e == cudaSuccess) e = cudaStreamWaitEvent(h->s_out, h->compute_done[i], 0);
   if (e == cudaSuccess && need_C) {
     if (ldc == p->N)
@@ -746,9 +886,18 @@ loops_status loops_spmm_host_async(loops_plan_t p, const void* B_host, int64_t l
                             (size_t)p->n_rows, cudaMemcpyDeviceToHost, h->s_out);
   }
   if (e == cudaSuccess) e = cudaEventRecord(h->out_done[i], h->s_out);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->out_done[i], 0);
   h->used[i] = true;
+  h->last = i;
   return cuda_status(e, "host pipeline");
+}
+
+loops_status loops_spmm_host_flush(loops_plan_t p, loops_stream_t stream) {
+  clear_error();
+  loops_status st = check_single(p);
+  if (st) return st;
+  if (!p->pipe || p->pipe->last < 0) return LOOPS_OK;
+  return cuda_status(cudaStreamWaitEvent((cudaStream_t)stream, p->pipe->out_done[p->pipe->last], 0),
+                     "host pipeline flush");
 }
 
 loops_status loops_spmm_backward(loops_plan_t p, const void* dC, int64_t lddc, const void* B, int64_t ldb,

@@ -14,15 +14,18 @@
 #include "loops_internal.h"
 
 // Tuning knobs of the memory-bound (non-FP64) CSR kernel: B-row loads kept in flight per
-// lane, and the minimum resident blocks per SM the register allocation must allow.
+// lane (per column vector), the minimum resident blocks per SM the register allocation must
+// allow, and the 16-byte column vectors each lane owns. Two vectors per lane with two
+// entries in flight (four 16-byte loads per lane) measured fastest on GB300 for the R-MAT
+// FP16 (N = 128) and GCN FP32 (N = 256) workloads.
 #ifndef LOOPS_CSR_UNROLL
-#define LOOPS_CSR_UNROLL 4
+#define LOOPS_CSR_UNROLL 2
 #endif
 #ifndef LOOPS_CSR_MIN_BLOCKS
 #define LOOPS_CSR_MIN_BLOCKS 4
 #endif
 #ifndef LOOPS_CSR_LANE_VECTORS
-#define LOOPS_CSR_LANE_VECTORS 1
+#define LOOPS_CSR_LANE_VECTORS 2
 #endif
 
 namespace loops {
@@ -64,12 +67,15 @@ __device__ __forceinline__ float out_scale<TrBF16>(const CsrKArgs& a, int64_t n)
 
 // Vector path: N % VE == 0, B/C/ld aligned for 16-byte B loads and vector C stores.
 // FP64: 8 resident blocks (at most 32 registers) keep enough warps in flight to feed the FP64
-// pipe; the other formats use the tuning knob.
-template <class Tr>
-constexpr int csr_min_blocks() { return std::is_same<Tr, TrF64>::value ? 8 : LOOPS_CSR_MIN_BLOCKS; }
+// pipe with one vector per lane; two vectors (N > 64) need 4 blocks (64 registers) to stay out
+// of local memory. The other formats use the tuning knob.
+template <class Tr, int VPL>
+constexpr int csr_min_blocks() {
+  return std::is_same<Tr, TrF64>::value ? (VPL == 1 ? 8 : 4) : LOOPS_CSR_MIN_BLOCKS;
+}
 
 template <class Tr, int G, int VPL, int U>
-__global__ void __launch_bounds__(256, csr_min_blocks<Tr>()) csr_spmm_vec(CsrKArgs a) {
+__global__ void __launch_bounds__(256, (csr_min_blocks<Tr, VPL>())) csr_spmm_vec(CsrKArgs a) {
   using TB = typename Tr::TB;
   using TAcc = typename Tr::TAcc;
   using TC = typename Tr::TC;
@@ -275,8 +281,9 @@ cudaError_t launch_vec_g(const CsrKArgs& a, cudaStream_t s) {
   dim3 grid((unsigned)((threads + 255) / 256), (unsigned)chunks);
   // F64 is bound by the FP64 pipe: one entry at a time, so no FMA is ever spent on a padded
   // slot (a predicated-off DFMA still occupies the pipe) and registers stay low for occupancy.
-  // The other formats are bound by memory: U loads in flight per lane.
-  constexpr int U = std::is_same<Tr, TrF64>::value ? 1 : ((G >= 8) ? LOOPS_CSR_UNROLL : 4);
+  // The other formats are bound by memory: U x VPL loads in flight per lane (narrow groups with
+  // one vector per lane take four entries at a time, the register budget allows it).
+  constexpr int U = std::is_same<Tr, TrF64>::value ? 1 : ((G >= 8 || VPL > 1) ? LOOPS_CSR_UNROLL : 4);
   csr_spmm_vec<Tr, G, VPL, U><<<grid, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
@@ -309,12 +316,14 @@ cudaError_t launch_csr_t(const loops_plan_s* p, const CsrDev& d, const DenseArgs
   if (a.n_items > 0) {
     if (vec) {
       const int64_t nvec = a.N / VE;
-      // lanes per item: the 16-byte vectors of a row, LOOPS_CSR_LANE_VECTORS per lane (more
-      // vectors per lane: fewer shuffles per byte and more loads in flight per lane)
+      // lanes per item: the 16-byte vectors of a row, LOOPS_CSR_LANE_VECTORS per lane while
+      // the group keeps at least 8 lanes (more vectors per lane: fewer shuffles per byte and
+      // more loads in flight per lane; narrower groups lose more to the per-row overhead)
       constexpr int LV = LOOPS_CSR_LANE_VECTORS;
-      const int64_t nv = std::is_same<Tr, TrF64>::value ? nvec : (nvec + LV - 1) / LV;
+      const bool lv = !std::is_same<Tr, TrF64>::value && LV > 1 && nvec >= 8 * LV;
+      const int64_t nv = lv ? (nvec + LV - 1) / LV : nvec;
       const int G = next_pow2(nv);
-      const bool two = std::is_same<Tr, TrF64>::value ? nvec > 32 : (LV > 1 && nvec > 1) || nvec > 32;
+      const bool two = lv || nvec > 32;
       switch (G) {
         case 1: e = two ? launch_vec_g<Tr, 1, 2>(a, s) : launch_vec_g<Tr, 1, 1>(a, s); break;
         case 2: e = two ? launch_vec_g<Tr, 2, 2>(a, s) : launch_vec_g<Tr, 2, 1>(a, s); break;
@@ -521,16 +530,6 @@ __global__ void __launch_bounds__(256) scale_cast_kernel(const float* __restrict
 }
 
 // ------------------------------------------------------------------ value refresh from device
-template <class T>
-__device__ __forceinline__ T from_f64(double x);
-template <>
-__device__ __forceinline__ double from_f64<double>(double x) { return x; }
-template <>
-__device__ __forceinline__ float from_f64<float>(double x) { return __double2float_rn(x); }
-template <>
-__device__ __forceinline__ __half from_f64<__half>(double x) { return __double2half(x); }
-template <>
-__device__ __forceinline__ __nv_bfloat16 from_f64<__nv_bfloat16>(double x) { return __double2bfloat16(x); }
 
 // Stored value = round(scale * sum of the slot's input entries in input order), as the host
 // packer does: CSR positions have one source each, BCSR fragment slots zero or more.

@@ -35,6 +35,18 @@ struct TrBF16 {
   __device__ static __forceinline__ TAcc to_acc(TB x) { return __bfloat162float(x); }
 };
 
+// binary64 -> storage type, round to nearest even (the stored-value rounding of a plan).
+template <class T>
+__device__ __forceinline__ T from_f64(double x);
+template <>
+__device__ __forceinline__ double from_f64<double>(double x) { return x; }
+template <>
+__device__ __forceinline__ float from_f64<float>(double x) { return __double2float_rn(x); }
+template <>
+__device__ __forceinline__ __half from_f64<__half>(double x) { return __double2half(x); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 from_f64<__nv_bfloat16>(double x) { return __double2bfloat16(x); }
+
 // 16-byte vector of B elements, unpacked to accumulator values.
 template <class Tr>
 __device__ __forceinline__ void unpack16(const uint4& v, typename Tr::TAcc (&out)[Tr::kVE]);

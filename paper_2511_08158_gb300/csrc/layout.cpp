@@ -86,26 +86,6 @@ int bucket_of(int64_t len) {
 
 }  // namespace
 
-// Position in the fragment-ordered tile array of (tile t, row r), per dtype.
-int64_t frag_index(loops_dtype d, int64_t t, int32_t r, int32_t br) {
-  if (d == LOOPS_F64) {  // K = 4 tiles per group, 32 lanes x 1 value
-    const int64_t g = t / 4;
-    const int32_t tt = (int32_t)(t % 4);
-    return g * 32 + (int64_t)(r * 4 + tt);
-  }
-  if (d == LOOPS_F16 || d == LOOPS_BF16) {  // K = 16 tiles per group, 32 lanes x 8 values
-    const int64_t g = t / 16;
-    const int32_t k = (int32_t)(t % 16);
-    const int32_t q = r & 7, hi_r = r >> 3;          // row = q + 8 * hi_r
-    const int32_t hi_k = k >> 3, kk = k & 7;         // tile = 2*tq + lo + 8 * hi_k
-    const int32_t tq = kk >> 1, lo = kk & 1;
-    const int32_t lane = q * 4 + tq;
-    const int32_t j = hi_k * 4 + hi_r * 2 + lo;
-    return g * 256 + lane * 8 + j;
-  }
-  return t * br + r;
-}
-
 loops_status upload_part(loops_plan_s* p, int64_t N) {
   const Canon& c = p->canon;
   PartDev& d = p->dev;

@@ -75,6 +75,35 @@ loops_status build_canon(const loops_csr* A, const double* vals, loops_dtype dty
 double round_store(double v, double scale, loops_dtype d);
 
 // ------------------------------------------------------------------ device layout
+#ifdef __CUDACC__
+#define LOOPS_HD __host__ __device__
+#else
+#define LOOPS_HD
+#endif
+
+// Position in the fragment-ordered tile array of (tile t, row r), per dtype:
+//   F64  (m8n8k4, K = 4 tiles, B_r = 8):  group g, lane l = 4*row + t -> A[row][t]
+//   F16/BF16 (m16n8k16, K = 16, B_r = 16): group g, lane l = 4*q + t, j = 0..7 ->
+//        row = q + 8*(j>>1 & 1), tile = 2t + (j & 1) + 8*(j >> 2)
+//   F32  (CUDA-core outer product): tile-major, B_r values of a tile contiguous.
+LOOPS_HD inline int64_t frag_index(loops_dtype d, int64_t t, int32_t r, int32_t br) {
+  if (d == LOOPS_F64) {  // K = 4 tiles per group, 32 lanes x 1 value
+    const int64_t g = t / 4;
+    const int32_t tt = (int32_t)(t % 4);
+    return g * 32 + (int64_t)(r * 4 + tt);
+  }
+  if (d == LOOPS_F16 || d == LOOPS_BF16) {  // K = 16 tiles per group, 32 lanes x 8 values
+    const int64_t g = t / 16;
+    const int32_t k = (int32_t)(t % 16);
+    const int32_t q = r & 7, hi_r = r >> 3;          // row = q + 8 * hi_r
+    const int32_t hi_k = k >> 3, kk = k & 7;         // tile = 2*tq + lo + 8 * hi_k
+    const int32_t tq = kk >> 1, lo = kk & 1;
+    const int32_t lane = q * 4 + tq;
+    const int32_t j = hi_k * 4 + hi_r * 2 + lo;
+    return g * 256 + lane * 8 + j;
+  }
+  return t * br + r;
+}
 // CSR part work items: item i covers entries [item_ptr[i], item_ptr[i+1]) of col/val and
 // writes C row item_row[i] (>= 0) or partial-sum slot -1 - item_row[i] (< 0).
 struct CsrDev {
@@ -211,6 +240,7 @@ struct HostPipe {
               out_done[2] = {nullptr, nullptr};
   bool used[2] = {false, false};
   int next = 0;
+  int last = -1;                       // buffer set of the last call (for the flush)
 };
 void destroy_pipe(HostPipe* h);
 
@@ -246,6 +276,10 @@ struct loops_plan_s {
   bool timing;
   loops::BatchState* batch;            // non-null for a batched plan
   int64_t other_bytes;                 // device bytes outside the part arrays
+  // partition counts (canonical): CSR-part rows and entries, BCSR blocks and tiles
+  int64_t n_csr_rows, nnz_csr, n_rb, n_tiles;
+  bool device_built;                   // built by loops_plan_device (no host canonical copy)
+  bool has_vmap;                       // value maps present (loops_plan_set_values works)
 };
 
 namespace loops {
@@ -290,6 +324,27 @@ loops_status cuda_status(cudaError_t e, const char* what);
 loops_status resolve_block_rows(loops_dtype dtype, const loops_plan_opts& o, int32_t* br);
 loops_status check_plan(loops_plan_t p);
 void destroy_batch(BatchState* b);
+
+// ------------------------------------------------------------------ device-side plan build
+// A CSR matrix whose arrays are in device memory (values binary64, or binary32 when vals_f32).
+struct DevCsrIn {
+  int64_t n_rows, n_cols, nnz;
+  const int64_t* rp;
+  const int32_t* ci;
+  const void* vals;
+  int vals_f32;
+};
+// Checks of validate_csr on the device; max_abs = max |a| over finite values.
+loops_status validate_csr_device(const DevCsrIn& A, loops_dtype dtype, cudaStream_t s, double* max_abs);
+double plan_scale_from_max(double max_abs, loops_dtype d);
+// Fills plan->dev (and plan->vmap when want_maps) from A on the device; plan fields dtype, br,
+// kpad, scale, split_len and tile_min must be set. `remap` (device, optional) maps A's entries
+// to the caller's input order (the transposed plan).
+loops_status build_part_device(loops_plan_s* p, const DevCsrIn& A, const int64_t* remap, int64_t N, double tau,
+                               bool contiguous, int64_t r_boundary, bool want_maps, cudaStream_t s);
+loops_status build_sddmm_device(loops_plan_s* p, const DevCsrIn& A, cudaStream_t s);
+loops_status transpose_device(const DevCsrIn& A, int64_t** t_rp, int32_t** t_ci, double** t_vals, int64_t** perm,
+                              cudaStream_t s);
 
 cudaError_t launch_set_values(const loops_plan_s* p, const void* vals, loops_dtype vd, cudaStream_t s);
 cudaError_t launch_cast_scaled(const float* X, int64_t rows, int64_t cols, int64_t ldx,

@@ -194,9 +194,20 @@ def test_spmm_host_async_pipeline(lp):
     Cs = [torch.full((3000, 16), float("nan"), dtype=torch.float64).pin_memory() for _ in range(5)]
     for B, C in zip(Bs, Cs):
         plan.spmm_host_async(B, C)
-    torch.cuda.synchronize()
+    plan.host_flush()
+    torch.cuda.current_stream().synchronize()
     for B, C in zip(Bs, Cs):
         assert rel_l2(C.numpy(), oracle.spmm(A, B.numpy())) <= TOL["f64"]
+    # a flush with no pipelined call before it is a no-op; one C buffer reused by every call
+    # ends with the last call's result
+    fresh = lp.Plan(A, 16, "f64", tau=2.0)
+    fresh.host_flush()
+    C1 = torch.full((3000, 16), float("nan"), dtype=torch.float64).pin_memory()
+    for B in Bs:
+        fresh.spmm_host_async(B, C1)
+        fresh.host_flush()
+        torch.cuda.current_stream().synchronize()
+        assert rel_l2(C1.numpy(), oracle.spmm(A, B.numpy())) <= TOL["f64"]
 
 
 @pytest.mark.parametrize("fmt", ["f64", "bf16"])

@@ -73,6 +73,18 @@ def test_spmm_empty_rows_and_empty_matrix():
     assert oracle.spmm(E, B).shape == (0, 3)
 
 
+def test_spmm_threads_bit_identical_to_one_thread():
+    # the threaded timing leg runs the same row loop on row ranges; any thread count, empty
+    # rows and an empty matrix give the single-threaded result bit for bit
+    rng = np.random.default_rng(4)
+    A = W.random_csr(700, 300, 0.02, 2, duplicates=True, unsorted=True)
+    B = rng.standard_normal((300, 9))
+    for t in (1, 2, 5, 16, 1000):
+        assert np.array_equal(oracle.spmm_threads(A, B, t), oracle.spmm(A, B))
+    E = W.CSR(0, 300, np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0))
+    assert oracle.spmm_threads(E, B, 4).shape == (0, 9)
+
+
 def test_spmm_rows_equals_full():
     A = W.random_csr(40, 40, 0.15, 9)
     B = W.dense_normal(40, 7, 2)
