@@ -36,6 +36,15 @@ constexpr int kThreads = 256;
 constexpr int kItems = 8;
 constexpr int kTile = kThreads * kItems;  // elements per block in scans and radix passes
 
+// Index checks of the build kernels: an index outside its array is recorded here and the
+// access skipped; the host turns a non-zero word into an error status.
+__device__ int g_build_err;
+#define BUILD_CHECK(cond)                  \
+  if (!(cond)) {                            \
+    atomicOr(&g_build_err, 1);              \
+    continue;                               \
+  }
+
 // ------------------------------------------------------------------ temporaries
 // Device allocations that live for one build; released (after the stream is drained) when the
 // arena goes out of scope.
@@ -213,8 +222,12 @@ __global__ void __launch_bounds__(kThreads) radix_scatter_k(const uint64_t* kin,
     __syncthreads();
     if (valid) {
       const int64_t pos = base_off[d] + wcnt[warp][d] + rank_w;
-      kout[pos] = k;
-      vout[pos] = vin[i];
+      if (pos >= 0 && pos < n) {
+        kout[pos] = k;
+        vout[pos] = vin[i];
+      } else {
+        atomicOr(&g_build_err, 1);
+      }
     }
     __syncthreads();
   }
@@ -319,16 +332,20 @@ __global__ void tile_flags_k(const uint64_t* key, int64_t nnz, int32_t* flag) {
 
 __global__ void tile_first_k(const int32_t* flag, const int64_t* tpos, int64_t nnz, int64_t* tile_first,
                              int64_t n_t) {
-  GS_LOOP(p, nnz)
-    if (flag[p]) tile_first[tpos[p]] = p;
+  GS_LOOP(p, nnz) {
+    if (!flag[p]) continue;
+    BUILD_CHECK(tpos[p] >= 0 && tpos[p] < n_t);
+    tile_first[tpos[p]] = p;
+  }
   if (blockIdx.x == 0 && threadIdx.x == 0) tile_first[n_t] = nnz;
 }
 
 // Per tile: its block's distinct-column and kept-tile counts, and the first tile of a block.
 __global__ void tile_stats_k(const uint64_t* key, const int64_t* tile_first, int64_t n_t, int cb, int32_t tile_min,
-                             int32_t* u, int32_t* keep, int64_t* blk_first) {
+                             int64_t nb, int32_t* u, int32_t* keep, int64_t* blk_first) {
   GS_LOOP(t, n_t) {
     const int64_t b = (int64_t)(key[tile_first[t]] >> cb);
+    BUILD_CHECK(b >= 0 && b < nb);
     atomicAdd(&u[b], 1);
     const int64_t cnt = tile_first[t + 1] - tile_first[t];
     if (tile_min <= 1 || cnt >= tile_min) atomicAdd(&keep[b], 1);
@@ -355,18 +372,20 @@ __global__ void block_decide_k(const int64_t* rp, int64_t n_rows, int64_t nb, in
 
 __global__ void block_out_k(const uint8_t* is_bcsr, const int64_t* rb_pos, const int64_t* rb_tile0, int64_t nb,
                             int64_t n_rb, int64_t n_tiles, int32_t* rb_id, int64_t* rb_ptr) {
-  GS_LOOP(b, nb)
-    if (is_bcsr[b]) {
-      rb_id[rb_pos[b]] = (int32_t)b;
-      rb_ptr[rb_pos[b]] = rb_tile0[b];
-    }
+  GS_LOOP(b, nb) {
+    if (!is_bcsr[b]) continue;
+    BUILD_CHECK(rb_pos[b] >= 0 && rb_pos[b] < n_rb);
+    rb_id[rb_pos[b]] = (int32_t)b;
+    rb_ptr[rb_pos[b]] = rb_tile0[b];
+  }
   if (blockIdx.x == 0 && threadIdx.x == 0) rb_ptr[n_rb] = n_tiles;
 }
 
 __global__ void tile_kept_k(const uint64_t* key, const int64_t* tile_first, int64_t n_t, int cb,
-                            const uint8_t* is_bcsr, int32_t tile_min, int64_t* kept) {
+                            const uint8_t* is_bcsr, int32_t tile_min, int64_t nb, int64_t* kept) {
   GS_LOOP(t, n_t) {
     const int64_t b = (int64_t)(key[tile_first[t]] >> cb);
+    BUILD_CHECK(b >= 0 && b < nb);
     const int64_t cnt = tile_first[t + 1] - tile_first[t];
     kept[t] = (is_bcsr[b] && (tile_min <= 1 || cnt >= tile_min)) ? 1 : 0;
   }
@@ -377,11 +396,12 @@ __global__ void tile_kept_k(const uint64_t* key, const int64_t* tile_first, int6
 // of the kept-tile flags (tile t is kept when kept[t + 1] > kept[t]).
 __global__ void entry_class_k(const uint64_t* key, const int64_t* idx, const int32_t* flag, const int64_t* tpos,
                               const int64_t* kept, const uint8_t* is_bcsr, const int32_t* erow, int64_t nnz, int cb,
-                              uint8_t* cls, int32_t* rowlen1) {
+                              int64_t n_t, int64_t nb, int64_t n_rows, uint8_t* cls, int32_t* rowlen1) {
   GS_LOOP(p, nnz) {
     const int64_t t = tpos[p] + flag[p] - 1;
     const int64_t b = (int64_t)(key[p] >> cb);
     const int64_t k = idx[p];
+    BUILD_CHECK(t >= 0 && t < n_t && b >= 0 && b < nb && k >= 0 && k < nnz && erow[k] >= 0 && erow[k] < n_rows);
     uint8_t c = 0;
     if (is_bcsr[b]) {
       c = kept[t + 1] > kept[t] ? 2 : 1;
@@ -415,6 +435,8 @@ struct TileArgs {
   int64_t* slot_src;
   const int64_t* remap;
   unsigned long long* n_sub;
+  int64_t n_tiles;           // tiles of the BCSR part (incl. padding)
+  int64_t n_src;             // entries of the slot map (second pass)
 };
 
 __device__ __forceinline__ bool tile_is_kept(const TileArgs& a, int64_t t) { return a.kept[t + 1] > a.kept[t]; }
@@ -433,6 +455,7 @@ __global__ void tile_values_k(TileArgs a) {
     const uint64_t key = a.key[p0];
     const int64_t b = (int64_t)(key >> a.cb);
     const int64_t out = tile_out_index(a, t, b);
+    BUILD_CHECK(out >= 0 && out < a.n_tiles);
     a.tile_col[out] = (int32_t)(key & ((1ull << a.cb) - 1));
     double acc[16];
     int cnt[16];
@@ -441,6 +464,7 @@ __global__ void tile_values_k(TileArgs a) {
     for (int64_t p = p0; p < p1; ++p) {
       const int64_t k = a.idx[p];
       const int r = (int)(a.erow[k] - b * a.br);
+      if (r < 0 || r >= a.br) { atomicOr(&g_build_err, 1); continue; }
       const double v = load_val(a.vals, a.vf32, k);
 #pragma unroll
       for (int q = 0; q < 16; ++q)
@@ -468,6 +492,7 @@ __global__ void tile_srcmap_k(TileArgs a) {
     const int64_t p0 = a.tile_first[t], p1 = a.tile_first[t + 1];
     const int64_t b = (int64_t)(a.key[p0] >> a.cb);
     const int64_t out = tile_out_index(a, t, b);
+    BUILD_CHECK(out >= 0 && out < a.n_tiles);
     int fill[16];
 #pragma unroll
     for (int r = 0; r < 16; ++r) fill[r] = 0;
@@ -478,17 +503,22 @@ __global__ void tile_srcmap_k(TileArgs a) {
 #pragma unroll
       for (int q = 0; q < 16; ++q)
         if (q == r) off = fill[q]++;
+      if (r < 0 || r >= a.br) { atomicOr(&g_build_err, 1); continue; }
       const int64_t f = frag_index(a.dtype, out, r, a.br);
-      a.slot_src[a.slot_ptr[f] + off] = a.remap ? a.remap[k] : k;
+      const int64_t at = a.slot_ptr[f] + off;
+      if (at < 0 || at >= a.n_src) { atomicOr(&g_build_err, 1); continue; }
+      a.slot_src[at] = a.remap ? a.remap[k] : k;
     }
   }
 }
 
 __global__ void pad_tiles_k(const uint8_t* is_bcsr, const int32_t* keep, const int64_t* tpad, const int64_t* rb_tile0,
-                            int64_t nb, int32_t* tile_col) {
-  GS_LOOP(b, nb)
-    if (is_bcsr[b])
-      for (int64_t q = keep[b]; q < tpad[b]; ++q) tile_col[rb_tile0[b] + q] = -1;
+                            int64_t nb, int64_t n_tiles, int32_t* tile_col) {
+  GS_LOOP(b, nb) {
+    if (!is_bcsr[b]) continue;
+    BUILD_CHECK(rb_tile0[b] >= 0 && rb_tile0[b] + tpad[b] <= n_tiles);
+    for (int64_t q = keep[b]; q < tpad[b]; ++q) tile_col[rb_tile0[b] + q] = -1;
+  }
 }
 
 // Work units of the BCSR blocks: blocks above kBcsrSplitTiles tiles become several units
@@ -504,15 +534,18 @@ __global__ void unit_count_k(const int64_t* rb_ptr, int64_t n_rb, int64_t* n_uni
   }
 }
 
+// split_block / split_slot_ptr exist only when some block is cut (n_split > 0).
 __global__ void unit_emit_k(const int64_t* rb_ptr, int64_t n_rb, const int64_t* ubase, const int64_t* sbase,
-                            const int64_t* spidx, int64_t n_bslots, uint64_t* ukey, int64_t* uval, int32_t* pre_b,
-                            int64_t* pre_t0, int64_t* pre_t1, int32_t* pre_slot, int32_t* split_block,
+                            const int64_t* spidx, int64_t n_bslots, int64_t n_units, uint64_t* ukey, int64_t* uval,
+                            int32_t* pre_b, int64_t* pre_t0, int64_t* pre_t1, int32_t* pre_slot, int32_t* split_block,
                             int32_t* split_slot_ptr, int64_t n_split) {
   GS_LOOP(c, n_rb) {
     const int64_t t0 = rb_ptr[c], t1 = rb_ptr[c + 1];
     const bool sp = t1 - t0 > kBcsrSplitTiles;
     int64_t u = ubase[c], slot = sbase[c];
+    BUILD_CHECK(u >= 0 && u + (t1 - t0 + kBcsrSplitTiles - 1) / kBcsrSplitTiles <= n_units);
     if (sp) {
+      BUILD_CHECK(split_block && spidx[c] >= 0 && spidx[c] < n_split);
       split_block[spidx[c]] = (int32_t)c;
       split_slot_ptr[spidx[c]] = (int32_t)slot;
     }
@@ -527,7 +560,7 @@ __global__ void unit_emit_k(const int64_t* rb_ptr, int64_t n_rb, const int64_t* 
       ++u;
     }
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) split_slot_ptr[n_split] = (int32_t)n_bslots;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && split_slot_ptr) split_slot_ptr[n_split] = (int32_t)n_bslots;
 }
 
 __global__ void unit_gather_k(const int64_t* order, int64_t n, const int32_t* pre_b, const int64_t* pre_t0,
@@ -535,6 +568,7 @@ __global__ void unit_gather_k(const int64_t* order, int64_t n, const int32_t* pr
                               int32_t* us) {
   GS_LOOP(q, n) {
     const int64_t u = order[q];
+    BUILD_CHECK(u >= 0 && u < n);
     ub[q] = pre_b[u];
     u0[q] = pre_t0[u];
     u1[q] = pre_t1[u];
@@ -551,9 +585,13 @@ __global__ void class_flags_k(const uint8_t* cls, int64_t nnz, int32_t* f0, int3
 }
 
 // canonical position -> input entry, for one CSR set
-__global__ void canon_src_k(const uint8_t* cls, const int64_t* cpos, int64_t nnz, uint8_t which, int64_t* src) {
-  GS_LOOP(k, nnz)
-    if (cls[k] == which) src[cpos[k]] = k;
+__global__ void canon_src_k(const uint8_t* cls, const int64_t* cpos, int64_t nnz, uint8_t which, int64_t n_src,
+                            int64_t* src) {
+  GS_LOOP(k, nnz) {
+    if (cls[k] != which) continue;
+    BUILD_CHECK(cpos[k] >= 0 && cpos[k] < n_src);
+    src[cpos[k]] = k;
+  }
 }
 
 __device__ __forceinline__ int bucket_of_len(int64_t len) {  // floor(log2(len + 1)), at most 62
@@ -581,8 +619,8 @@ __global__ void row_count_k(const int64_t* rp, const uint8_t* is_bcsr, const int
 __global__ void row_emit_k(const int64_t* rp, const uint8_t* is_bcsr, const int32_t* rowlen1, const int64_t* cpos,
                            int64_t n_rows, int32_t br, int which, int64_t L, const int64_t* ibase,
                            const int64_t* sbase, const int64_t* spidx, int64_t n_slots, int64_t n_split,
-                           uint64_t* ikey, int64_t* ival, int32_t* pre_row, int64_t* pre_beg, int64_t* pre_len,
-                           int32_t* split_row, int32_t* split_slot_ptr) {
+                           int64_t n_items, uint64_t* ikey, int64_t* ival, int32_t* pre_row, int64_t* pre_beg,
+                           int64_t* pre_len, int32_t* split_row, int32_t* split_slot_ptr) {
   GS_LOOP(i, n_rows) {
     const bool in_b = is_bcsr[i / br] != 0;
     int64_t len = -1;
@@ -591,8 +629,10 @@ __global__ void row_emit_k(const int64_t* rp, const uint8_t* is_bcsr, const int3
     if (len < 0) continue;
     const int64_t beg = cpos[rp[i]];  // canonical position of the row's first entry in this set
     int64_t it = ibase[i];
+    BUILD_CHECK(it >= 0 && it + (len > L ? (len + L - 1) / L : 1) <= n_items);
     if (len > L) {
       int64_t slot = sbase[i];
+      BUILD_CHECK(split_row && spidx[i] >= 0 && spidx[i] < n_split);
       split_row[spidx[i]] = (int32_t)i;
       split_slot_ptr[spidx[i]] = (int32_t)slot;
       for (int64_t s0 = 0; s0 < len; s0 += L, ++it, ++slot) {
@@ -617,6 +657,7 @@ __global__ void item_order_k(const int64_t* order, int64_t n, const int32_t* pre
                              int32_t* item_row, int64_t* dlen) {
   GS_LOOP(q, n) {
     const int64_t u = order[q];
+    BUILD_CHECK(u >= 0 && u < n);
     item_row[q] = pre_row[u];
     dlen[q] = pre_len[u];
   }
@@ -625,14 +666,15 @@ __global__ void item_order_k(const int64_t* order, int64_t n, const int32_t* pre
 // One warp per item: columns and rounded values of its entries, and the value map.
 template <class TB>
 __global__ void item_gather_k(const int64_t* order, int64_t n, const int64_t* pre_beg, const int64_t* item_ptr,
-                              const int64_t* canon_src, const int32_t* ci, const void* vals, int vf32, double scale,
-                              double tiny, const int64_t* remap, int32_t* col, TB* val, int64_t* csr_src,
-                              unsigned long long* n_sub) {
+                              const int64_t* canon_src, int64_t n_canon, int64_t total, const int32_t* ci,
+                              const void* vals, int vf32, double scale, double tiny, const int64_t* remap,
+                              int32_t* col, TB* val, int64_t* csr_src, unsigned long long* n_sub) {
   const int lane = threadIdx.x & 31;
   for (int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < n;
        q += ((int64_t)gridDim.x * blockDim.x) >> 5) {
     const int64_t b = pre_beg[order[q]];
     const int64_t d0 = item_ptr[q], len = item_ptr[q + 1] - d0;
+    BUILD_CHECK(b >= 0 && b + len <= n_canon && d0 >= 0 && d0 + len <= total);
     unsigned long long sub = 0;
     for (int64_t e = lane; e < len; e += 32) {
       const int64_t k = canon_src[b + e];
@@ -657,10 +699,11 @@ __global__ void sddmm_count_k(const int64_t* rp, int64_t n_rows, int64_t L, int6
   }
 }
 
-__global__ void sddmm_emit_k(const int64_t* rp, int64_t n_rows, int64_t L, const int64_t* ibase, uint64_t* key,
-                             int64_t* val, int32_t* pre_row, int64_t* pre_beg, int64_t* pre_end) {
+__global__ void sddmm_emit_k(const int64_t* rp, int64_t n_rows, int64_t L, const int64_t* ibase, int64_t n_items,
+                             uint64_t* key, int64_t* val, int32_t* pre_row, int64_t* pre_beg, int64_t* pre_end) {
   GS_LOOP(i, n_rows) {
     int64_t it = ibase[i];
+    BUILD_CHECK(it >= 0 && it + (rp[i + 1] - rp[i] + L - 1) / L <= n_items);
     for (int64_t b = rp[i]; b < rp[i + 1]; b += L, ++it) {
       const int64_t e = min(b + L, rp[i + 1]);
       pre_row[it] = (int32_t)i;
@@ -676,6 +719,7 @@ __global__ void sddmm_gather_k(const int64_t* order, int64_t n, const int32_t* p
                                const int64_t* pre_end, int32_t* row, int64_t* beg, int64_t* end) {
   GS_LOOP(q, n) {
     const int64_t u = order[q];
+    BUILD_CHECK(u >= 0 && u < n);
     row[q] = pre_row[u];
     beg[q] = pre_beg[u];
     end[q] = pre_end[u];
@@ -725,12 +769,13 @@ cudaError_t launch_tile_values(const TileArgs& a, cudaStream_t s) {
 
 template <class TB>
 cudaError_t launch_item_gather(const int64_t* order, int64_t n, const int64_t* pre_beg, const int64_t* item_ptr,
-                               const int64_t* canon_src, const DevCsrIn& A, double scale, double tiny,
-                               const int64_t* remap, int32_t* col, void* val, int64_t* csr_src,
-                               unsigned long long* n_sub, cudaStream_t s) {
+                               const int64_t* canon_src, int64_t n_canon, int64_t total, const DevCsrIn& A,
+                               double scale, double tiny, const int64_t* remap, int32_t* col, void* val,
+                               int64_t* csr_src, unsigned long long* n_sub, cudaStream_t s) {
   const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n * 32 + kThreads - 1) / kThreads, 152 * 16));
-  item_gather_k<TB><<<blocks, kThreads, 0, s>>>(order, n, pre_beg, item_ptr, canon_src, A.ci, A.vals,
-                                                 A.vals_f32, scale, tiny, remap, col, (TB*)val, csr_src, n_sub);
+  item_gather_k<TB><<<blocks, kThreads, 0, s>>>(order, n, pre_beg, item_ptr, canon_src, n_canon, total, A.ci,
+                                                 A.vals, A.vals_f32, scale, tiny, remap, col, (TB*)val, csr_src,
+                                                 n_sub);
   return cudaGetLastError();
 }
 
@@ -745,20 +790,38 @@ cudaError_t dispatch_tile_values(loops_dtype d, const TileArgs& a, cudaStream_t 
 }
 
 cudaError_t dispatch_item_gather(loops_dtype d, const int64_t* order, int64_t n, const int64_t* pre_beg,
-                                 const int64_t* item_ptr, const int64_t* canon_src, const DevCsrIn& A, double scale,
-                                 double tiny, const int64_t* remap, int32_t* col, void* val, int64_t* csr_src,
-                                 unsigned long long* n_sub, cudaStream_t s) {
+                                 const int64_t* item_ptr, const int64_t* canon_src, int64_t n_canon, int64_t total,
+                                 const DevCsrIn& A, double scale, double tiny, const int64_t* remap, int32_t* col,
+                                 void* val, int64_t* csr_src, unsigned long long* n_sub, cudaStream_t s) {
+#define LOOPS_GATHER(TB) \
+  launch_item_gather<TB>(order, n, pre_beg, item_ptr, canon_src, n_canon, total, A, scale, tiny, remap, col, val, \
+                         csr_src, n_sub, s)
   switch (d) {
-    case LOOPS_F64:
-      return launch_item_gather<double>(order, n, pre_beg, item_ptr, canon_src, A, scale, tiny, remap, col, val, csr_src, n_sub, s);
-    case LOOPS_F32:
-      return launch_item_gather<float>(order, n, pre_beg, item_ptr, canon_src, A, scale, tiny, remap, col, val, csr_src, n_sub, s);
-    case LOOPS_F16:
-      return launch_item_gather<__half>(order, n, pre_beg, item_ptr, canon_src, A, scale, tiny, remap, col, val, csr_src, n_sub, s);
-    case LOOPS_BF16:
-      return launch_item_gather<__nv_bfloat16>(order, n, pre_beg, item_ptr, canon_src, A, scale, tiny, remap, col, val, csr_src, n_sub, s);
+    case LOOPS_F64: return LOOPS_GATHER(double);
+    case LOOPS_F32: return LOOPS_GATHER(float);
+    case LOOPS_F16: return LOOPS_GATHER(__half);
+    case LOOPS_BF16: return LOOPS_GATHER(__nv_bfloat16);
   }
+#undef LOOPS_GATHER
   return cudaErrorInvalidValue;
+}
+
+cudaError_t reset_build_err(cudaStream_t s) {
+  const int zero = 0;
+  return cudaMemcpyToSymbolAsync(g_build_err, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s);
+}
+
+// After a build stage: a recorded index check fails the build (no access was made).
+loops_status check_build_err(cudaStream_t s, const char* what) {
+  int h = 0;
+  cudaError_t e = cudaMemcpyFromSymbolAsync(&h, g_build_err, sizeof(int), 0, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_status(e, what);
+  if (h) {
+    set_error(std::string(what) + ": an index check failed (access skipped); the plan was not built");
+    return LOOPS_ERR_STATE;
+  }
+  return LOOPS_OK;
 }
 
 #define TRY(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) return cuda_status(e_, what); } while (0)
@@ -767,7 +830,7 @@ cudaError_t dispatch_item_gather(loops_dtype d, const int64_t* order, int64_t n,
 // One CSR set (0: rows of CSR blocks, 1: moved entries of BCSR blocks) into its work items.
 loops_status build_csr_set(loops_plan_s* p, const DevCsrIn& A, const int64_t* remap, int which, const uint8_t* cls,
                            const uint8_t* is_bcsr, const int32_t* rowlen1, const int64_t* cpos, const int64_t* csrc,
-                           int64_t N, double tiny, unsigned long long* n_sub, int64_t** csr_src_out, int64_t* n_src,
+                           int64_t n_canon, int64_t N, double tiny, unsigned long long* n_sub, int64_t** csr_src_out, int64_t* n_src,
                            Arena& ar, cudaStream_t s) {
   const char* what = "device plan build (CSR part)";
   CsrDev& cd = which == 0 ? p->dev.csr : p->dev.csr_acc;
@@ -805,7 +868,7 @@ loops_status build_csr_set(loops_plan_s* p, const DevCsrIn& A, const int64_t* re
     TRY(own(&cd.split_slot_ptr, n_sp + 1, bytes));
   }
   row_emit_k<<<grid_for(n), kThreads, 0, s>>>(A.rp, is_bcsr, rowlen1, cpos, n, p->br, which, L, n_items_r, n_slots_r,
-                                              split_r, n_sl, n_sp, ikey, ival, pre_row, pre_beg, pre_len,
+                                              split_r, n_sl, n_sp, n_it, ikey, ival, pre_row, pre_beg, pre_len,
                                               cd.split_row, cd.split_slot_ptr);
   TRY(cudaGetLastError());
   TRY(radix_sort<int64_t>(&ikey, &ival, &ikey2, &ival2, n_it, 6, ar, s));
@@ -826,8 +889,8 @@ loops_status build_csr_set(loops_plan_s* p, const DevCsrIn& A, const int64_t* re
     NEED(csr_src);
   }
   if (total)
-    TRY(dispatch_item_gather(p->dtype, ival, n_it, pre_beg, cd.item_ptr, csrc, A, p->scale, tiny, remap, cd.col,
-                             cd.val, csr_src, n_sub, s));
+    TRY(dispatch_item_gather(p->dtype, ival, n_it, pre_beg, cd.item_ptr, csrc, n_canon, total, A, p->scale, tiny,
+                             remap, cd.col, cd.val, csr_src, n_sub, s));
   if (n_sl) {
     const int acc_bytes = p->dtype == LOOPS_F64 ? 8 : 4;
     TRY(own((uint8_t**)&cd.scratch, n_sl * std::max<int64_t>(N, 1) * acc_bytes, bytes));
@@ -916,6 +979,7 @@ loops_status build_part_device(loops_plan_s* p, const DevCsrIn& A, const int64_t
   unsigned long long* n_sub = ar.get<unsigned long long>(1);
   NEED(n_sub);
   TRY(cudaMemsetAsync(n_sub, 0, sizeof(unsigned long long), s));
+  TRY(reset_build_err(s));
 
   // ---- 2. entries sorted by (row block, column), ties in input order; tiles are the runs
   int32_t* erow = ar.get<int32_t>(nnz);
@@ -953,7 +1017,7 @@ loops_status build_part_device(loops_plan_s* p, const DevCsrIn& A, const int64_t
     tile_first = ar.get<int64_t>(n_t + 1);
     NEED(tile_first);
     tile_first_k<<<grid_for(nnz), kThreads, 0, s>>>(flag, tpos, nnz, tile_first, n_t);
-    tile_stats_k<<<grid_for(n_t), kThreads, 0, s>>>(key, tile_first, n_t, cb, tile_min, u, keep, blk_first);
+    tile_stats_k<<<grid_for(n_t), kThreads, 0, s>>>(key, tile_first, n_t, cb, tile_min, nb, u, keep, blk_first);
     TRY(cudaGetLastError());
   }
 
@@ -977,11 +1041,11 @@ loops_status build_part_device(loops_plan_s* p, const DevCsrIn& A, const int64_t
   if (nnz) {
     kept = ar.get<int64_t>(n_t + 1);
     NEED(kept);
-    tile_kept_k<<<grid_for(n_t), kThreads, 0, s>>>(key, tile_first, n_t, cb, is_bcsr, tile_min, kept);
+    tile_kept_k<<<grid_for(n_t), kThreads, 0, s>>>(key, tile_first, n_t, cb, is_bcsr, tile_min, nb, kept);
     TRY(cudaGetLastError());
     TRY(excl_scan<int64_t>(kept, kept, n_t, true, ar, s));
-    entry_class_k<<<grid_for(nnz), kThreads, 0, s>>>(key, idx, flag, tpos, kept, is_bcsr, erow, nnz, cb, cls,
-                                                     rowlen1);
+    entry_class_k<<<grid_for(nnz), kThreads, 0, s>>>(key, idx, flag, tpos, kept, is_bcsr, erow, nnz, cb, n_t, nb,
+                                                     n, cls, rowlen1);
     TRY(cudaGetLastError());
   }
 
@@ -998,7 +1062,7 @@ loops_status build_part_device(loops_plan_s* p, const DevCsrIn& A, const int64_t
     TRY(cudaMemsetAsync(d.bcsr.tile_val, 0, (size_t)(n_fslots * es), s));
     block_out_k<<<grid_for(nb), kThreads, 0, s>>>(is_bcsr, rb_pos, rb_tile0, nb, n_rb, n_tiles, d.bcsr.rb_id,
                                                   d.bcsr.rb_ptr);
-    pad_tiles_k<<<grid_for(nb), kThreads, 0, s>>>(is_bcsr, keep, tpad, rb_tile0, nb, d.bcsr.tile_col);
+    pad_tiles_k<<<grid_for(nb), kThreads, 0, s>>>(is_bcsr, keep, tpad, rb_tile0, nb, n_tiles, d.bcsr.tile_col);
     TRY(cudaGetLastError());
     TileArgs ta;
     ta.key = key;
@@ -1023,6 +1087,8 @@ loops_status build_part_device(loops_plan_s* p, const DevCsrIn& A, const int64_t
     ta.slot_src = nullptr;
     ta.remap = remap;
     ta.n_sub = n_sub;
+    ta.n_tiles = n_tiles;
+    ta.n_src = 0;
     int64_t* slot_cnt = nullptr;
     if (want_maps) {
       slot_cnt = ar.get<int64_t>(n_fslots);
@@ -1040,6 +1106,7 @@ loops_status build_part_device(loops_plan_s* p, const DevCsrIn& A, const int64_t
       NEED(slot_src);
       ta.slot_ptr = slot_ptr;
       ta.slot_src = slot_src;
+      ta.n_src = n_src;
       tile_srcmap_k<<<grid_for(n_t), kThreads, 0, s>>>(ta);
       TRY(cudaGetLastError());
     }
@@ -1070,8 +1137,8 @@ loops_status build_part_device(loops_plan_s* p, const DevCsrIn& A, const int64_t
       TRY(own(&d.bcsr.split_block, n_bsplit, bytes));
       TRY(own(&d.bcsr.split_slot_ptr, n_bsplit + 1, bytes));
     }
-    unit_emit_k<<<grid_for(n_rb), kThreads, 0, s>>>(d.bcsr.rb_ptr, n_rb, nu, ns, sp, n_bslots, uk, uv, pb, p0, p1,
-                                                    ps, d.bcsr.split_block, d.bcsr.split_slot_ptr, n_bsplit);
+    unit_emit_k<<<grid_for(n_rb), kThreads, 0, s>>>(d.bcsr.rb_ptr, n_rb, nu, ns, sp, n_bslots, n_units, uk, uv, pb,
+                                                    p0, p1, ps, d.bcsr.split_block, d.bcsr.split_slot_ptr, n_bsplit);
     TRY(cudaGetLastError());
     TRY(radix_sort<int64_t>(&uk, &uv, &uk2, &uv2, n_units, bit_width((uint64_t)kBcsrSplitTiles - 1), ar, s));
     TRY(own(&d.bcsr.unit_block, n_units, bytes));
@@ -1109,17 +1176,18 @@ loops_status build_part_device(loops_plan_s* p, const DevCsrIn& A, const int64_t
   int64_t* src1 = ar.get<int64_t>(nnz1);
   NEED(src1);
   if (nnz) {
-    canon_src_k<<<grid_for(nnz), kThreads, 0, s>>>(cls, c0, nnz, 0, src0);
-    canon_src_k<<<grid_for(nnz), kThreads, 0, s>>>(cls, c1, nnz, 1, src1);
+    canon_src_k<<<grid_for(nnz), kThreads, 0, s>>>(cls, c0, nnz, 0, nnz0, src0);
+    canon_src_k<<<grid_for(nnz), kThreads, 0, s>>>(cls, c1, nnz, 1, nnz1, src1);
     TRY(cudaGetLastError());
   }
   int64_t* csr_src = nullptr;
   int64_t n_csr_src = 0;
   loops_status st;
-  if ((st = build_csr_set(p, A, remap, 0, cls, is_bcsr, rowlen1, c0, src0, N, tiny, n_sub,
+  if ((st = build_csr_set(p, A, remap, 0, cls, is_bcsr, rowlen1, c0, src0, nnz0, N, tiny, n_sub,
                           want_maps ? &csr_src : nullptr, &n_csr_src, ar, s)))
     return st;
-  if ((st = build_csr_set(p, A, remap, 1, cls, is_bcsr, rowlen1, c1, src1, N, tiny, n_sub, nullptr, nullptr, ar, s)))
+  if ((st = build_csr_set(p, A, remap, 1, cls, is_bcsr, rowlen1, c1, src1, nnz1, N, tiny, n_sub, nullptr, nullptr,
+                          ar, s)))
     return st;
   // canonical CSR rows: every row of a CSR block, plus the rows with moved entries. Row blocks
   // hold B_r rows except possibly the last one.
@@ -1159,7 +1227,7 @@ loops_status build_part_device(loops_plan_s* p, const DevCsrIn& A, const int64_t
   unsigned long long sub = 0;
   TRY(to_host(&sub, n_sub, s));
   p->n_subnormal = (int64_t)sub;
-  return LOOPS_OK;
+  return check_build_err(s, what);
 }
 
 // SDDMM items of A's own pattern (rows cut at L entries, stably ordered by decreasing length)
@@ -1171,6 +1239,7 @@ loops_status build_sddmm_device(loops_plan_s* p, const DevCsrIn& A, cudaStream_t
   const int64_t n = A.n_rows, L = std::max<int64_t>(p->split_len, 1);
   int64_t* ni = ar.get<int64_t>(n + 1);
   NEED(ni);
+  TRY(reset_build_err(s));
   if (n) sddmm_count_k<<<grid_for(n), kThreads, 0, s>>>(A.rp, n, L, ni);
   TRY(cudaGetLastError());
   TRY(excl_scan<int64_t>(ni, ni, n, true, ar, s));
@@ -1191,7 +1260,7 @@ loops_status build_sddmm_device(loops_plan_s* p, const DevCsrIn& A, cudaStream_t
   int64_t* pb = ar.get<int64_t>(n_it);
   int64_t* pe = ar.get<int64_t>(n_it);
   NEED(pe);
-  sddmm_emit_k<<<grid_for(n), kThreads, 0, s>>>(A.rp, n, L, ni, k1, v1, pr, pb, pe);
+  sddmm_emit_k<<<grid_for(n), kThreads, 0, s>>>(A.rp, n, L, ni, n_it, k1, v1, pr, pb, pe);
   TRY(cudaGetLastError());
   TRY(radix_sort<int64_t>(&k1, &v1, &k2, &v2, n_it, bit_width((uint64_t)L), ar, s));
   TRY(cudaMalloc((void**)&p->sddmm.item_row, (size_t)n_it * 4));
@@ -1201,7 +1270,7 @@ loops_status build_sddmm_device(loops_plan_s* p, const DevCsrIn& A, cudaStream_t
   sddmm_gather_k<<<grid_for(n_it), kThreads, 0, s>>>(v1, n_it, pr, pb, pe, p->sddmm.item_row, p->sddmm.item_beg,
                                                      p->sddmm.item_end);
   TRY(cudaGetLastError());
-  return LOOPS_OK;
+  return check_build_err(s, what);
 }
 
 // A^T in CSR on the device: entries stably sorted by column (so each column keeps A's row
@@ -1228,6 +1297,7 @@ loops_status transpose_device(const DevCsrIn& A, int64_t** t_rp, int32_t** t_ci,
   int64_t* v2 = ar.get<int64_t>(nnz);
   NEED(v2);
   TRY(cudaMemsetAsync(cnt, 0, (size_t)(m + 1) * 8, s));
+  TRY(reset_build_err(s));
   if (nnz) {
     entry_rows_k<<<grid_for(nnz), kThreads, 0, s>>>(A.rp, A.n_rows, nnz, erow);
     col_keys_k<<<grid_for(nnz), kThreads, 0, s>>>(A.ci, nnz, k1, v1, cnt);
@@ -1241,7 +1311,7 @@ loops_status transpose_device(const DevCsrIn& A, int64_t** t_rp, int32_t** t_ci,
     transpose_fill_k<<<grid_for(nnz), kThreads, 0, s>>>(v1, erow, A.vals, A.vals_f32, nnz, *t_ci, *t_vals);
     TRY(cudaGetLastError());
   }
-  return LOOPS_OK;
+  return check_build_err(s, what);
 }
 
 #undef TRY
