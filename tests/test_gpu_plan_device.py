@@ -202,8 +202,9 @@ def test_device_build_backward_and_values(lp, fmt):
     assert rel_l2(outs[1][0], oracle.spmm_t(A_r, dC_eff)) <= TOL[fmt]
     assert rel_l2(outs[1][1], oracle.sddmm(A, dC_eff, B_eff)) <= TOL[fmt]
     # value refresh from the device (set_values) and from the host (update_values) agree with
-    # a plan built from the new values
-    v2 = rng.standard_normal(A.nnz)
+    # a plan built from the new values (a permutation keeps max|a|, so the kept plan scale
+    # s_A is also the new plan's)
+    v2 = rng.permutation(A.vals)
     A2 = W.CSR(A.n_rows, A.n_cols, A.row_ptr, A.col_idx, v2)
     fresh = lp.Plan(A2, N, fmt, tau=1.5, want_backward=True)
     pd.set_values(torch.as_tensor(v2).cuda())
