@@ -27,6 +27,14 @@
 #ifndef LOOPS_CSR_LANE_VECTORS
 #define LOOPS_CSR_LANE_VECTORS 2
 #endif
+// FP64 (bound by the FP64 pipe): entries in flight per lane and resident blocks per SM with
+// one vector per lane.
+#ifndef LOOPS_CSR_F64_UNROLL
+#define LOOPS_CSR_F64_UNROLL 1
+#endif
+#ifndef LOOPS_CSR_F64_MIN_BLOCKS
+#define LOOPS_CSR_F64_MIN_BLOCKS 8
+#endif
 
 namespace loops {
 
@@ -71,7 +79,7 @@ __device__ __forceinline__ float out_scale<TrBF16>(const CsrKArgs& a, int64_t n)
 // of local memory. The other formats use the tuning knob.
 template <class Tr, int VPL>
 constexpr int csr_min_blocks() {
-  return std::is_same<Tr, TrF64>::value ? (VPL == 1 ? 8 : 4) : LOOPS_CSR_MIN_BLOCKS;
+  return std::is_same<Tr, TrF64>::value ? (VPL == 1 ? LOOPS_CSR_F64_MIN_BLOCKS : 4) : LOOPS_CSR_MIN_BLOCKS;
 }
 
 template <class Tr, int G, int VPL, int U>
@@ -283,7 +291,8 @@ cudaError_t launch_vec_g(const CsrKArgs& a, cudaStream_t s) {
   // slot (a predicated-off DFMA still occupies the pipe) and registers stay low for occupancy.
   // The other formats are bound by memory: U x VPL loads in flight per lane (narrow groups with
   // one vector per lane take four entries at a time, the register budget allows it).
-  constexpr int U = std::is_same<Tr, TrF64>::value ? 1 : ((G >= 8 || VPL > 1) ? LOOPS_CSR_UNROLL : 4);
+  constexpr int U = std::is_same<Tr, TrF64>::value ? LOOPS_CSR_F64_UNROLL
+                                                   : ((G >= 8 || VPL > 1) ? LOOPS_CSR_UNROLL : 4);
   csr_spmm_vec<Tr, G, VPL, U><<<grid, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
