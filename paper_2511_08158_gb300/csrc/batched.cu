@@ -47,27 +47,22 @@ __device__ __forceinline__ float col_mult(const BatchDesc& d, int64_t n) {
   return d.col_scale ? d.col_scale[n] * d.inv_scale : d.inv_scale;
 }
 
-// One CSR item (row or segment partial) for a group of G lanes (runtime G); each lane owns V
-// 16-byte column vectors (lane sub holds vectors sub, sub + G, ...) and keeps U entries' B
-// loads in flight (G * V * VE = N).
-template <class Tr, int V, int U>
+// One CSR item for a group of G lanes (runtime G): row or segment partial.
+template <class Tr>
 __device__ __forceinline__ void csr_item(const BatchDesc& d, int64_t item, int G, int sub, unsigned gmask) {
   using TB = typename Tr::TB;
   using TAcc = typename Tr::TAcc;
   using TC = typename Tr::TC;
   constexpr int VE = Tr::kVE;
+  constexpr int U = 4;
   const int64_t beg = d.item_ptr[item], end = d.item_ptr[item + 1];
   const int32_t row = d.item_row[item];
-  int64_t coff[V];
-#pragma unroll
-  for (int p = 0; p < V; ++p) coff[p] = (int64_t)(p * G + sub) * VE;
+  const int64_t coff = (int64_t)sub * VE;
   const TB* Bp = reinterpret_cast<const TB*>(d.B);
   const TB* vals = reinterpret_cast<const TB*>(d.val);
-  TAcc acc[V][VE];
+  TAcc acc[VE];
 #pragma unroll
-  for (int p = 0; p < V; ++p)
-#pragma unroll
-    for (int e = 0; e < VE; ++e) acc[p][e] = TAcc(0);
+  for (int e = 0; e < VE; ++e) acc[e] = TAcc(0);
   for (int64_t k0 = beg; k0 < end; k0 += G) {
     const int64_t k = k0 + sub;
     int32_t c = 0;
@@ -79,56 +74,43 @@ __device__ __forceinline__ void csr_item(const BatchDesc& d, int64_t item, int G
     const int cnt = (int)(end - k0 < (int64_t)G ? end - k0 : (int64_t)G);
     int j0 = 0;
     for (; j0 + U <= cnt; j0 += U) {
-      uint4 bv[U][V];
+      uint4 bv[U];
       TAcc av[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int cj = __shfl_sync(gmask, c, j0 + u, G);
         av[u] = __shfl_sync(gmask, v, j0 + u, G);
-        const TB* brow = Bp + (int64_t)cj * d.ldb;
-#pragma unroll
-        for (int p = 0; p < V; ++p) bv[u][p] = ldg16(brow + coff[p]);
+        bv[u] = ldg16(Bp + (int64_t)cj * d.ldb + coff);
       }
 #pragma unroll
-      for (int u = 0; u < U; ++u)
+      for (int u = 0; u < U; ++u) {
+        TAcc b[VE];
+        unpack16<Tr>(bv[u], b);
 #pragma unroll
-        for (int p = 0; p < V; ++p) {
-          TAcc b[VE];
-          unpack16<Tr>(bv[u][p], b);
-#pragma unroll
-          for (int e = 0; e < VE; ++e) acc[p][e] = fma(av[u], b[e], acc[p][e]);
-        }
+        for (int e = 0; e < VE; ++e) acc[e] = fma(av[u], b[e], acc[e]);
+      }
     }
     for (; j0 < cnt; ++j0) {
       const int cj = __shfl_sync(gmask, c, j0, G);
       const TAcc aj = __shfl_sync(gmask, v, j0, G);
-      const TB* brow = Bp + (int64_t)cj * d.ldb;
+      TAcc b[VE];
+      unpack16<Tr>(ldg16(Bp + (int64_t)cj * d.ldb + coff), b);
 #pragma unroll
-      for (int p = 0; p < V; ++p) {
-        TAcc b[VE];
-        unpack16<Tr>(ldg16(brow + coff[p]), b);
-#pragma unroll
-        for (int e = 0; e < VE; ++e) acc[p][e] = fma(aj, b[e], acc[p][e]);
-      }
+      for (int e = 0; e < VE; ++e) acc[e] = fma(aj, b[e], acc[e]);
     }
   }
+  if (row >= 0) {
+    TC* crow = reinterpret_cast<TC*>(d.C) + (int64_t)row * d.ldc + coff;
+    TC o[VE];
 #pragma unroll
-  for (int p = 0; p < V; ++p) {
-    if (row >= 0) {
-      TC* crow = reinterpret_cast<TC*>(d.C) + (int64_t)row * d.ldc + coff[p];
-      TC o[VE];
+    for (int e = 0; e < VE; ++e) o[e] = Tr::kScaled ? (TC)(acc[e] * col_mult<Tr>(d, coff + e)) : (TC)acc[e];
 #pragma unroll
-      for (int e = 0; e < VE; ++e)
-        o[e] = Tr::kScaled ? (TC)(acc[p][e] * col_mult<Tr>(d, coff[p] + e)) : (TC)acc[p][e];
+    for (int q = 0; q < (int)(VE * sizeof(TC) / 16); ++q)
+      *reinterpret_cast<uint4*>(crow + q * (16 / sizeof(TC))) = *reinterpret_cast<const uint4*>(&o[q * (16 / sizeof(TC))]);
+  } else {
+    TAcc* srow = reinterpret_cast<TAcc*>(d.scratch) + (int64_t)(-1 - row) * d.N + coff;
 #pragma unroll
-      for (int q = 0; q < (int)(VE * sizeof(TC) / 16); ++q)
-        *reinterpret_cast<uint4*>(crow + q * (16 / sizeof(TC))) =
-            *reinterpret_cast<const uint4*>(&o[q * (16 / sizeof(TC))]);
-    } else {
-      TAcc* srow = reinterpret_cast<TAcc*>(d.scratch) + (int64_t)(-1 - row) * d.N + coff[p];
-#pragma unroll
-      for (int e = 0; e < VE; ++e) srow[e] = acc[p][e];
-    }
+    for (int e = 0; e < VE; ++e) srow[e] = acc[e];
   }
 }
 
@@ -282,14 +264,13 @@ __global__ void __launch_bounds__(256, LOOPS_BATCHED_MIN_BLOCKS) batched_persist
         hmma_block<typename Tr::TB>(d, task.first, reinterpret_cast<typename Tr::TB*>(smem + warp * smem_per_warp), lane);
       continue;
     }
-    const int G = task.kind == 0 ? d.Gc : d.G;  // CSR items: Gc lanes of Vc vectors each
+    const int G = d.G;
     const int grp = lane / G, sub = lane % G;
     const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (grp * G));
     const int per_round = 32 / G;
     for (int32_t i = grp; i < task.count; i += per_round) {
       if (task.kind == 0) {
-        if (d.Vc == 2) csr_item<Tr, 2, 2>(d, task.first + i, G, sub, gmask);
-        else csr_item<Tr, 1, 4>(d, task.first + i, G, sub, gmask);
+        csr_item<Tr>(d, task.first + i, G, sub, gmask);
       } else if constexpr (std::is_same<Tr, TrF32>::value) {
         ffma_block<BR>(d, task.first + i, sub);
       }

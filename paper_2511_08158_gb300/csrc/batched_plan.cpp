@@ -8,13 +8,6 @@
 
 namespace loops {
 
-// Lanes per CSR item of the batched kernel for a row of G 16-byte vectors: two vectors per lane
-// while the group keeps at least 8 lanes (as the single-matrix CSR kernel does).
-#ifndef LOOPS_BATCHED_LANE_VECTORS
-#define LOOPS_BATCHED_LANE_VECTORS 2
-#endif
-static int csr_item_lanes(int G) { return (LOOPS_BATCHED_LANE_VECTORS == 2 && G >= 16) ? G / 2 : G; }
-
 struct BatchState {
   std::vector<loops_plan_s*> subs;
   int32_t count = 0;
@@ -88,12 +81,11 @@ loops_status build_batch(const loops_csr* As, const int64_t* Ns, int32_t count, 
     b->total_rows += As[m].n_rows;
     const int G = (int)(N / VE);
     const int per_round = 32 / G;
-    const int per_round_c = 32 / csr_item_lanes(G);
     // CSR items: consecutive items (similar length, longest first) up to ~1024 entries
     const CsrDev& c = p->dev.csr;
     for (int64_t i = 0; i < c.n_items;) {
       int64_t j = i, nnz = 0;
-      while (j < c.n_items && (j - i) < (int64_t)32 * per_round_c && (nnz < 1024 || (j - i) < per_round_c)) {
+      while (j < c.n_items && (j - i) < (int64_t)32 * per_round && (nnz < 1024 || (j - i) < per_round)) {
         nnz += c.h_item_ptr[(size_t)j + 1] - c.h_item_ptr[(size_t)j];
         ++j;
       }
@@ -174,8 +166,6 @@ loops_status build_batch(const loops_csr* As, const int64_t* Ns, int32_t count, 
     d.n_rows = p->n_rows;
     d.inv_scale = (float)(1.0 / p->scale);
     d.G = (int32_t)(p->N / VE);
-    d.Gc = csr_item_lanes(d.G);
-    d.Vc = d.G / d.Gc;
     b->device_bytes += p->dev.device_bytes;
   }
   *out = b;

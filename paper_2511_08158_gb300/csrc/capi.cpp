@@ -152,11 +152,6 @@ static loops_plan_s* new_plan(int64_t n_rows, int64_t n_cols, int64_t nnz, int64
   p->other_bytes = 0;
   p->n_csr_rows = p->nnz_csr = p->n_rb = p->n_tiles = 0;
   p->device_built = false;
-  p->l2_bytes = 0;
-  int dev = 0, l2 = 0;
-  if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) == cudaSuccess)
-    p->l2_bytes = l2;
-  cudaGetLastError();
   p->has_vmap = false;
   p->n_subnormal = 0;
   p->nnz_bcsr = 0;

@@ -27,12 +27,9 @@
 #ifndef LOOPS_CSR_LANE_VECTORS
 #define LOOPS_CSR_LANE_VECTORS 2
 #endif
-// L2-sized column chunks (memory-bound formats): when the B columns one launch covers would
-// occupy more than LOOPS_CSR_CHUNK_L2_PCT percent of the L2, the columns are cut into chunks that
-// fit (grid.y, run one after another), so each gathered B row stays in L2 while the chunk is
-// processed; A is then read once per chunk. 0 disables it.
-#ifndef LOOPS_CSR_CHUNK_L2_PCT
-#define LOOPS_CSR_CHUNK_L2_PCT 100
+// Two-lane packed FP32 FMAs in the accumulation of the binary32-accumulating formats.
+#ifndef LOOPS_CSR_FFMA2
+#define LOOPS_CSR_FFMA2 0
 #endif
 // FP64 (bound by the FP64 pipe): entries in flight per lane and resident blocks per SM with
 // one vector per lane.
@@ -146,8 +143,7 @@ __global__ void __launch_bounds__(256, (csr_min_blocks<Tr, VPL>())) csr_spmm_vec
         for (int p = 0; p < VPL; ++p) {
           TAcc b[VE];
           unpack16<Tr>(bv[u][p], b);
-#pragma unroll
-          for (int e = 0; e < VE; ++e) acc[p][e] = fma(av[u], b[e], acc[p][e]);
+          fma_vec<LOOPS_CSR_FFMA2 != 0>(acc[p], av[u], b);
         }
     }
     if constexpr (U > 1) {
@@ -171,8 +167,7 @@ __global__ void __launch_bounds__(256, (csr_min_blocks<Tr, VPL>())) csr_spmm_vec
           for (int p = 0; p < VPL; ++p) {
             TAcc b[VE];
             unpack16<Tr>(bv[u][p], b);
-#pragma unroll
-            for (int e = 0; e < VE; ++e) acc[p][e] = fma(av[u], b[e], acc[p][e]);
+            fma_vec<LOOPS_CSR_FFMA2 != 0>(acc[p], av[u], b);
           }
         }
       }
@@ -331,16 +326,7 @@ cudaError_t launch_csr_t(const loops_plan_s* p, const CsrDev& d, const DenseArgs
   cudaError_t e = cudaSuccess;
   if (a.n_items > 0) {
     if (vec) {
-      int64_t nvec = a.N / VE;  // 16-byte vectors per row this launch covers (per column chunk)
-      if (!std::is_same<Tr, TrF64>::value && LOOPS_CSR_CHUNK_L2_PCT > 0 && p->l2_bytes > 0) {
-        const int64_t budget = p->l2_bytes / 100 * LOOPS_CSR_CHUNK_L2_PCT;
-        const int64_t col_bytes = std::max<int64_t>(p->n_cols, 1) * 16;  // one vector column of B
-        if (nvec * col_bytes > budget) {
-          int64_t fit = std::max<int64_t>(budget / col_bytes, 1), pw = 1;
-          while (pw * 2 <= fit) pw *= 2;
-          nvec = std::min(nvec, pw);
-        }
-      }
+      const int64_t nvec = a.N / VE;
       // lanes per item: the 16-byte vectors of a row, LOOPS_CSR_LANE_VECTORS per lane while
       // the group keeps at least 8 lanes (more vectors per lane: fewer shuffles per byte and
       // more loads in flight per lane; narrower groups lose more to the per-row overhead)

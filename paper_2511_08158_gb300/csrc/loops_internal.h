@@ -203,8 +203,7 @@ struct BatchDesc {
   const float* col_scale;
   int64_t ldb, ldc, N, n_rows;
   float inv_scale;
-  int32_t G;                           // lanes per F32 BCSR block: N / elements per 16 B
-  int32_t Gc, Vc;                      // CSR items: Gc lanes of Vc 16-byte vectors (Gc * Vc = G)
+  int32_t G;                           // lanes per CSR item / F32 block: N / elements per 16 B
 };
 
 // One task of the persistent batched kernel: kind 0 CSR items [first, first + count) of
@@ -280,7 +279,6 @@ struct loops_plan_s {
   // partition counts (canonical): CSR-part rows and entries, BCSR blocks and tiles
   int64_t n_csr_rows, nnz_csr, n_rb, n_tiles;
   bool device_built;                   // built by loops_plan_device (no host canonical copy)
-  int64_t l2_bytes;                    // L2 size of the plan's device (column chunking)
   bool has_vmap;                       // value maps present (loops_plan_set_values works)
 };
 
