@@ -27,10 +27,6 @@
 #ifndef LOOPS_CSR_LANE_VECTORS
 #define LOOPS_CSR_LANE_VECTORS 2
 #endif
-// Two-lane packed FP32 FMAs in the accumulation of the binary32-accumulating formats.
-#ifndef LOOPS_CSR_FFMA2
-#define LOOPS_CSR_FFMA2 0
-#endif
 // FP64 (bound by the FP64 pipe): entries in flight per lane and resident blocks per SM with
 // one vector per lane.
 #ifndef LOOPS_CSR_F64_UNROLL
@@ -143,7 +139,8 @@ __global__ void __launch_bounds__(256, (csr_min_blocks<Tr, VPL>())) csr_spmm_vec
         for (int p = 0; p < VPL; ++p) {
           TAcc b[VE];
           unpack16<Tr>(bv[u][p], b);
-          fma_vec<LOOPS_CSR_FFMA2 != 0>(acc[p], av[u], b);
+#pragma unroll
+          for (int e = 0; e < VE; ++e) acc[p][e] = fma(av[u], b[e], acc[p][e]);
         }
     }
     if constexpr (U > 1) {
@@ -167,7 +164,8 @@ __global__ void __launch_bounds__(256, (csr_min_blocks<Tr, VPL>())) csr_spmm_vec
           for (int p = 0; p < VPL; ++p) {
             TAcc b[VE];
             unpack16<Tr>(bv[u][p], b);
-            fma_vec<LOOPS_CSR_FFMA2 != 0>(acc[p], av[u], b);
+#pragma unroll
+            for (int e = 0; e < VE; ++e) acc[p][e] = fma(av[u], b[e], acc[p][e]);
           }
         }
       }

@@ -35,28 +35,6 @@ struct TrBF16 {
   __device__ static __forceinline__ TAcc to_acc(TB x) { return __bfloat162float(x); }
 };
 
-// acc[e] += a * b[e] for e < VE, each an IEEE fused multiply-add. With `packed` and binary32
-// accumulators the pairs (e, e + 1) go through one two-lane fma.rn.f32x2 (sm_100 and later),
-// which rounds each lane exactly as a scalar fma does.
-template <bool packed, class TAcc, int VE>
-__device__ __forceinline__ void fma_vec(TAcc (&acc)[VE], TAcc a, const TAcc (&b)[VE]) {
-  if constexpr (packed && sizeof(TAcc) == 4 && VE % 2 == 0) {
-    unsigned long long aa;
-    asm("mov.b64 %0, {%1, %1};" : "=l"(aa) : "f"(a));
-#pragma unroll
-    for (int e = 0; e < VE; e += 2) {
-      unsigned long long dd, bb;
-      asm("mov.b64 %0, {%1, %2};" : "=l"(dd) : "f"(acc[e]), "f"(acc[e + 1]));
-      asm("mov.b64 %0, {%1, %2};" : "=l"(bb) : "f"(b[e]), "f"(b[e + 1]));
-      asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(dd) : "l"(aa), "l"(bb));
-      asm("mov.b64 {%0, %1}, %2;" : "=f"(acc[e]), "=f"(acc[e + 1]) : "l"(dd));
-    }
-  } else {
-#pragma unroll
-    for (int e = 0; e < VE; ++e) acc[e] = fma(a, b[e], acc[e]);
-  }
-}
-
 // binary64 -> storage type, round to nearest even (the stored-value rounding of a plan).
 template <class T>
 __device__ __forceinline__ T from_f64(double x);
