@@ -49,10 +49,11 @@ def parse():
     ap.add_argument("--impl", choices=["loops", "reference"], default="loops")
     ap.add_argument("--N", type=int, default=64)
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["laplacian", "rmat", "gcn", "batched", "uniform"], default="laplacian",
-                    help="laplacian (default, the FP64 hybrid-split workload) or one of the other four "
+    ap.add_argument("--workload", choices=["laplacian", "rmat", "gcn", "batched", "uniform", "mixed"],
+                    default="laplacian",
+                    help="laplacian (default, the FP64 hybrid-split workload) or one of the other "
                          "synthetic workloads, measured the same way")
-    ap.add_argument("--dtype", default=None, help="rmat: f16 or bf16; batched: f32 or bf16")
+    ap.add_argument("--dtype", default=None, help="rmat: f16 or bf16; batched, mixed: f32 or bf16")
     ap.add_argument("--batch-count", type=int, default=512,
                     help="batched: number of matrices (smaller counts give small profiling cases)")
     return ap.parse_args()
@@ -351,7 +352,9 @@ def run_loops(args):
     # variants (same inputs, same accuracy), fewer steps
     var_out = {}
     for k, p in vplans.items():
+        torch.cuda.nvtx.range_push(f"variant:{k}")  # lets a profiler select one variant's launches
         s, c, b = time_plan(torch, p, Bd, Cd, max(10, args.steps // 2), 3, flush)
+        torch.cuda.nvtx.range_pop()
         inf_ = p.info()
         var_out[k] = {"tau": variants[k][0], "tile_min": variants[k][1],
                       "gflops": flops / (statistics.mean(s) * 1e-3) / 1e9,
@@ -534,6 +537,16 @@ def run_other(args):
         X = torch.as_tensor(B, dtype=torch.float32).cuda()
         Bd, sc = lp.cast_scaled(X, fmt)
         desc = f"R-MAT 2^20 (a=0.57,b=0.19,c=0.19), avg degree 16, N=128, {fmt} with per-column scaling"
+    elif wl == "mixed":
+        fmt = args.dtype or "f32"
+        A, B = W.block_mix(n=1 << 20, N=64)
+        N, e, c = 64, (4 if fmt == "f32" else 2), 4
+        if fmt == "f32":
+            Bd, sc = torch.as_tensor(B, dtype=torch.float32).cuda(), None
+        else:
+            Bd, sc = lp.cast_scaled(torch.as_tensor(B, dtype=torch.float32).cuda(), fmt)
+        desc = (f"block mix 2^20: half the 16-row blocks two dense 16x16 blocks, the rest 16 uniform "
+                f"columns per row, N=64, {fmt}")
     elif wl == "uniform":
         fmt = "f32"
         A, B = W.uniform_rows(2000, 10, 32, seed=1)
@@ -554,7 +567,9 @@ def run_other(args):
     for name, tau in (("autotuned", -1.0), ("csr_only", math.inf), ("hybrid_tau2", 2.0), ("bcsr_only", 0.0)):
         p = lp.Plan(A, N, fmt, tau=tau, want_backward=(wl == "gcn" and name == "autotuned"))
         plans[name] = p
+        torch.cuda.nvtx.range_push(f"variant:{name}")  # lets a profiler select one variant's launches
         st = time_fn(torch, lambda: p.spmm(Bd, Cd, col_scale=sc), args.steps, args.warmup, flush)
+        torch.cuda.nvtx.range_pop()
         inf = p.info()
         ms = statistics.mean(st)
         res[name] = {"tau": inf["tau"], "gflops": flops / (ms * 1e-3) / 1e9, "ms_per_step": ms,

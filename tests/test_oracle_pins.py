@@ -277,3 +277,20 @@ def test_laplacian_blocks_closed_form_split():
     # tiles of a fully interior augmented block: 8 dense + 8 up + 8 down + left + right
     nnz_bcsr = int(np.count_nonzero(part["tile_val"]))
     assert nnz_bcsr <= 4096 * 82
+
+
+def test_block_mix_split_selects_exactly_the_dense_row_blocks():
+    # A dense row block holds two 16 x 16 blocks: 512 nnz over 32 distinct columns (d = 16);
+    # a sparse one 16 rows x 16 distinct uniform columns: 256 nnz over at most 256 columns
+    # (d = 1 unless columns collide, which needs > 128 collisions to reach d = 2). So tau = 2
+    # selects exactly the dense row blocks, and every tile of them holds 16 entries.
+    A, B = W.block_mix(n=1 << 13, N=4, seed=6)
+    rb_nnz = np.add.reduceat(np.diff(A.row_ptr), np.arange(0, A.n_rows, 16))
+    dense = np.flatnonzero(rb_nnz == 512)
+    assert set(np.unique(rb_nnz)) == {256, 512} and 0 < dense.size < rb_nnz.size
+    part = oracle.partition(A, "f64", block_rows=16, k_pad=1, tau=2.0)
+    assert np.array_equal(part["rb_ids"], dense)
+    assert np.array_equal(np.diff(part["rb_ptr"]), np.full(dense.size, 32))
+    assert np.count_nonzero(part["tile_val"]) == dense.size * 512
+    ref = oracle.spmm(A, B)  # the parts sum in another order: equal up to rounding
+    assert np.allclose(oracle.spmm_partitioned(part, A.n_rows, B), ref, rtol=1e-12, atol=1e-12)

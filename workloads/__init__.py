@@ -217,6 +217,31 @@ def dense_blocks(n: int, blocks_per_row_block: int, bs: int, rng: np.random.Gene
     return csr_from_coo(n, n, r, c, rng.standard_normal(r.size))
 
 
+def block_mix(n: int = 1 << 20, dense_fraction: float = 0.5, blocks_per_row_block: int = 2, bs: int = 16,
+              per_row: int = 16, seed: int = 6, N: int = 64):
+    """One square matrix mixing the two structures the hybrid split separates: a random
+    ``dense_fraction`` of the bs-row blocks hold ``blocks_per_row_block`` dense bs x bs blocks
+    at distinct random bs-aligned columns (bs entries per B_r x 1 tile), the other row blocks
+    ``per_row`` distinct uniform columns per row (about one entry per tile). Values N(0, 1);
+    then B, n x N, N(0, 1). One generator draws everything in that order."""
+    rng = np.random.default_rng(seed)
+    n_rb = (n + bs - 1) // bs
+    dense_rb = rng.random(n_rb) < dense_fraction
+    D = dense_blocks(n, blocks_per_row_block, bs, rng)
+    d_rows = D.row_ids()
+    keep_d = dense_rb[d_rows // bs]
+    sparse_rows = np.flatnonzero(~dense_rb[np.arange(n) // bs])
+    counts = np.full(sparse_rows.size, min(per_row, n), dtype=np.int64)
+    s_cols = _distinct_cols_per_row(rng, counts, n)
+    s_rows = np.repeat(sparse_rows, counts)
+    rows = np.concatenate([d_rows[keep_d], s_rows])
+    cols = np.concatenate([D.col_idx.astype(np.int64)[keep_d], s_cols])
+    vals = np.concatenate([D.vals[keep_d], rng.standard_normal(s_rows.size)])
+    A = csr_from_coo(n, n, rows, cols, vals)
+    B = rng.standard_normal((n, N))
+    return A, B
+
+
 def batched_mix(count: int = 512, seed: int = 5, min_rows: int = 1000, max_rows: int = 65536,
                 Ns=(16, 32, 64, 128)):
     """``count`` square matrices with rows = floor(exp(U[ln min_rows, ln max_rows])); the
