@@ -146,3 +146,27 @@ def test_bad_arguments_are_status_codes(loops_lib):
     assert L.loops_plan_info_get(ctypes.c_void_p(0), ctypes.byref(info)) == 7
     bogus = (ctypes.c_uint64 * 64)()
     assert L.loops_plan_info_get(ctypes.cast(bogus, ctypes.c_void_p), ctypes.byref(info)) == 7
+
+
+def test_plan_device_argument_checks_need_no_gpu(loops_lib):
+    # every check below returns before the first CUDA call (the arrays are never read)
+    L = loops_lib.load()
+    A = W.random_csr(10, 10, 0.3, 1)
+    cs, keep = loops_lib._csr_struct(A)
+    h = ctypes.c_void_p()
+    o = loops_lib._opts(tau=2.0)
+    assert L.loops_plan_device(ctypes.byref(cs), 8, 0, ctypes.byref(o), None, None) == 1        # NULL out
+    assert L.loops_plan_device(None, 8, 0, ctypes.byref(o), None, ctypes.byref(h)) == 1         # NULL A
+    assert L.loops_plan_device(ctypes.byref(cs), 8, 9, ctypes.byref(o), None, ctypes.byref(h)) == 1  # dtype
+    assert L.loops_plan_device(ctypes.byref(cs), -1, 0, ctypes.byref(o), None, ctypes.byref(h)) == 1  # N < 0
+    assert L.loops_plan_device(ctypes.byref(cs), 1 << 21, 0, ctypes.byref(o), None, ctypes.byref(h)) == 3
+    bad_br = loops_lib._opts(tau=2.0, block_rows=12)
+    assert L.loops_plan_device(ctypes.byref(cs), 8, 0, ctypes.byref(bad_br), None, ctypes.byref(h)) == 3
+    nan_tau = loops_lib._opts(tau=float("nan"))
+    assert L.loops_plan_device(ctypes.byref(cs), 8, 0, ctypes.byref(nan_tau), None, ctypes.byref(h)) == 1
+    both = loops_lib._opts(tau=2.0, want_backward=True, tile_min=2)
+    assert L.loops_plan_device(ctypes.byref(cs), 8, 0, ctypes.byref(both), None, ctypes.byref(h)) == 3
+    assert b"tile-level split" in L.loops_last_error()
+    f16_vals = loops_lib._Csr(cs.n_rows, cs.n_cols, cs.nnz, cs.row_ptr, cs.col_idx, cs.vals, 2)
+    assert L.loops_plan_device(ctypes.byref(f16_vals), 8, 0, ctypes.byref(o), None, ctypes.byref(h)) == 3
+    assert h.value is None
