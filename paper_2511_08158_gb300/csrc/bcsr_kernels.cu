@@ -347,16 +347,24 @@ cudaError_t launch_dmma(const BcsrKArgs& a, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------------ F32: CUDA-core outer product
-// A group of G lanes owns one row block and 4*G columns (float4 per lane); per tile it loads
-// the B_r tile values (broadcast) and its float4 of the B row, and does B_r * 4 FMAs.
+// A group of G lanes owns one work unit (tiles of a row block) and VE*G columns (a float4 per
+// lane, or one float). The group reads G tile columns at once and broadcasts them with
+// shuffles; LOOPS_FFMA_BATCH tiles' B loads are kept in flight before their FMAs. Per tile a
+// lane loads the B_r tile values (the same 64 bytes for the whole group: an L1 broadcast) and
+// does B_r * VE FMAs.
+#ifndef LOOPS_FFMA_BATCH
+#define LOOPS_FFMA_BATCH 4
+#endif
 template <int BR, int G, bool VEC>
 __global__ void __launch_bounds__(256) bcsr_ffma(BcsrKArgs a) {
   constexpr int VE = VEC ? 4 : 1;
+  constexpr int U = LOOPS_FFMA_BATCH;
   const int lane = threadIdx.x & 31;
   const int sub = lane & (G - 1);
+  const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
   const int64_t gid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
   const int64_t n_ct = (a.N + G * VE - 1) / (G * VE);
-  if (gid >= a.n_units * n_ct) return;
+  if (gid >= a.n_units * n_ct) return;  // a group leaves as a whole
   const int64_t u = gid / n_ct;
   const int64_t n = (gid % n_ct) * (G * VE) + (int64_t)sub * VE;
   const int32_t b = a.unit_block[u];
@@ -371,29 +379,46 @@ __global__ void __launch_bounds__(256) bcsr_ffma(BcsrKArgs a) {
 #pragma unroll
     for (int e = 0; e < VE; ++e) acc[r][e] = 0.f;
   const bool colok = n < a.N;
-  for (int64_t tt = t0; tt < t1; ++tt) {
-    const int32_t c = __ldg(a.tile_col + tt);
-    float bv[VE];
-    if (VEC) {
-      const uint4 v = (colok && c >= 0) ? ldg16(Bp + (int64_t)c * a.ldb + n) : make_uint4(0, 0, 0, 0);
-      bv[0] = __uint_as_float(v.x);
-      if (VE > 1) { bv[1 % VE] = __uint_as_float(v.y); bv[2 % VE] = __uint_as_float(v.z); bv[3 % VE] = __uint_as_float(v.w); }
-    } else {
-      bv[0] = (colok && c >= 0) ? __ldg(Bp + (int64_t)c * a.ldb + n) : 0.f;
+  for (int64_t k0 = t0; k0 < t1; k0 += G) {
+    const int32_t cmine = k0 + sub < t1 ? __ldg(a.tile_col + k0 + sub) : -1;
+    const int cnt = (int)(t1 - k0 < (int64_t)G ? t1 - k0 : (int64_t)G);  // uniform in the group
+    for (int j0 = 0; j0 < cnt; j0 += U) {
+      float bv[U][VE];
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        const int32_t c = __shfl_sync(gmask, cmine, (j0 + q) & (G - 1), G);
+        const bool ok = colok && j0 + q < cnt && c >= 0;
+        if (VEC) {
+          const uint4 v = ok ? ldg16(Bp + (int64_t)c * a.ldb + n) : make_uint4(0, 0, 0, 0);
+          bv[q][0] = __uint_as_float(v.x);
+          if (VE > 1) {
+            bv[q][1 % VE] = __uint_as_float(v.y);
+            bv[q][2 % VE] = __uint_as_float(v.z);
+            bv[q][3 % VE] = __uint_as_float(v.w);
+          }
+        } else {
+          bv[q][0] = ok ? __ldg(Bp + (int64_t)c * a.ldb + n) : 0.f;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        if (j0 + q >= cnt) break;  // uniform in the group: no FMA on a slot past the unit
+        const int64_t tt = k0 + j0 + q;
+        float av[BR];
+#pragma unroll
+        for (int r4 = 0; r4 < BR / 4; ++r4) {
+          const uint4 v = ldg16(Av + tt * BR + r4 * 4);
+          av[r4 * 4 + 0] = __uint_as_float(v.x);
+          av[r4 * 4 + 1] = __uint_as_float(v.y);
+          av[r4 * 4 + 2] = __uint_as_float(v.z);
+          av[r4 * 4 + 3] = __uint_as_float(v.w);
+        }
+#pragma unroll
+        for (int r = 0; r < BR; ++r)
+#pragma unroll
+          for (int e = 0; e < VE; ++e) acc[r][e] = fmaf(av[r], bv[q][e], acc[r][e]);
+      }
     }
-    float av[BR];
-#pragma unroll
-    for (int r4 = 0; r4 < BR / 4; ++r4) {
-      const uint4 v = ldg16(Av + tt * BR + r4 * 4);
-      av[r4 * 4 + 0] = __uint_as_float(v.x);
-      av[r4 * 4 + 1] = __uint_as_float(v.y);
-      av[r4 * 4 + 2] = __uint_as_float(v.z);
-      av[r4 * 4 + 3] = __uint_as_float(v.w);
-    }
-#pragma unroll
-    for (int r = 0; r < BR; ++r)
-#pragma unroll
-      for (int e = 0; e < VE; ++e) acc[r][e] = fmaf(av[r], bv[e], acc[r][e]);
   }
   if (!colok) return;
   if (slot >= 0) {  // one unit of a split block: partial sums of its BR rows
