@@ -54,7 +54,8 @@ typedef enum {
 
 typedef enum { LOOPS_F64 = 0, LOOPS_F32 = 1, LOOPS_F16 = 2, LOOPS_BF16 = 3 } loops_dtype;
 
-/* Sparse input A in CSR form, all arrays on the HOST and borrowed only for the call.
+/* Sparse input A in CSR form; the arrays are borrowed only for the call and live on the HOST
+ * (loops_plan, loops_partition_host, loops_plan_batched) or on the DEVICE (loops_plan_device).
  * row_ptr: int64[n_rows + 1], row_ptr[0] = 0, non-decreasing, row_ptr[n_rows] = nnz.
  * col_idx: int32[nnz], 0 <= col < n_cols; columns may be unsorted and may repeat (repeats
  *          are summed). vals: nnz values of type vals_dtype (LOOPS_F64 or LOOPS_F32). */
