@@ -272,8 +272,9 @@ loops_status loops_plan_set_timing_events(loops_plan_t plan, void* const* events
  * LOOPS_ERR_TIMEOUT when a bounded device-side wait gave up in an earlier launch. */
 loops_status loops_plan_check(loops_plan_t plan, loops_stream_t stream);
 
-/* Batched plan (the benchmark spec batching pattern; the paper runs one matrix at a time): `count`
- * matrices As[m] (host CSR, as for loops_plan) with their own N = Ns[m], in one dtype
+/* Batched plan (the paper runs one matrix at a time; many matrices in one launch has no
+ * counterpart there): `count` matrices As[m] (host CSR, as for loops_plan) with their own
+ * N = Ns[m], in one dtype
  * (LOOPS_F32, LOOPS_F16 or LOOPS_BF16). Each N must be a multiple of the elements of a 16-byte
  * vector (4 for F32, 8 otherwise) and at most 128 (F32: 128, 16-bit: 128). opts->tau < 0 autotunes the
  * split threshold (and, for F32 with block_rows 0, the tile height) by timing the whole batch
@@ -281,6 +282,14 @@ loops_status loops_plan_check(loops_plan_t plan, loops_stream_t stream);
  * a CUDA graph by the first loops_spmm_batched call and replayed by later ones. */
 loops_status loops_plan_batched(const loops_csr* As, const int64_t* Ns, int32_t count, loops_dtype dtype,
                                 const loops_plan_opts* opts, loops_stream_t stream, loops_plan_t* out);
+
+/* The same batched plan with every matrix's conversion run on the GPU (as loops_plan_device):
+ * the CSR arrays of As[m] are DEVICE pointers, borrowed for the call. Each matrix is validated
+ * once on the device (errors name the matrix); the sub-plans equal loops_plan_batched's bit for
+ * bit, and so does the task list. Synchronises `stream`. No counterpart in the paper. */
+loops_status loops_plan_batched_device(const loops_csr* As, const int64_t* Ns, int32_t count,
+                                       loops_dtype dtype, const loops_plan_opts* opts,
+                                       loops_stream_t stream, loops_plan_t* out);
 
 /* C_m = A_m . B_m for every matrix of a batched plan. Bs, Cs, ldbs, ldcs: HOST arrays of
  * `count` entries holding device pointers / leading dimensions (rows 16-byte aligned);

@@ -33,7 +33,8 @@ EXPORTED = ["loops_version", "loops_status_str", "loops_last_error", "loops_plan
             "loops_spmm_scaled", "loops_spmm_host", "loops_spmm_backward", "loops_cast_scaled",
             "loops_plan_check", "loops_plan_set_timing_events", "loops_plan_set_values",
             "loops_csr_spmm_noalloc", "loops_plan_batched", "loops_spmm_batched", "loops_plan_batched_info",
-            "loops_spmm_host_async", "loops_spmm_host_flush", "loops_plan_device"]
+            "loops_spmm_host_async", "loops_spmm_host_flush", "loops_plan_device",
+            "loops_plan_batched_device"]
 
 
 class LoopsError(RuntimeError):
@@ -120,6 +121,8 @@ def load():
     L.loops_plan_set_values.argtypes = [vp, vp, ctypes.c_int, vp]
     L.loops_csr_spmm_noalloc.argtypes = [i64, i64, i64, vp, vp, vp, ctypes.c_int, vp, i64, i64, vp, i64, vp]
     L.loops_plan_batched.argtypes = [ctypes.POINTER(_Csr), ctypes.POINTER(ctypes.c_int64), ctypes.c_int32, ctypes.c_int,
+                                     ctypes.POINTER(_Opts), vp, ctypes.POINTER(vp)]
+    L.loops_plan_batched_device.argtypes = [ctypes.POINTER(_Csr), ctypes.POINTER(ctypes.c_int64), ctypes.c_int32, ctypes.c_int,
                                      ctypes.POINTER(_Opts), vp, ctypes.POINTER(vp)]
     L.loops_spmm_batched.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(vp),
                                      ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(vp), vp]
@@ -384,7 +387,9 @@ class BatchedPlan:
     (``loops_plan_batched`` / ``loops_spmm_batched``)."""
 
     def __init__(self, As, Ns, dtype: str = "f32", tau: float = -1.0, block_rows: int = 0, split_len: int = 0,
-                 stream=None):
+                 stream=None, build_on_device: bool = False):
+        """build_on_device: convert every matrix on the GPU (``loops_plan_batched_device``);
+        the matrices' arrays may then be CUDA tensors (host arrays are copied first)."""
         L = load()
         self._L = L
         self.dtype = _DT[dtype]
@@ -393,15 +398,15 @@ class BatchedPlan:
         self.shapes = [(int(A.n_rows), int(A.n_cols)) for A in As]
         structs, self._keep = [], []
         for A in As:
-            cs, keep = _csr_struct(A)
+            cs, keep = _csr_struct_device(A) if build_on_device else _csr_struct(A)
             structs.append(cs)
             self._keep.append(keep)
         arr = (_Csr * max(1, self.count))(*structs)
         ns = (ctypes.c_int64 * max(1, self.count))(*self.Ns)
         o = _opts(tau, block_rows, False, 0, False, split_len)
         h = ctypes.c_void_p()
-        _check(L.loops_plan_batched(arr, ns, self.count, self.dtype, ctypes.byref(o), _stream_handle(stream),
-                                    ctypes.byref(h)))
+        entry = L.loops_plan_batched_device if build_on_device else L.loops_plan_batched
+        _check(entry(arr, ns, self.count, self.dtype, ctypes.byref(o), _stream_handle(stream), ctypes.byref(h)))
         self._keep = None  # the plan does not keep the host CSR arrays
         self._h = h
 

@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <functional>
 
 #include "loops_internal.h"
 
@@ -48,9 +49,14 @@ namespace {
 
 int elems_per_16b(loops_dtype d) { return d == LOOPS_F32 ? 4 : 8; }
 
+// Builds the sub-plan of matrix m for the given options, tile height and threshold.
+using SubBuilder = std::function<loops_status(int32_t m, const loops_plan_opts& o, int32_t br, double tau,
+                                              loops_plan_s** out)>;
+
 // Build the sub-plans, task list and descriptor tables for a fixed tau.
 loops_status build_batch(const loops_csr* As, const int64_t* Ns, int32_t count, loops_dtype dtype,
-                         const loops_plan_opts& o, int32_t br, double tau, BatchState** out) {
+                         const loops_plan_opts& o, int32_t br, double tau, const SubBuilder& sub,
+                         BatchState** out) {
   *out = nullptr;
   BatchState* b = new (std::nothrow) BatchState();
   if (!b) { set_error("host allocation failed"); return LOOPS_ERR_OOM; }
@@ -63,7 +69,6 @@ loops_status build_batch(const loops_csr* As, const int64_t* Ns, int32_t count, 
   std::vector<BatchTask> tasks;
   std::vector<double> cost;
   std::vector<int2> splits, bsplits;
-  std::vector<double> vals;
   for (int32_t m = 0; m < count && !st; ++m) {
     const int64_t N = Ns[m];
     if (N <= 0 || N % VE != 0 || N > (dtype == LOOPS_F32 ? 32 * VE : 128)) {
@@ -72,10 +77,8 @@ loops_status build_batch(const loops_csr* As, const int64_t* Ns, int32_t count, 
       st = LOOPS_ERR_UNSUPPORTED;
       break;
     }
-    if ((st = validate_csr(&As[m]))) break;
-    read_vals_f64(&As[m], vals);
     loops_plan_s* p = nullptr;
-    if ((st = make_plan(&As[m], vals.data(), N, dtype, o, br, tau, true, &p))) break;
+    if ((st = sub(m, o, br, tau, &p))) break;
     b->subs.push_back(p);
     b->total_nnz += As[m].nnz;
     b->total_rows += As[m].n_rows;
@@ -238,10 +241,11 @@ loops_status spmm_batch(BatchState* b, const void* const* Bs, const int64_t* ldb
 
 using namespace loops;
 
-extern "C" {
-
-loops_status loops_plan_batched(const loops_csr* As, const int64_t* Ns, int32_t count, loops_dtype dtype,
-                                const loops_plan_opts* opts, loops_stream_t stream, loops_plan_t* out) {
+// loops_plan_batched / loops_plan_batched_device: the matrices' arrays are on the host
+// (`device` false) or on the device.
+static loops_status plan_batched(const loops_csr* As, const int64_t* Ns, int32_t count, loops_dtype dtype,
+                                 const loops_plan_opts* opts, loops_stream_t stream, bool device,
+                                 loops_plan_t* out) {
   clear_error();
   if (!out) { set_error("out is NULL"); return LOOPS_ERR_INVALID_ARG; }
   *out = nullptr;
@@ -265,9 +269,42 @@ loops_status loops_plan_batched(const loops_csr* As, const int64_t* Ns, int32_t 
   loops_status st = resolve_block_rows(dtype, o, &br);
   if (st) return st;
   cudaStream_t s = (cudaStream_t)stream;
+  // per-matrix sub-plan builder: validate and convert on the host, or validate each matrix
+  // once on the device (its plan scale kept) and convert on the device
+  std::vector<double> vals, scales;
+  if (device) {
+    scales.assign((size_t)std::max(count, 0), 1.0);
+    for (int32_t m = 0; m < count; ++m) {
+      if (As[m].vals_dtype != LOOPS_F64 && As[m].vals_dtype != LOOPS_F32) {
+        set_error("A values must be LOOPS_F64 or LOOPS_F32 on input (matrix " + std::to_string(m) + ")");
+        return LOOPS_ERR_UNSUPPORTED;
+      }
+      const DevCsrIn d{As[m].n_rows, As[m].n_cols, As[m].nnz, As[m].row_ptr, As[m].col_idx, As[m].vals,
+                       As[m].vals_dtype == LOOPS_F32};
+      double mx = 0.0;
+      if ((st = validate_csr_device(d, dtype, s, &mx))) {
+        set_error(std::string(loops_last_error()) + " (matrix " + std::to_string(m) + ")");
+        return st;
+      }
+      scales[(size_t)m] = plan_scale_from_max(mx, dtype);
+    }
+  }
+  const SubBuilder sub = [&](int32_t m, const loops_plan_opts& oc, int32_t brc, double t, loops_plan_s** q) {
+    loops_status r;
+    if (device) {
+      const DevCsrIn d{As[m].n_rows, As[m].n_cols, As[m].nnz, As[m].row_ptr, As[m].col_idx, As[m].vals,
+                       As[m].vals_dtype == LOOPS_F32};
+      r = make_plan_device(d, nullptr, scales[(size_t)m], Ns[m], dtype, oc, brc, t, false, true, s, q);
+      if (!r) r = download_mirrors(*q);
+      return r;
+    }
+    if ((r = validate_csr(&As[m]))) return r;
+    read_vals_f64(&As[m], vals);
+    return make_plan(&As[m], vals.data(), Ns[m], dtype, oc, brc, t, true, q);
+  };
   BatchState* best = nullptr;
   if (o.tau >= 0.0) {
-    if ((st = build_batch(As, Ns, count, dtype, o, br, o.tau, &best))) return st;
+    if ((st = build_batch(As, Ns, count, dtype, o, br, o.tau, sub, &best))) return st;
   } else {
     // autotune: split threshold (and, for F32, the tile height) by timing the whole batch
     struct Cand { double tau; int32_t br; };
@@ -302,7 +339,7 @@ loops_status loops_plan_batched(const loops_csr* As, const int64_t* Ns, int32_t 
       loops_plan_opts oc = o;
       oc.block_rows = c.br;
       BatchState* b = nullptr;
-      if ((st = build_batch(As, Ns, count, dtype, oc, c.br, c.tau, &b))) break;
+      if ((st = build_batch(As, Ns, count, dtype, oc, c.br, c.tau, sub, &b))) break;
       float ms = INFINITY;
       for (int it = 0; it < 5 && !st; ++it) {
         if (it >= 2) cudaEventRecord(e0, s);
@@ -368,8 +405,21 @@ loops_status loops_plan_batched(const loops_csr* As, const int64_t* Ns, int32_t 
     p->nnz_bcsr += sp->nnz_bcsr;
     p->n_subnormal += sp->n_subnormal;
   }
+  p->device_built = device;
   *out = p;
   return LOOPS_OK;
+}
+
+extern "C" {
+
+loops_status loops_plan_batched(const loops_csr* As, const int64_t* Ns, int32_t count, loops_dtype dtype,
+                                const loops_plan_opts* opts, loops_stream_t stream, loops_plan_t* out) {
+  return plan_batched(As, Ns, count, dtype, opts, stream, false, out);
+}
+
+loops_status loops_plan_batched_device(const loops_csr* As, const int64_t* Ns, int32_t count, loops_dtype dtype,
+                                       const loops_plan_opts* opts, loops_stream_t stream, loops_plan_t* out) {
+  return plan_batched(As, Ns, count, dtype, opts, stream, true, out);
 }
 
 loops_status loops_spmm_batched(loops_plan_t p, const void* const* Bs, const int64_t* ldbs, void* const* Cs,

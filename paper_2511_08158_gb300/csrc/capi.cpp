@@ -199,9 +199,9 @@ loops_status make_plan(const loops_csr* A, const double* vals, int64_t N, loops_
 }
 
 // The same plan built on the device from a device-resident CSR matrix (plan_device.cu).
-static loops_status make_plan_device(const DevCsrIn& A, const int64_t* remap, double scale, int64_t N,
-                                     loops_dtype dtype, const loops_plan_opts& o, int32_t br, double tau,
-                                     bool want_maps, cudaStream_t s, loops_plan_s** out) {
+loops_status make_plan_device(const DevCsrIn& A, const int64_t* remap, double scale, int64_t N, loops_dtype dtype,
+                              const loops_plan_opts& o, int32_t br, double tau, bool want_maps, bool light,
+                              cudaStream_t s, loops_plan_s** out) {
   *out = nullptr;
   loops_plan_s* p = new_plan(A.n_rows, A.n_cols, A.nnz, N, dtype, o, br, tau);
   if (!p) return LOOPS_ERR_OOM;
@@ -209,7 +209,7 @@ static loops_status make_plan_device(const DevCsrIn& A, const int64_t* remap, do
   p->scale = scale;
   loops_status st = build_part_device(p, A, remap, N, tau, o.contiguous_split != 0, o.r_boundary,
                                       want_maps && p->tile_min == 0, s);
-  if (!st) st = plan_runtime(p);
+  if (!st && !light) st = plan_runtime(p);
   if (st) { destroy_plan(p); return st; }
   *out = p;
   return LOOPS_OK;
@@ -601,7 +601,7 @@ loops_status loops_plan_device(const loops_csr* A, int64_t N, loops_dtype dtype,
   if ((st = validate_csr_device(d, dtype, s, &max_abs))) return st;
   const double scale = plan_scale_from_max(max_abs, dtype);
   const PlanBuilder dev_build = [&](const loops_plan_opts& oc, double t, loops_plan_s** q) {
-    return make_plan_device(d, nullptr, scale, N, dtype, oc, br, t, false, s, q);
+    return make_plan_device(d, nullptr, scale, N, dtype, oc, br, t, false, false, s, q);
   };
   double tau = o.tau;
   if (tau < 0.0 && !o.contiguous_split) {
@@ -616,7 +616,7 @@ loops_status loops_plan_device(const loops_csr* A, int64_t N, loops_dtype dtype,
       return st;
   }
   loops_plan_s* p = nullptr;
-  if ((st = make_plan_device(d, nullptr, scale, N, dtype, o, br, tau, true, s, &p))) return st;
+  if ((st = make_plan_device(d, nullptr, scale, N, dtype, o, br, tau, true, false, s, &p))) return st;
   if (o.want_backward) {
     int64_t* trp = nullptr;
     int32_t* tci = nullptr;
@@ -629,7 +629,7 @@ loops_status loops_plan_device(const loops_csr* A, int64_t N, loops_dtype dtype,
       ot.want_backward = 0;
       ot.contiguous_split = 0;
       loops_plan_s* pt = nullptr;
-      st = make_plan_device(dt, perm, scale, N, dtype, ot, br, tau, true, s, &pt);
+      st = make_plan_device(dt, perm, scale, N, dtype, ot, br, tau, true, false, s, &pt);
       p->transposed = pt;
     }
     if (!st) st = build_sddmm_device(p, d, s);

@@ -345,6 +345,14 @@ loops_status build_part_device(loops_plan_s* p, const DevCsrIn& A, const int64_t
 loops_status build_sddmm_device(loops_plan_s* p, const DevCsrIn& A, cudaStream_t s);
 loops_status transpose_device(const DevCsrIn& A, int64_t** t_rp, int32_t** t_ci, double** t_vals, int64_t** perm,
                               cudaStream_t s);
+// A plan built on the device (capi.cpp); `light` plans (sub-plans of a batch) get no side
+// stream, events or error word.
+loops_status make_plan_device(const DevCsrIn& A, const int64_t* remap, double scale, int64_t N, loops_dtype dtype,
+                              const loops_plan_opts& o, int32_t br, double tau, bool want_maps, bool light,
+                              cudaStream_t s, loops_plan_s** out);
+// Host copies of the work-item offsets and unit lengths of a device-built plan (the batched
+// task list is formed from them on the host).
+loops_status download_mirrors(loops_plan_s* p);
 
 cudaError_t launch_set_values(const loops_plan_s* p, const void* vals, loops_dtype vd, cudaStream_t s);
 cudaError_t launch_cast_scaled(const float* X, int64_t rows, int64_t cols, int64_t ldx,

@@ -1314,6 +1314,24 @@ loops_status transpose_device(const DevCsrIn& A, int64_t** t_rp, int32_t** t_ci,
   return check_build_err(s, what);
 }
 
+loops_status download_mirrors(loops_plan_s* p) {
+  const char* what = "device plan build (host mirrors)";
+  for (CsrDev* cd : {&p->dev.csr, &p->dev.csr_acc}) {
+    cd->h_item_ptr.assign((size_t)(cd->n_items ? cd->n_items + 1 : 0), 0);
+    if (cd->n_items)
+      TRY(cudaMemcpy(cd->h_item_ptr.data(), cd->item_ptr, (size_t)(cd->n_items + 1) * 8, cudaMemcpyDeviceToHost));
+  }
+  BcsrDev& bd = p->dev.bcsr;
+  bd.h_unit_tiles.assign((size_t)bd.n_units, 0);
+  if (bd.n_units) {
+    std::vector<int64_t> u0((size_t)bd.n_units), u1((size_t)bd.n_units);
+    TRY(cudaMemcpy(u0.data(), bd.unit_t0, (size_t)bd.n_units * 8, cudaMemcpyDeviceToHost));
+    TRY(cudaMemcpy(u1.data(), bd.unit_t1, (size_t)bd.n_units * 8, cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < u0.size(); ++i) bd.h_unit_tiles[i] = u1[i] - u0[i];
+  }
+  return LOOPS_OK;
+}
+
 #undef TRY
 #undef NEED
 

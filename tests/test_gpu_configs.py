@@ -106,6 +106,41 @@ def test_config4_gcn_forward_backward(lp):
     assert rel_l2(dv.double().cpu().numpy()[ks], dv_ref[ks]) <= TOL["f32"]
 
 
+def _same_export(a, b):
+    for k in ("csr_rows", "csr_ptr", "csr_col", "rb_ids", "rb_ptr", "tile_col", "csr_val", "tile_val"):
+        assert np.array_equal(np.asarray(a[k]), np.asarray(b[k])), k
+
+
+@pytest.mark.parametrize("tau", [2.0, 1.25, 0.0])
+def test_config3_device_built_plan_equals_host_plan(lp, rmat20, tau):
+    # the conversion on the GPU at full size (15.6 M entries, hub rows cut into segments and
+    # long blocks into units): the same partition, values and product as the host build
+    A, B = rmat20
+    ph = lp.Plan(A, 128, "f16", tau=tau)
+    pd = lp.Plan(A, 128, "f16", tau=tau, build_on_device=True)
+    _same_export(ph.export(), pd.export())
+    for k in ("n_csr_rows", "nnz_csr", "n_row_blocks", "n_tiles", "nnz_bcsr", "n_split_rows", "n_segments",
+              "n_subnormal_vals", "scale"):
+        assert ph.info()[k] == pd.info()[k], k
+    Bq, s = oracle.scale_round_columns(B, "f16")
+    Bd = torch.as_tensor(Bq).to(torch.float16).cuda()
+    sd = torch.as_tensor(s, dtype=torch.float32).cuda()
+    assert torch.equal(ph.spmm(Bd, col_scale=sd), pd.spmm(Bd, col_scale=sd))
+
+
+def test_config4_device_built_backward_equals_host(lp):
+    A, X, dY = W.gcn_graph(scale=18, samples_per_node=16, seed=4, N=256)
+    A32 = W.CSR(A.n_rows, A.n_cols, A.row_ptr, A.col_idx, A.vals.astype(np.float32))
+    ph = lp.Plan(A32, 256, "f32", tau=2.0, want_backward=True)
+    pd = lp.Plan(A32, 256, "f32", tau=2.0, want_backward=True, build_on_device=True)
+    _same_export(ph.export(), pd.export())
+    Xd = torch.as_tensor(X, dtype=torch.float32).cuda()
+    dYd = torch.as_tensor(dY, dtype=torch.float32).cuda()
+    assert torch.equal(ph.spmm(Xd), pd.spmm(Xd))
+    (dXh, dvh), (dXd, dvd) = ph.backward(dYd, Xd), pd.backward(dYd, Xd)
+    assert torch.equal(dXh, dXd) and torch.equal(dvh, dvd)
+
+
 @pytest.fixture(scope="module")
 def batch512():
     return W.batched_mix(count=512, seed=5)

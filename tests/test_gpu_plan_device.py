@@ -238,3 +238,38 @@ def test_device_build_rejects_invalid_csr_like_host(lp):
         assert msgs[0] == msgs[1], (name, msgs)
     # the context is still usable afterwards
     lp.Plan(good, 8, "f64", tau=2.0, build_on_device=True)
+
+
+@pytest.mark.parametrize("fmt", ["f32", "bf16"])
+@pytest.mark.parametrize("tau", [math.inf, 2.0, 0.0, -1.0])
+def test_batched_device_build_equals_host_build(lp, fmt, tau):
+    mats = W.batched_mix(count=12, seed=9, min_rows=100, max_rows=4000)
+    As = [A for A, _ in mats]
+    Ns = [N for _, N in mats]
+    bh = lp.BatchedPlan(As, Ns, fmt, tau=tau)
+    bd = lp.BatchedPlan(As, Ns, fmt, tau=tau, build_on_device=True)
+    dt = torch.float32 if fmt == "f32" else torch.bfloat16
+    g = torch.Generator(device="cuda").manual_seed(3)
+    Bs = [torch.randn((A.n_cols, N), device="cuda", generator=g).to(dt) for A, N in mats]
+    if tau >= 0:  # fixed split: the same sub-plans and task list, so the same outputs bit for bit
+        assert bh.info() == bd.info()
+        for Ch, Cd in zip(bh.spmm(Bs), bd.spmm(Bs)):
+            assert torch.equal(Ch, Cd)
+    else:  # autotuned: each may time a different winner; both agree with the oracle
+        for (A, N), B, C in zip(mats, Bs, bd.spmm(Bs)):
+            s_a = oracle.plan_scale(A.vals, fmt)
+            A_r = W.CSR(A.n_rows, A.n_cols, A.row_ptr, A.col_idx, oracle.round_to(A.vals * s_a, fmt) / s_a)
+            ref = oracle.spmm(A_r, B.double().cpu().numpy())
+            assert rel_l2(C.double().cpu().numpy(), ref) <= TOL[fmt]
+
+
+def test_batched_device_build_names_the_invalid_matrix(lp):
+    mats = W.batched_mix(count=3, seed=9, min_rows=100, max_rows=400)
+    As = [A for A, _ in mats]
+    bad = As[1]
+    ci = bad.col_idx.copy()
+    ci[3] = bad.n_cols  # out of range (only compared, never used as an index)
+    As[1] = W.CSR(bad.n_rows, bad.n_cols, bad.row_ptr, ci, bad.vals)
+    with pytest.raises(lp.LoopsError) as ei:
+        lp.BatchedPlan(As, [N for _, N in mats], "f32", tau=2.0, build_on_device=True)
+    assert "matrix 1" in str(ei.value) and "column index out of range at entry 3" in str(ei.value)
