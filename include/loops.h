@@ -189,7 +189,17 @@ loops_status loops_plan(const loops_csr* A, int64_t N, loops_dtype dtype,
 loops_status loops_plan_device(const loops_csr* A, int64_t N, loops_dtype dtype,
                                const loops_plan_opts* opts, loops_stream_t stream, loops_plan_t* out);
 
-/* Release a plan and its device memory (synchronises the device first). NULL is a no-op. */
+/* Test hook for the error paths (not for production use): the n-th device or pinned-host
+ * allocation the library makes from now on (n >= 1) fails as if memory were exhausted, and the
+ * call that made it returns LOOPS_ERR_OOM after releasing what it had allocated; n <= 0 disarms.
+ * Returns the number of allocations made since the previous call of this hook, so a test can
+ * count the allocations of an operation first and then fail each of them in turn. The paper
+ * has no counterpart. Process-wide; not meant to be armed while other threads build plans. */
+int64_t loops_test_fail_alloc(int64_t n);
+
+/* Release a plan and its device memory (synchronises the device first). NULL is a no-op. A
+ * handle that is not a live plan (never returned, or already destroyed) gives
+ * LOOPS_ERR_STATE here and in every other call, without its memory being read. */
 loops_status loops_plan_destroy(loops_plan_t plan);
 
 /* Counts of the plan (host only, no GPU work). */

@@ -34,7 +34,7 @@ EXPORTED = ["loops_version", "loops_status_str", "loops_last_error", "loops_plan
             "loops_plan_check", "loops_plan_set_timing_events", "loops_plan_set_values",
             "loops_csr_spmm_noalloc", "loops_plan_batched", "loops_spmm_batched", "loops_plan_batched_info",
             "loops_spmm_host_async", "loops_spmm_host_flush", "loops_plan_device",
-            "loops_plan_batched_device"]
+            "loops_plan_batched_device", "loops_test_fail_alloc"]
 
 
 class LoopsError(RuntimeError):
@@ -104,6 +104,8 @@ def load():
     L.loops_partition_free.argtypes = [ctypes.POINTER(_Part)]
     L.loops_partition_free.restype = None
     L.loops_plan.argtypes = [ctypes.POINTER(_Csr), i64, ctypes.c_int, ctypes.POINTER(_Opts), vp, ctypes.POINTER(vp)]
+    L.loops_test_fail_alloc.argtypes = [i64]
+    L.loops_test_fail_alloc.restype = i64
     L.loops_plan_device.argtypes = [ctypes.POINTER(_Csr), i64, ctypes.c_int, ctypes.POINTER(_Opts), vp,
                                     ctypes.POINTER(vp)]
     L.loops_plan_destroy.argtypes = [vp]

@@ -126,15 +126,15 @@ loops_status build_batch(const loops_csr* As, const int64_t* Ns, int32_t count, 
   b->smem_per_warp = dtype == LOOPS_F32 ? 0 : (16 * (64 + 8) * 2 + 127) / 128 * 128;  // one 64-column chunk
   b->grid = batched_grid_blocks(dtype, br, b->smem_per_warp);
   // descriptors (static parts now; B/C pointers per call)
-  cudaError_t e = cudaMallocHost((void**)&b->h_desc, sizeof(BatchDesc) * (size_t)std::max(count, 1));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_desc, sizeof(BatchDesc) * (size_t)std::max(count, 1));
-  if (e == cudaSuccess && b->n_tasks) e = cudaMalloc((void**)&b->d_tasks, sizeof(BatchTask) * (size_t)b->n_tasks);
+  cudaError_t e = host_malloc((void**)&b->h_desc, sizeof(BatchDesc) * (size_t)std::max(count, 1));
+  if (e == cudaSuccess) e = dev_malloc((void**)&b->d_desc, sizeof(BatchDesc) * (size_t)std::max(count, 1));
+  if (e == cudaSuccess && b->n_tasks) e = dev_malloc((void**)&b->d_tasks, sizeof(BatchTask) * (size_t)b->n_tasks);
   if (e == cudaSuccess && b->n_tasks)
     e = cudaMemcpy(b->d_tasks, sorted.data(), sizeof(BatchTask) * (size_t)b->n_tasks, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && b->n_splits) e = cudaMalloc((void**)&b->d_splits, sizeof(int2) * (size_t)b->n_splits);
+  if (e == cudaSuccess && b->n_splits) e = dev_malloc((void**)&b->d_splits, sizeof(int2) * (size_t)b->n_splits);
   if (e == cudaSuccess && b->n_splits)
     e = cudaMemcpy(b->d_splits, splits.data(), sizeof(int2) * (size_t)b->n_splits, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && b->n_bsplits) e = cudaMalloc((void**)&b->d_bsplits, sizeof(int2) * (size_t)b->n_bsplits);
+  if (e == cudaSuccess && b->n_bsplits) e = dev_malloc((void**)&b->d_bsplits, sizeof(int2) * (size_t)b->n_bsplits);
   if (e == cudaSuccess && b->n_bsplits)
     e = cudaMemcpy(b->d_bsplits, bsplits.data(), sizeof(int2) * (size_t)b->n_bsplits, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
@@ -323,8 +323,8 @@ static loops_status plan_batched(const loops_csr* As, const int64_t* Ns, int32_t
     cudaError_t e = cudaSuccess;
     for (int32_t m = 0; m < count && e == cudaSuccess; ++m) {
       void *pb = nullptr, *pc = nullptr;
-      e = cudaMalloc(&pb, (size_t)std::max<int64_t>(As[m].n_cols * Ns[m] * eb, 16));
-      if (e == cudaSuccess) e = cudaMalloc(&pc, (size_t)std::max<int64_t>(As[m].n_rows * Ns[m] * 4, 16));
+      e = dev_malloc(&pb, (size_t)std::max<int64_t>(As[m].n_cols * Ns[m] * eb, 16));
+      if (e == cudaSuccess) e = dev_malloc(&pc, (size_t)std::max<int64_t>(As[m].n_rows * Ns[m] * 4, 16));
       if (e == cudaSuccess) e = cudaMemsetAsync(pb, 0x3C, (size_t)(As[m].n_cols * Ns[m] * eb), s);
       bufs.push_back(pb);
       bufs.push_back(pc);
@@ -406,6 +406,7 @@ static loops_status plan_batched(const loops_csr* As, const int64_t* Ns, int32_t
     p->n_subnormal += sp->n_subnormal;
   }
   p->device_built = device;
+  register_plan(p);
   *out = p;
   return LOOPS_OK;
 }

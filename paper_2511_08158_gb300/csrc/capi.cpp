@@ -1,5 +1,8 @@
 // C-ABI entry points of libloops.so (declared in include/loops.h).
 #include <algorithm>
+#include <atomic>
+#include <mutex>
+#include <unordered_set>
 #include <functional>
 #include <cmath>
 #include <cstdlib>
@@ -28,12 +31,60 @@ loops_status cuda_status(cudaError_t e, const char* what) {
   return e == cudaErrorMemoryAllocation ? LOOPS_ERR_OOM : LOOPS_ERR_CUDA;
 }
 
+// ------------------------------------------------------------------ allocation hook
+static std::atomic<int64_t> g_alloc_countdown{0};  // > 0: this many allocations from now, the last fails
+static std::atomic<int64_t> g_alloc_seen{0};       // allocations since the last loops_test_fail_alloc
+
+static bool alloc_should_fail() {
+  g_alloc_seen.fetch_add(1, std::memory_order_relaxed);
+  int64_t c = g_alloc_countdown.load();
+  while (c > 0) {
+    if (g_alloc_countdown.compare_exchange_weak(c, c - 1)) return c == 1;
+  }
+  return false;
+}
+
+cudaError_t dev_malloc_raw(void** p, size_t bytes) {
+  if (alloc_should_fail()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, bytes);
+}
+
+cudaError_t host_malloc_raw(void** p, size_t bytes) {
+  if (alloc_should_fail()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMallocHost(p, bytes);
+}
+
+// ------------------------------------------------------------------ live handles
+static std::mutex g_plans_mu;
+static std::unordered_set<const loops_plan_s*> g_plans;
+
+void register_plan(const loops_plan_s* p) {
+  std::lock_guard<std::mutex> g(g_plans_mu);
+  g_plans.insert(p);
+}
+
+void unregister_plan(const loops_plan_s* p) {
+  std::lock_guard<std::mutex> g(g_plans_mu);
+  g_plans.erase(p);
+}
+
+static bool plan_live(const loops_plan_s* p) {
+  std::lock_guard<std::mutex> g(g_plans_mu);
+  return g_plans.count(p) != 0;
+}
+
 static bool valid_dtype(loops_dtype d) {
   return d == LOOPS_F64 || d == LOOPS_F32 || d == LOOPS_F16 || d == LOOPS_BF16;
 }
 
 loops_status check_plan(loops_plan_t p) {
-  if (!p || p->magic != kPlanMagic) {
+  if (!p || !plan_live(p) || p->magic != kPlanMagic) {
     set_error("invalid or destroyed plan handle");
     return LOOPS_ERR_STATE;
   }
@@ -161,7 +212,7 @@ static loops_plan_s* new_plan(int64_t n_rows, int64_t n_cols, int64_t nnz, int64
 
 // Error word, side stream and fork/join events of a plan that runs SpMM calls.
 static loops_status plan_runtime(loops_plan_s* p) {
-  cudaError_t e = cudaMalloc((void**)&p->d_error, sizeof(int32_t));
+  cudaError_t e = dev_malloc((void**)&p->d_error, sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMemset(p->d_error, 0, sizeof(int32_t));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
@@ -246,7 +297,7 @@ static loops_status build_sddmm(loops_plan_s* p, const loops_csr* A) {
   p->sddmm.n_items = (int64_t)it.size();
   auto up = [&](void** dst, const void* src, size_t bytes) -> loops_status {
     if (!bytes) { *dst = nullptr; return LOOPS_OK; }
-    cudaError_t e = cudaMalloc(dst, bytes);
+    cudaError_t e = dev_malloc(dst, bytes);
     if (e == cudaSuccess) e = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) p->other_bytes += (int64_t)bytes;
     return cuda_status(e, "upload SDDMM pattern");
@@ -341,8 +392,8 @@ loops_status autotune_tau(const PlanBuilder& build, int64_t n_rows, int64_t n_co
   if (nnz == 0 || N == 0 || n_rows == 0) return LOOPS_OK;
   const int64_t eb = dense_elem_bytes(dtype), ec = out_elem_bytes(dtype);
   void *dB = nullptr, *dC = nullptr;
-  cudaError_t e = cudaMalloc(&dB, (size_t)std::max<int64_t>(n_cols * N * eb, 16));
-  if (e == cudaSuccess) e = cudaMalloc(&dC, (size_t)std::max<int64_t>(n_rows * N * ec, 16));
+  cudaError_t e = dev_malloc(&dB, (size_t)std::max<int64_t>(n_cols * N * eb, 16));
+  if (e == cudaSuccess) e = dev_malloc(&dC, (size_t)std::max<int64_t>(n_rows * N * ec, 16));
   if (e == cudaSuccess) e = fill_finite(dB, n_cols * N * eb, s);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
@@ -394,8 +445,8 @@ loops_status model_boundary(const PlanBuilder& build, int64_t n_rows, int64_t n_
   if (nnz == 0 || N == 0 || n_rows == 0) return LOOPS_OK;
   const int64_t eb = dense_elem_bytes(dtype), ec = out_elem_bytes(dtype);
   void *dB = nullptr, *dC = nullptr;
-  cudaError_t e = cudaMalloc(&dB, (size_t)std::max<int64_t>(n_cols * N * eb, 16));
-  if (e == cudaSuccess) e = cudaMalloc(&dC, (size_t)std::max<int64_t>(n_rows * N * ec, 16));
+  cudaError_t e = dev_malloc(&dB, (size_t)std::max<int64_t>(n_cols * N * eb, 16));
+  if (e == cudaSuccess) e = dev_malloc(&dC, (size_t)std::max<int64_t>(n_rows * N * ec, 16));
   if (e == cudaSuccess) e = fill_finite(dB, n_cols * N * eb, s);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
@@ -566,6 +617,7 @@ loops_status loops_plan(const loops_csr* A, int64_t N, loops_dtype dtype, const 
     if ((st = upload_value_maps(pt, &p->t_perm))) { destroy_plan(p); return st; }
     p->has_vmap = pt->has_vmap = true;
   }
+  register_plan(p);
   *out = p;
   return LOOPS_OK;
 }
@@ -641,8 +693,15 @@ loops_status loops_plan_device(const loops_csr* A, int64_t N, loops_dtype dtype,
   }
   cudaError_t e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) { destroy_plan(p); return cuda_status(e, "device plan build"); }
+  register_plan(p);
   *out = p;
   return LOOPS_OK;
+}
+
+int64_t loops_test_fail_alloc(int64_t n) {
+  const int64_t seen = g_alloc_seen.exchange(0);
+  g_alloc_countdown.store(n > 0 ? n : 0);
+  return seen;
 }
 
 loops_status loops_plan_destroy(loops_plan_t plan) {
@@ -650,6 +709,7 @@ loops_status loops_plan_destroy(loops_plan_t plan) {
   if (!plan) return LOOPS_OK;
   loops_status st = check_plan(plan);
   if (st) return st;
+  unregister_plan(plan);
   cudaDeviceSynchronize();
   destroy_plan(plan);
   return LOOPS_OK;
@@ -715,7 +775,7 @@ loops_status loops_plan_update_values(loops_plan_t p, const void* vals, loops_dt
     const size_t bytes = (size_t)p->nnz * (vd == LOOPS_F64 ? 8 : 4);
     void* dv = nullptr;
     cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = bytes ? cudaMalloc(&dv, bytes) : cudaSuccess;
+    cudaError_t e = bytes ? dev_malloc(&dv, bytes) : cudaSuccess;
     if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(dv, vals, bytes, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = launch_set_values(p, dv, vd, s);
     if (e == cudaSuccess && p->transposed) e = launch_set_values(p->transposed, dv, vd, s);
@@ -800,7 +860,7 @@ loops_status loops_spmm_host(loops_plan_t p, const void* B_host, int64_t ldb, vo
     if (p->stage_B) cudaFree(p->stage_B);
     p->stage_B = nullptr;
     p->stage_B_bytes = 0;
-    e = cudaMalloc(&p->stage_B, (size_t)need_B);
+    e = dev_malloc(&p->stage_B, (size_t)need_B);
     if (e != cudaSuccess) return cuda_status(e, "staging allocation");
     p->stage_B_bytes = need_B;
   }
@@ -808,7 +868,7 @@ loops_status loops_spmm_host(loops_plan_t p, const void* B_host, int64_t ldb, vo
     if (p->stage_C) cudaFree(p->stage_C);
     p->stage_C = nullptr;
     p->stage_C_bytes = 0;
-    e = cudaMalloc(&p->stage_C, (size_t)need_C);
+    e = dev_malloc(&p->stage_C, (size_t)need_C);
     if (e != cudaSuccess) return cuda_status(e, "staging allocation");
     p->stage_C_bytes = need_C;
   }
@@ -848,8 +908,8 @@ loops_status loops_spmm_host_async(loops_plan_t p, const void* B_host, int64_t l
       e = cudaEventCreateWithFlags(&h->in_done[i], cudaEventDisableTiming);
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->compute_done[i], cudaEventDisableTiming);
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->out_done[i], cudaEventDisableTiming);
-      if (e == cudaSuccess) e = cudaMalloc(&h->B[i], (size_t)std::max<int64_t>(need_B, 16));
-      if (e == cudaSuccess) e = cudaMalloc(&h->C[i], (size_t)std::max<int64_t>(need_C, 16));
+      if (e == cudaSuccess) e = dev_malloc(&h->B[i], (size_t)std::max<int64_t>(need_B, 16));
+      if (e == cudaSuccess) e = dev_malloc(&h->C[i], (size_t)std::max<int64_t>(need_C, 16));
     }
     if (e != cudaSuccess) { destroy_pipe(h); return cuda_status(e, "host pipeline setup"); }
     h->B_bytes = need_B;

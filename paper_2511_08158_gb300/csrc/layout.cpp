@@ -24,7 +24,7 @@ template <typename T>
 loops_status dev_upload(T** dst, const T* src, size_t n, int64_t& bytes) {
   *dst = nullptr;
   if (n == 0) return LOOPS_OK;
-  cudaError_t e = cudaMalloc((void**)dst, n * sizeof(T));
+  cudaError_t e = dev_malloc((void**)dst, n * sizeof(T));
   if (e != cudaSuccess) {
     cudaGetLastError();
     *dst = nullptr;

@@ -15,6 +15,15 @@ namespace loops {
 void set_error(const std::string& msg);
 void clear_error();
 
+// Every device (and pinned host) allocation of the library goes through these, so that a test
+// can make the n-th one fail (loops_test_fail_alloc) and exercise each error path.
+cudaError_t dev_malloc_raw(void** p, size_t bytes);
+cudaError_t host_malloc_raw(void** p, size_t bytes);
+template <class T>
+cudaError_t dev_malloc(T** p, size_t bytes) { return dev_malloc_raw(reinterpret_cast<void**>(p), bytes); }
+template <class T>
+cudaError_t host_malloc(T** p, size_t bytes) { return host_malloc_raw(reinterpret_cast<void**>(p), bytes); }
+
 // A device-side wait gave up (bit set in the plan's error word).
 constexpr int32_t kErrWaitTimeout = 1;
 
@@ -285,6 +294,11 @@ struct loops_plan_s {
 namespace loops {
 
 constexpr uint64_t kPlanMagic = 0x4c4f4f5053504c4eull;  // "LOOPSPLN"
+
+// Handles given to callers are registered until loops_plan_destroy, so a destroyed or foreign
+// handle is recognised without reading the memory it points to.
+void register_plan(const loops_plan_s* p);
+void unregister_plan(const loops_plan_s* p);
 
 // Device upload of a canonical partition (partition.cpp). Sets plan->dev.
 loops_status upload_part(loops_plan_s* plan, int64_t N);

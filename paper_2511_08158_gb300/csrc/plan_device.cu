@@ -56,7 +56,7 @@ struct Arena {
   T* get(int64_t n) {
     if (err != cudaSuccess) return nullptr;
     void* q = nullptr;
-    err = cudaMalloc(&q, (size_t)std::max<int64_t>(n, 1) * sizeof(T));
+    err = dev_malloc(&q, (size_t)std::max<int64_t>(n, 1) * sizeof(T));
     if (err != cudaSuccess) { cudaGetLastError(); return nullptr; }
     ptrs.push_back(q);
     return (T*)q;
@@ -755,7 +755,7 @@ template <class T>
 cudaError_t own(T** dst, int64_t n, int64_t& bytes) {
   *dst = nullptr;
   if (n <= 0) return cudaSuccess;
-  cudaError_t e = cudaMalloc((void**)dst, (size_t)n * sizeof(T));
+  cudaError_t e = dev_malloc((void**)dst, (size_t)n * sizeof(T));
   if (e != cudaSuccess) { cudaGetLastError(); *dst = nullptr; return e; }
   bytes += n * (int64_t)sizeof(T);
   return cudaSuccess;
@@ -921,7 +921,7 @@ loops_status validate_csr_device(const DevCsrIn& A, loops_dtype dtype, cudaStrea
   }
   ValStat h;
   ValStat* d = nullptr;
-  TRY(cudaMalloc(&d, sizeof(ValStat)));
+  TRY(dev_malloc(&d, sizeof(ValStat)));
   h.bad_row = h.bad_entry = ~0ull;
   h.max_bits = 0;
   h.rp0 = h.rpn = 0;
@@ -1247,7 +1247,7 @@ loops_status build_sddmm_device(loops_plan_s* p, const DevCsrIn& A, cudaStream_t
   TRY(to_host(&n_it, ni + n, s));
   p->sddmm.n_items = n_it;
   if (A.nnz) {
-    TRY(cudaMalloc((void**)&p->sddmm.col, (size_t)A.nnz * 4));
+    TRY(dev_malloc((void**)&p->sddmm.col, (size_t)A.nnz * 4));
     p->other_bytes += A.nnz * 4;
     TRY(cudaMemcpyAsync(p->sddmm.col, A.ci, (size_t)A.nnz * 4, cudaMemcpyDeviceToDevice, s));
   }
@@ -1263,9 +1263,9 @@ loops_status build_sddmm_device(loops_plan_s* p, const DevCsrIn& A, cudaStream_t
   sddmm_emit_k<<<grid_for(n), kThreads, 0, s>>>(A.rp, n, L, ni, n_it, k1, v1, pr, pb, pe);
   TRY(cudaGetLastError());
   TRY(radix_sort<int64_t>(&k1, &v1, &k2, &v2, n_it, bit_width((uint64_t)L), ar, s));
-  TRY(cudaMalloc((void**)&p->sddmm.item_row, (size_t)n_it * 4));
-  TRY(cudaMalloc((void**)&p->sddmm.item_beg, (size_t)n_it * 8));
-  TRY(cudaMalloc((void**)&p->sddmm.item_end, (size_t)n_it * 8));
+  TRY(dev_malloc((void**)&p->sddmm.item_row, (size_t)n_it * 4));
+  TRY(dev_malloc((void**)&p->sddmm.item_beg, (size_t)n_it * 8));
+  TRY(dev_malloc((void**)&p->sddmm.item_end, (size_t)n_it * 8));
   p->other_bytes += n_it * 20;
   sddmm_gather_k<<<grid_for(n_it), kThreads, 0, s>>>(v1, n_it, pr, pb, pe, p->sddmm.item_row, p->sddmm.item_beg,
                                                      p->sddmm.item_end);
@@ -1286,9 +1286,9 @@ loops_status transpose_device(const DevCsrIn& A, int64_t** t_rp, int32_t** t_ci,
   *t_ci = nullptr;
   *t_vals = nullptr;
   *perm = nullptr;
-  TRY(cudaMalloc((void**)t_rp, (size_t)(m + 1) * 8));
-  TRY(cudaMalloc((void**)t_ci, (size_t)std::max<int64_t>(nnz, 1) * 4));
-  TRY(cudaMalloc((void**)t_vals, (size_t)std::max<int64_t>(nnz, 1) * 8));
+  TRY(dev_malloc((void**)t_rp, (size_t)(m + 1) * 8));
+  TRY(dev_malloc((void**)t_ci, (size_t)std::max<int64_t>(nnz, 1) * 4));
+  TRY(dev_malloc((void**)t_vals, (size_t)std::max<int64_t>(nnz, 1) * 8));
   int64_t* cnt = ar.get<int64_t>(m + 1);
   int32_t* erow = ar.get<int32_t>(nnz);
   uint64_t* k1 = ar.get<uint64_t>(nnz);
@@ -1305,7 +1305,7 @@ loops_status transpose_device(const DevCsrIn& A, int64_t** t_rp, int32_t** t_ci,
     TRY(radix_sort<int64_t>(&k1, &v1, &k2, &v2, nnz, bit_width(m > 1 ? (uint64_t)(m - 1) : 1), ar, s));
   }
   TRY(excl_scan<int64_t>(cnt, *t_rp, m, true, ar, s));
-  TRY(cudaMalloc((void**)perm, (size_t)std::max<int64_t>(nnz, 1) * 8));
+  TRY(dev_malloc((void**)perm, (size_t)std::max<int64_t>(nnz, 1) * 8));
   if (nnz) {
     TRY(cudaMemcpyAsync(*perm, v1, (size_t)nnz * 8, cudaMemcpyDeviceToDevice, s));
     transpose_fill_k<<<grid_for(nnz), kThreads, 0, s>>>(v1, erow, A.vals, A.vals_f32, nnz, *t_ci, *t_vals);
