@@ -52,6 +52,14 @@ cudaError_t dev_malloc_raw(void** p, size_t bytes) {
   return cudaMalloc(p, bytes);
 }
 
+cudaError_t dev_malloc_async_raw(void** p, size_t bytes, cudaStream_t s) {
+  if (alloc_should_fail()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMallocAsync(p, bytes, s);
+}
+
 cudaError_t host_malloc_raw(void** p, size_t bytes) {
   if (alloc_should_fail()) {
     *p = nullptr;

@@ -18,7 +18,12 @@ void clear_error();
 // Every device (and pinned host) allocation of the library goes through these, so that a test
 // can make the n-th one fail (loops_test_fail_alloc) and exercise each error path.
 cudaError_t dev_malloc_raw(void** p, size_t bytes);
+cudaError_t dev_malloc_async_raw(void** p, size_t bytes, cudaStream_t s);  // stream-ordered (pool)
 cudaError_t host_malloc_raw(void** p, size_t bytes);
+template <class T>
+cudaError_t dev_malloc_async(T** p, size_t bytes, cudaStream_t s) {
+  return dev_malloc_async_raw(reinterpret_cast<void**>(p), bytes, s);
+}
 template <class T>
 cudaError_t dev_malloc(T** p, size_t bytes) { return dev_malloc_raw(reinterpret_cast<void**>(p), bytes); }
 template <class T>

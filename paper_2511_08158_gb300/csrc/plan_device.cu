@@ -46,8 +46,9 @@ __device__ int g_build_err;
   }
 
 // ------------------------------------------------------------------ temporaries
-// Device allocations that live for one build; released (after the stream is drained) when the
-// arena goes out of scope.
+// Device allocations that live for one build: stream-ordered (the device's memory pool, no
+// device-wide synchronisation per allocation), released on the build's stream when the arena
+// goes out of scope.
 struct Arena {
   std::vector<void*> ptrs;
   cudaStream_t s = nullptr;
@@ -56,14 +57,13 @@ struct Arena {
   T* get(int64_t n) {
     if (err != cudaSuccess) return nullptr;
     void* q = nullptr;
-    err = dev_malloc(&q, (size_t)std::max<int64_t>(n, 1) * sizeof(T));
+    err = dev_malloc_async(&q, (size_t)std::max<int64_t>(n, 1) * sizeof(T), s);
     if (err != cudaSuccess) { cudaGetLastError(); return nullptr; }
     ptrs.push_back(q);
     return (T*)q;
   }
   ~Arena() {
-    if (s) cudaStreamSynchronize(s);
-    for (void* q : ptrs) cudaFree(q);
+    for (void* q : ptrs) cudaFreeAsync(q, s);
   }
 };
 
@@ -921,7 +921,7 @@ loops_status validate_csr_device(const DevCsrIn& A, loops_dtype dtype, cudaStrea
   }
   ValStat h;
   ValStat* d = nullptr;
-  TRY(dev_malloc(&d, sizeof(ValStat)));
+  TRY(dev_malloc_async(&d, sizeof(ValStat), s));
   h.bad_row = h.bad_entry = ~0ull;
   h.max_bits = 0;
   h.rp0 = h.rpn = 0;
@@ -932,8 +932,8 @@ loops_status validate_csr_device(const DevCsrIn& A, loops_dtype dtype, cudaStrea
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(d, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  cudaFree(d);
   TRY(e);
   // reported in the order the host validation checks them
   if (h.rp0 != 0) { set_error("row_ptr[0] != 0"); return LOOPS_ERR_INVALID_CSR; }

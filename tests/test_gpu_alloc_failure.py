@@ -33,9 +33,12 @@ def _matrix():
     A, _ = W.laplacian_blocks(grid=24, n_blocks=10, block=8, seed=3, N=8)
     n = A.n_rows
     rng = np.random.default_rng(4)
-    r = np.concatenate([A.row_ids(), np.full(900, 5), np.repeat(np.arange(32, 48), 300)])
-    c = np.concatenate([A.col_idx.astype(np.int64), rng.integers(0, n, 900), rng.integers(0, n, 16 * 300)])
-    v = np.concatenate([A.vals, rng.standard_normal(900 + 16 * 300)])
+    # row 5: 300 distinct extra columns (its row block stays sparse, d < 2, and the row is longer
+    # than the split length 128); rows 32-47: 300 entries each over 576 columns (dense, > 256 tiles)
+    r = np.concatenate([A.row_ids(), np.full(300, 5), np.repeat(np.arange(32, 48), 300)])
+    c = np.concatenate([A.col_idx.astype(np.int64), rng.choice(n, 300, replace=False),
+                        rng.integers(0, n, 16 * 300)])
+    v = np.concatenate([A.vals, rng.standard_normal(300 + 16 * 300)])
     return W.csr_from_coo(n, n, r, c, v)
 
 
