@@ -247,6 +247,7 @@ static loops_status plan_batched(const loops_csr* As, const int64_t* Ns, int32_t
                                  const loops_plan_opts* opts, loops_stream_t stream, bool device,
                                  loops_plan_t* out) {
   clear_error();
+  NvtxScope nvtx(device ? "loops_plan_batched_device" : "loops_plan_batched");
   if (!out) { set_error("out is NULL"); return LOOPS_ERR_INVALID_ARG; }
   *out = nullptr;
   if (count < 0 || (count > 0 && (!As || !Ns))) { set_error("bad batch arrays"); return LOOPS_ERR_INVALID_ARG; }
@@ -426,6 +427,7 @@ loops_status loops_plan_batched_device(const loops_csr* As, const int64_t* Ns, i
 loops_status loops_spmm_batched(loops_plan_t p, const void* const* Bs, const int64_t* ldbs, void* const* Cs,
                                 const int64_t* ldcs, const float* const* col_scales, loops_stream_t stream) {
   clear_error();
+  NvtxScope nvtx("loops_spmm_batched");
   loops_status st = check_plan(p);
   if (st) return st;
   if (!p->batch) { set_error("not a batched plan"); return LOOPS_ERR_STATE; }

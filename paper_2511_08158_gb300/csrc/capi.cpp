@@ -3,6 +3,8 @@
 #include <atomic>
 #include <mutex>
 #include <unordered_set>
+
+#include <nvtx3/nvToolsExt.h>
 #include <functional>
 #include <cmath>
 #include <cstdlib>
@@ -31,11 +33,37 @@ loops_status cuda_status(cudaError_t e, const char* what) {
   return e == cudaErrorMemoryAllocation ? LOOPS_ERR_OOM : LOOPS_ERR_CUDA;
 }
 
+// ------------------------------------------------------------------ NVTX
+static nvtxDomainHandle_t nvtx_domain() {
+  static nvtxDomainHandle_t d = nvtxDomainCreateA("loops");
+  return d;
+}
+
+NvtxScope::NvtxScope(const char* name) {
+  nvtxEventAttributes_t a = {};
+  a.version = NVTX_VERSION;
+  a.size = NVTX_EVENT_ATTRIB_STRUCT_SIZE;
+  a.messageType = NVTX_MESSAGE_TYPE_ASCII;
+  a.message.ascii = name;
+  nvtxDomainRangePushEx(nvtx_domain(), &a);
+}
+
+NvtxScope::~NvtxScope() { nvtxDomainRangePop(nvtx_domain()); }
+
 // ------------------------------------------------------------------ allocation hook
 static std::atomic<int64_t> g_alloc_countdown{0};  // > 0: this many allocations from now, the last fails
 static std::atomic<int64_t> g_alloc_seen{0};       // allocations since the last loops_test_fail_alloc
 
 static bool alloc_should_fail() {
+  // LOOPS_FAULT_ALLOC=k in the environment arms the hook once, for the k-th allocation of the
+  // process (the same hook as loops_test_fail_alloc)
+  static std::once_flag env_once;
+  std::call_once(env_once, [] {
+    if (const char* v = std::getenv("LOOPS_FAULT_ALLOC")) {
+      const long long k = std::atoll(v);
+      if (k > 0) g_alloc_countdown.store(k);
+    }
+  });
   g_alloc_seen.fetch_add(1, std::memory_order_relaxed);
   int64_t c = g_alloc_countdown.load();
   while (c > 0) {
@@ -559,6 +587,7 @@ void loops_partition_free(loops_partition* part) {
 loops_status loops_plan(const loops_csr* A, int64_t N, loops_dtype dtype, const loops_plan_opts* opts,
                         loops_stream_t stream, loops_plan_t* out) {
   clear_error();
+  NvtxScope nvtx("loops_plan");
   if (!out) { set_error("out is NULL"); return LOOPS_ERR_INVALID_ARG; }
   *out = nullptr;
   if (!valid_dtype(dtype)) { set_error("bad dtype"); return LOOPS_ERR_INVALID_ARG; }
@@ -633,6 +662,7 @@ loops_status loops_plan(const loops_csr* A, int64_t N, loops_dtype dtype, const 
 loops_status loops_plan_device(const loops_csr* A, int64_t N, loops_dtype dtype, const loops_plan_opts* opts,
                                loops_stream_t stream, loops_plan_t* out) {
   clear_error();
+  NvtxScope nvtx("loops_plan_device");
   if (!out) { set_error("out is NULL"); return LOOPS_ERR_INVALID_ARG; }
   *out = nullptr;
   if (!A) { set_error("A is NULL"); return LOOPS_ERR_INVALID_ARG; }
@@ -842,6 +872,7 @@ loops_status loops_spmm(loops_plan_t p, const void* B, int64_t ldb, void* C, int
 loops_status loops_spmm_scaled(loops_plan_t p, const void* B, int64_t ldb, const float* col_scale,
                                void* C, int64_t ldc, loops_stream_t stream) {
   clear_error();
+  NvtxScope nvtx("loops_spmm");
   loops_status st = check_single(p);
   if (st) return st;
   if ((st = check_dense(B, p->n_cols, p->N, ldb, "B"))) return st;
@@ -856,6 +887,7 @@ loops_status loops_spmm_scaled(loops_plan_t p, const void* B, int64_t ldb, const
 loops_status loops_spmm_host(loops_plan_t p, const void* B_host, int64_t ldb, void* C_host, int64_t ldc,
                              loops_stream_t stream) {
   clear_error();
+  NvtxScope nvtx("loops_spmm_host");
   loops_status st = check_single(p);
   if (st) return st;
   if ((st = check_dense(B_host, p->n_cols, p->N, ldb, "B"))) return st;
@@ -899,6 +931,7 @@ loops_status loops_spmm_host(loops_plan_t p, const void* B_host, int64_t ldb, vo
 loops_status loops_spmm_host_async(loops_plan_t p, const void* B_host, int64_t ldb, void* C_host, int64_t ldc,
                                    loops_stream_t stream) {
   clear_error();
+  NvtxScope nvtx("loops_spmm_host_async");
   loops_status st = check_single(p);
   if (st) return st;
   if ((st = check_dense(B_host, p->n_cols, p->N, ldb, "B"))) return st;
@@ -971,6 +1004,7 @@ loops_status loops_spmm_host_flush(loops_plan_t p, loops_stream_t stream) {
 loops_status loops_spmm_backward(loops_plan_t p, const void* dC, int64_t lddc, const void* B, int64_t ldb,
                                  void* dB, int64_t lddb, void* dvals, loops_stream_t stream) {
   clear_error();
+  NvtxScope nvtx("loops_spmm_backward");
   loops_status st = check_single(p);
   if (st) return st;
   if (!p->transposed) {

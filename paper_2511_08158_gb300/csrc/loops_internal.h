@@ -29,6 +29,17 @@ cudaError_t dev_malloc(T** p, size_t bytes) { return dev_malloc_raw(reinterpret_
 template <class T>
 cudaError_t host_malloc(T** p, size_t bytes) { return host_malloc_raw(reinterpret_cast<void**>(p), bytes); }
 
+// NVTX range in the library's own domain ("loops") for the duration of a scope: plan builds
+// and SpMM calls show up in a profiler timeline without touching the caller's default-domain
+// ranges. Costs a few nanoseconds when no tool is attached.
+class NvtxScope {
+ public:
+  explicit NvtxScope(const char* name);
+  ~NvtxScope();
+  NvtxScope(const NvtxScope&) = delete;
+  NvtxScope& operator=(const NvtxScope&) = delete;
+};
+
 // A device-side wait gave up (bit set in the plan's error word).
 constexpr int32_t kErrWaitTimeout = 1;
 

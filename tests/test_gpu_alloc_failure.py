@@ -139,3 +139,27 @@ def test_destroyed_handle_is_refused(lp):
     assert L.loops_plan_destroy(h) == STATE
     assert L.loops_spmm(h, None, 8, None, 8, None) == STATE
     assert b"destroyed" in L.loops_last_error()
+
+
+def test_fault_alloc_environment_variable(lp):
+    # LOOPS_FAULT_ALLOC=k arms the same hook at start-up: the process's first allocation fails
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = (
+        "import sys; sys.path.insert(0, %r)\n"
+        "import paper_2511_08158_gb300 as lp, workloads as W\n"
+        "A = W.random_csr(50, 50, 0.1, 1)\n"
+        "try:\n"
+        "    lp.Plan(A, 8, 'f64', tau=2.0)\n"
+        "    print('built')\n"
+        "except lp.LoopsError as e:\n"
+        "    print('status', e.status)\n"
+        "lp.Plan(A, 8, 'f64', tau=2.0)\n"
+        "print('second ok')\n" % root)
+    env = dict(os.environ, LOOPS_FAULT_ALLOC="1")
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stderr
+    assert "status 4" in out.stdout and "second ok" in out.stdout, out.stdout
