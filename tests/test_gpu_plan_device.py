@@ -273,3 +273,44 @@ def test_batched_device_build_names_the_invalid_matrix(lp):
     with pytest.raises(lp.LoopsError) as ei:
         lp.BatchedPlan(As, [N for _, N in mats], "f32", tau=2.0, build_on_device=True)
     assert "matrix 1" in str(ei.value) and "column index out of range at entry 3" in str(ei.value)
+
+
+def _random_case(seed):
+    """A seeded random matrix and plan options: uneven shapes, clustered rows (dense column
+    runs, so that some row blocks pass every threshold), long rows, empty row blocks,
+    duplicates, unsorted columns and explicit zeros."""
+    rng = np.random.default_rng(1000 + seed)
+    n_rows, n_cols = int(rng.integers(1, 2500)), int(rng.integers(1, 2500))
+    A = W.random_csr(n_rows, n_cols, float(rng.choice([0.0005, 0.004, 0.02])), seed,
+                     duplicates=bool(rng.integers(0, 2)), unsorted=bool(rng.integers(0, 2)),
+                     explicit_zeros=bool(rng.integers(0, 2)))
+    r, c, v = [A.row_ids()], [A.col_idx.astype(np.int64)], [A.vals]
+    for _ in range(int(rng.integers(0, 4))):  # dense patches and a long row
+        r0, c0 = int(rng.integers(0, n_rows)), int(rng.integers(0, n_cols))
+        h, w = int(rng.integers(1, 40)), int(rng.integers(1, 300))
+        rr, cc = np.meshgrid(np.arange(r0, min(r0 + h, n_rows)), np.arange(c0, min(c0 + w, n_cols)), indexing="ij")
+        r.append(rr.ravel()); c.append(cc.ravel()); v.append(rng.standard_normal(rr.size))
+    A = W.csr_from_coo(n_rows, n_cols, np.concatenate(r), np.concatenate(c), np.concatenate(v),
+                       sort_cols=bool(rng.integers(0, 2)))
+    fmt = str(rng.choice(FMTS))
+    opts = {"tau": float(rng.choice([0.0, 0.5, 1.0, 1.25, 2.0, 3.0, math.inf])),
+            "split_len": int(rng.choice([0, 16, 64])),
+            "tile_min": int(rng.choice([0, 0, 2, 3]))}
+    if rng.integers(0, 5) == 0:
+        opts = {"contiguous_split": True, "r_boundary": int(rng.integers(0, n_rows + 1)),
+                "split_len": opts["split_len"]}
+    return A, fmt, opts
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_device_build_random_cases_equal_host_build(lp, seed):
+    A, fmt, opts = _random_case(seed)
+    N = 8 if fmt in ("f16", "bf16") else 4
+    ph = lp.Plan(A, N, fmt, **opts)
+    pd = lp.Plan(A, N, fmt, build_on_device=True, **opts)
+    _same_partition(ph.export(), pd.export())
+    _same_counts(ph, pd)
+    if A.nnz:
+        Ch, Cd, ref = _spmm_both(lp, ph, pd, A, fmt, N, seed=seed)
+        assert np.array_equal(Ch, Cd)
+        assert rel_l2(Cd, ref) <= TOL[fmt]
