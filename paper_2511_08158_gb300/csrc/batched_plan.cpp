@@ -334,7 +334,6 @@ static loops_status plan_batched(const loops_csr* As, const int64_t* Ns, int32_t
       ld[(size_t)m] = Ns[m];
     }
     st = cuda_status(e, "autotune buffers");
-    double best_tau = 2.0;
     for (const Cand& c : cands) {
       if (st) break;
       loops_plan_opts oc = o;
@@ -355,7 +354,6 @@ static loops_status plan_batched(const loops_csr* As, const int64_t* Ns, int32_t
       }
       if (!st && ms < best_ms) {
         best_ms = ms;
-        best_tau = c.tau;
         if (best) destroy_batch(best);
         best = b;
         br = c.br;
@@ -369,7 +367,6 @@ static loops_status plan_batched(const loops_csr* As, const int64_t* Ns, int32_t
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st) { if (best) destroy_batch(best); return st; }
-    (void)best_tau;
     // a plan built during tuning has captured dummy pointers: drop its graph state so the
     // first real call uploads the caller's descriptors
     best->copied_once = false;

@@ -128,7 +128,8 @@ loops_status upload_part(loops_plan_s* p, int64_t N) {
       }
     }
     cd.h_split_slot_ptr.push_back((int32_t)n_slots);
-    std::stable_sort(items.begin(), items.end(), [](const It& a, const It& b) { return a.bucket > b.bucket; });
+    if (LOOPS_CSR_ITEMS_BY_LENGTH)
+      std::stable_sort(items.begin(), items.end(), [](const It& a, const It& b) { return a.bucket > b.bucket; });
     cd.n_items = (int64_t)items.size();
     cd.n_split = (int64_t)cd.h_split_row.size();
     cd.n_slots = n_slots;

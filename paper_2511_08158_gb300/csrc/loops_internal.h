@@ -154,6 +154,12 @@ struct CsrDev {
 // kBcsrSplitTiles tiles is cut into several units whose partial sums (B_r x N accumulators,
 // slot unit_slot) are added in slot order by a second kernel; unit_slot -1 writes C directly.
 constexpr int64_t kBcsrSplitTiles = 256;
+
+// CSR work items: 1 = ordered by decreasing length class (longest work first, row order within
+// a class), 0 = row order. Both plan builders follow it.
+#ifndef LOOPS_CSR_ITEMS_BY_LENGTH
+#define LOOPS_CSR_ITEMS_BY_LENGTH 1
+#endif
 struct BcsrDev {
   int64_t n_rb = 0, n_tiles = 0;
   int32_t* rb_id = nullptr;

@@ -639,14 +639,14 @@ __global__ void row_emit_k(const int64_t* rp, const uint8_t* is_bcsr, const int3
         pre_row[it] = (int32_t)(-1 - slot);
         pre_beg[it] = beg + s0;
         pre_len[it] = min(L, len - s0);
-        ikey[it] = 0;  // bucket 63 first
+        ikey[it] = 0;  // bucket 63 first (or row order)
         ival[it] = it;
       }
     } else {
       pre_row[it] = (int32_t)i;
       pre_beg[it] = beg;
       pre_len[it] = len;
-      ikey[it] = (uint64_t)(63 - bucket_of_len(len));
+      ikey[it] = LOOPS_CSR_ITEMS_BY_LENGTH ? (uint64_t)(63 - bucket_of_len(len)) : 0;
       ival[it] = it;
     }
   }
