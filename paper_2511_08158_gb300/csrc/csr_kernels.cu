@@ -410,19 +410,39 @@ __global__ void __launch_bounds__(256) sddmm_vec(SddmmKArgs a) {
       for (int p = 0; p < VPL; ++p)
         bv[u][p] = (ok && colok[p]) ? ldg16(Bp + (int64_t)cj[u] * a.ldb + coff[p]) : make_uint4(0, 0, 0, 0);
     }
+    TAcc s[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      TAcc s = TAcc(0);
+      s[u] = TAcc(0);
 #pragma unroll
       for (int p = 0; p < VPL; ++p) {
         TAcc b[VE];
         unpack16<Tr>(bv[u][p], b);
 #pragma unroll
-        for (int e = 0; e < VE; ++e) s = fma(g[p][e], b[e], s);
+        for (int e = 0; e < VE; ++e) s[u] = fma(g[p][e], b[e], s[u]);
       }
+    }
+    if constexpr (G >= 4 && U == 4) {
+      // the four entries' sums over the group at once (a butterfly that halves the values a
+      // lane holds while it halves the lanes it spans): 6 shuffles instead of 4 x log2(G)
+      const bool h1 = (sub & (G / 2)) != 0, h2 = (sub & (G / 4)) != 0;
+      TAcc k0v = h1 ? s[2] : s[0], k1v = h1 ? s[3] : s[1];
+      k0v += __shfl_xor_sync(gmask, h1 ? s[0] : s[2], G / 2, G);
+      k1v += __shfl_xor_sync(gmask, h1 ? s[1] : s[3], G / 2, G);
+      TAcc v = h2 ? k1v : k0v;
+      v += __shfl_xor_sync(gmask, h2 ? k0v : k1v, G / 4, G);
 #pragma unroll
-      for (int off = G / 2; off > 0; off >>= 1) s += __shfl_xor_sync(gmask, s, off, G);
-      if (sub == 0 && k0 + u < end) reinterpret_cast<TC*>(a.dvals)[k0 + u] = (TC)s;
+      for (int off = G / 8; off > 0; off >>= 1) v += __shfl_xor_sync(gmask, v, off, G);
+      const int e = (h1 ? 2 : 0) + (h2 ? 1 : 0);  // the entry this lane's sum belongs to
+      if ((sub & (G / 4 - 1)) == 0 && k0 + e < end) reinterpret_cast<TC*>(a.dvals)[k0 + e] = (TC)v;
+    } else {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        TAcc t = s[u];
+#pragma unroll
+        for (int off = G / 2; off > 0; off >>= 1) t += __shfl_xor_sync(gmask, t, off, G);
+        if (sub == 0 && k0 + u < end) reinterpret_cast<TC*>(a.dvals)[k0 + u] = (TC)t;
+      }
     }
   }
 }
