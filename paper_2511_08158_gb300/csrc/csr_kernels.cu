@@ -13,6 +13,11 @@
 #include "device_common.cuh"
 #include "loops_internal.h"
 
+// SDDMM: reduce the four in-flight entries' partial dot products with one butterfly (1) or each
+// with its own shuffle tree (0).
+#ifndef LOOPS_SDDMM_BUTTERFLY
+#define LOOPS_SDDMM_BUTTERFLY 1
+#endif
 // Tuning knobs of the memory-bound (non-FP64) CSR kernel: B-row loads kept in flight per
 // lane (per column vector), the minimum resident blocks per SM the register allocation must
 // allow, and the 16-byte column vectors each lane owns. Two vectors per lane with two
@@ -422,7 +427,7 @@ __global__ void __launch_bounds__(256) sddmm_vec(SddmmKArgs a) {
         for (int e = 0; e < VE; ++e) s[u] = fma(g[p][e], b[e], s[u]);
       }
     }
-    if constexpr (G >= 4 && U == 4) {
+    if constexpr (LOOPS_SDDMM_BUTTERFLY && G >= 4 && U == 4) {
       // the four entries' sums over the group at once (a butterfly that halves the values a
       // lane holds while it halves the lanes it spans): 6 shuffles instead of 4 x log2(G)
       const bool h1 = (sub & (G / 2)) != 0, h2 = (sub & (G / 4)) != 0;
