@@ -118,7 +118,7 @@ __device__ __forceinline__ void csr_item(const BatchDesc& d, int64_t item, int G
 // Tiles whose B loads an F32 BCSR task keeps in flight, for B_r = 8 and 16 (register-limited:
 // the whole persistent kernel shares one allocation).
 #ifndef LOOPS_BFFMA_UB8
-#define LOOPS_BFFMA_UB8 2
+#define LOOPS_BFFMA_UB8 4
 #endif
 #ifndef LOOPS_BFFMA_UB16
 #define LOOPS_BFFMA_UB16 1
