@@ -116,7 +116,7 @@ __device__ __forceinline__ void csr_item(const BatchDesc& d, int64_t item, int G
 
 // One F32 BCSR unit (B_r rows, tile-major values) for a group of G lanes.
 // Tiles whose B loads an F32 BCSR task keeps in flight, for B_r = 8 and 16 (register-limited:
-// the whole persistent kernel shares one allocation).
+// the whole persistent kernel shares one allocation); 0 walks the tiles one at a time.
 #ifndef LOOPS_BFFMA_UB8
 #define LOOPS_BFFMA_UB8 4
 #endif
@@ -140,11 +140,27 @@ __device__ __forceinline__ void ffma_block(const BatchDesc& d, int64_t u, int G,
   for (int r = 0; r < BR; ++r)
 #pragma unroll
     for (int e = 0; e < 4; ++e) acc[r][e] = 0.f;
-  for (int64_t k0 = t0; k0 < t1; k0 += G) {
+  if constexpr (UB == 0) {  // one tile at a time, each lane reading the tile column itself
+    for (int64_t tt = t0; tt < t1; ++tt) {
+      const int32_t c = __ldg(d.tile_col + tt);
+      const uint4 v = c >= 0 ? ldg16(Bp + (int64_t)c * d.ldb + n) : make_uint4(0, 0, 0, 0);
+      const float b4[4] = {__uint_as_float(v.x), __uint_as_float(v.y), __uint_as_float(v.z), __uint_as_float(v.w)};
+#pragma unroll
+      for (int r4 = 0; r4 < BR / 4; ++r4) {
+        const uint4 w = ldg16(Av + tt * BR + r4 * 4);
+        const float a4[4] = {__uint_as_float(w.x), __uint_as_float(w.y), __uint_as_float(w.z), __uint_as_float(w.w)};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) acc[r4 * 4 + i][e] = fmaf(a4[i], b4[e], acc[r4 * 4 + i][e]);
+      }
+    }
+  }
+  for (int64_t k0 = t0; k0 < t1 && UB > 0; k0 += G) {
     const int32_t cmine = k0 + sub < t1 ? __ldg(d.tile_col + k0 + sub) : -1;
     const int cnt = (int)(t1 - k0 < (int64_t)G ? t1 - k0 : (int64_t)G);  // uniform in the group
     for (int j0 = 0; j0 < cnt; j0 += UB) {
-      uint4 bv[UB];
+      uint4 bv[UB > 0 ? UB : 1];
 #pragma unroll
       for (int q = 0; q < UB; ++q) {
         const int32_t c = __shfl_sync(gmask, cmine, (j0 + q) & (G - 1), G);
