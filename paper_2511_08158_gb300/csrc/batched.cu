@@ -115,19 +115,8 @@ __device__ __forceinline__ void csr_item(const BatchDesc& d, int64_t item, int G
 }
 
 // One F32 BCSR unit (B_r rows, tile-major values) for a group of G lanes.
-// Tiles whose B loads an F32 BCSR task keeps in flight, for B_r = 8 and 16 (register-limited:
-// the whole persistent kernel shares one allocation); 0 walks the tiles one at a time.
-#ifndef LOOPS_BFFMA_UB8
-#define LOOPS_BFFMA_UB8 4
-#endif
-#ifndef LOOPS_BFFMA_UB16
-#define LOOPS_BFFMA_UB16 1
-#endif
 template <int BR>
-__device__ __forceinline__ void ffma_block(const BatchDesc& d, int64_t u, int G, int sub, unsigned gmask) {
-  // the group reads G tile columns at once and broadcasts them with shuffles; UB tiles' B loads
-  // are in flight before their FMAs
-  constexpr int UB = BR >= 16 ? LOOPS_BFFMA_UB16 : LOOPS_BFFMA_UB8;
+__device__ __forceinline__ void ffma_block(const BatchDesc& d, int64_t u, int sub) {
   const int32_t b = d.unit_block[u];
   const int64_t rb = d.rb_id[b];
   const int64_t t0 = d.unit_t0[u], t1 = d.unit_t1[u];
@@ -140,48 +129,18 @@ __device__ __forceinline__ void ffma_block(const BatchDesc& d, int64_t u, int G,
   for (int r = 0; r < BR; ++r)
 #pragma unroll
     for (int e = 0; e < 4; ++e) acc[r][e] = 0.f;
-  if constexpr (UB == 0) {  // one tile at a time, each lane reading the tile column itself
-    for (int64_t tt = t0; tt < t1; ++tt) {
-      const int32_t c = __ldg(d.tile_col + tt);
-      const uint4 v = c >= 0 ? ldg16(Bp + (int64_t)c * d.ldb + n) : make_uint4(0, 0, 0, 0);
-      const float b4[4] = {__uint_as_float(v.x), __uint_as_float(v.y), __uint_as_float(v.z), __uint_as_float(v.w)};
+  for (int64_t tt = t0; tt < t1; ++tt) {
+    const int32_t c = __ldg(d.tile_col + tt);
+    const uint4 v = c >= 0 ? ldg16(Bp + (int64_t)c * d.ldb + n) : make_uint4(0, 0, 0, 0);
+    const float bv[4] = {__uint_as_float(v.x), __uint_as_float(v.y), __uint_as_float(v.z), __uint_as_float(v.w)};
 #pragma unroll
-      for (int r4 = 0; r4 < BR / 4; ++r4) {
-        const uint4 w = ldg16(Av + tt * BR + r4 * 4);
-        const float a4[4] = {__uint_as_float(w.x), __uint_as_float(w.y), __uint_as_float(w.z), __uint_as_float(w.w)};
+    for (int r4 = 0; r4 < BR / 4; ++r4) {
+      const uint4 w = ldg16(Av + tt * BR + r4 * 4);
+      const float a4[4] = {__uint_as_float(w.x), __uint_as_float(w.y), __uint_as_float(w.z), __uint_as_float(w.w)};
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < 4; ++i)
 #pragma unroll
-          for (int e = 0; e < 4; ++e) acc[r4 * 4 + i][e] = fmaf(a4[i], b4[e], acc[r4 * 4 + i][e]);
-      }
-    }
-  }
-  for (int64_t k0 = t0; k0 < t1 && UB > 0; k0 += G) {
-    const int32_t cmine = k0 + sub < t1 ? __ldg(d.tile_col + k0 + sub) : -1;
-    const int cnt = (int)(t1 - k0 < (int64_t)G ? t1 - k0 : (int64_t)G);  // uniform in the group
-    for (int j0 = 0; j0 < cnt; j0 += UB) {
-      uint4 bv[UB > 0 ? UB : 1];
-#pragma unroll
-      for (int q = 0; q < UB; ++q) {
-        const int32_t c = __shfl_sync(gmask, cmine, (j0 + q) & (G - 1), G);
-        bv[q] = (j0 + q < cnt && c >= 0) ? ldg16(Bp + (int64_t)c * d.ldb + n) : make_uint4(0, 0, 0, 0);
-      }
-#pragma unroll
-      for (int q = 0; q < UB; ++q) {
-        if (j0 + q >= cnt) break;  // uniform in the group
-        const int64_t tt = k0 + j0 + q;
-        const float b4[4] = {__uint_as_float(bv[q].x), __uint_as_float(bv[q].y), __uint_as_float(bv[q].z),
-                             __uint_as_float(bv[q].w)};
-#pragma unroll
-        for (int r4 = 0; r4 < BR / 4; ++r4) {
-          const uint4 w = ldg16(Av + tt * BR + r4 * 4);
-          const float a4[4] = {__uint_as_float(w.x), __uint_as_float(w.y), __uint_as_float(w.z), __uint_as_float(w.w)};
-#pragma unroll
-          for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) acc[r4 * 4 + i][e] = fmaf(a4[i], b4[e], acc[r4 * 4 + i][e]);
-        }
-      }
+        for (int e = 0; e < 4; ++e) acc[r4 * 4 + i][e] = fmaf(a4[i], bv[e], acc[r4 * 4 + i][e]);
     }
   }
   if (slot >= 0) {  // unit of a split block: partial sums
@@ -313,7 +272,7 @@ __global__ void __launch_bounds__(256, LOOPS_BATCHED_MIN_BLOCKS) batched_persist
       if (task.kind == 0) {
         csr_item<Tr>(d, task.first + i, G, sub, gmask);
       } else if constexpr (std::is_same<Tr, TrF32>::value) {
-        ffma_block<BR>(d, task.first + i, G, sub, gmask);
+        ffma_block<BR>(d, task.first + i, sub);
       }
     }
   }
