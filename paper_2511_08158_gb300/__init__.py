@@ -146,7 +146,9 @@ def _check(status: int):
 
 
 def _csr_struct(A):
-    """Host CSR arrays of A (attributes n_rows, n_cols, row_ptr, col_idx, vals) -> (_Csr, keepalive)."""
+    """Host CSR arrays of A (attributes n_rows, n_cols, row_ptr, col_idx, vals) -> (_Csr, keepalive).
+    nnz is the length of col_idx, so the library's validation (row_ptr[n_rows] == nnz) catches
+    arrays shorter than row_ptr claims instead of reading past them."""
     rp = np.ascontiguousarray(A.row_ptr, dtype=np.int64)
     ci = np.ascontiguousarray(A.col_idx, dtype=np.int32)
     v = np.ascontiguousarray(A.vals)
@@ -155,8 +157,11 @@ def _csr_struct(A):
     else:
         v = np.ascontiguousarray(v, dtype=np.float64)
         vd = F64
-    s = _Csr(int(A.n_rows), int(A.n_cols), int(rp[-1]) if rp.size else 0, rp.ctypes.data, ci.ctypes.data,
-             v.ctypes.data, vd)
+    if rp.size != int(A.n_rows) + 1:
+        raise ValueError("row_ptr must have n_rows + 1 entries")
+    if v.size != ci.size:
+        raise ValueError("vals and col_idx must have the same length")
+    s = _Csr(int(A.n_rows), int(A.n_cols), int(ci.size), rp.ctypes.data, ci.ctypes.data, v.ctypes.data, vd)
     return s, (rp, ci, v)
 
 
@@ -174,6 +179,10 @@ def _csr_struct_device(A):
     v0 = A.vals
     f32 = (v0.dtype == torch.float32) if isinstance(v0, torch.Tensor) else (np.asarray(v0).dtype == np.float32)
     v = dev(v0, torch.float32 if f32 else torch.float64)
+    if rp.numel() != int(A.n_rows) + 1:
+        raise ValueError("row_ptr must have n_rows + 1 entries")
+    if v.numel() != ci.numel():
+        raise ValueError("vals and col_idx must have the same length")
     s = _Csr(int(A.n_rows), int(A.n_cols), int(ci.numel()), rp.data_ptr(), ci.data_ptr(), v.data_ptr(),
              F32 if f32 else F64)
     return s, (rp, ci, v)
@@ -259,8 +268,8 @@ class Plan:
             self.nnz = int(cs.nnz)
             _check(L.loops_plan_device(ctypes.byref(cs), self.N, self.dtype, ctypes.byref(o), s, ctypes.byref(h)))
         else:
-            self.nnz = int(np.asarray(A.row_ptr)[-1]) if len(A.row_ptr) else 0
             cs, keep = _csr_struct(A)
+            self.nnz = int(cs.nnz)
             _check(L.loops_plan(ctypes.byref(cs), self.N, self.dtype, ctypes.byref(o), s, ctypes.byref(h)))
         self._h = h
 

@@ -170,3 +170,17 @@ def test_plan_device_argument_checks_need_no_gpu(loops_lib):
     f16_vals = loops_lib._Csr(cs.n_rows, cs.n_cols, cs.nnz, cs.row_ptr, cs.col_idx, cs.vals, 2)
     assert L.loops_plan_device(ctypes.byref(f16_vals), 8, 0, ctypes.byref(o), None, ctypes.byref(h)) == 3
     assert h.value is None
+
+
+def test_binding_rejects_inconsistent_arrays_before_reading_them(loops_lib):
+    A = W.random_csr(30, 30, 0.2, 3)
+    # row_ptr claims more entries than col_idx holds: the library's validation rejects it
+    rp = A.row_ptr.copy()
+    rp[-1] += 5
+    with pytest.raises(loops_lib.LoopsError) as ei:
+        loops_lib.Plan(W.CSR(30, 30, rp, A.col_idx, A.vals), 8, "f64", tau=2.0)
+    assert ei.value.status == 2 and "row_ptr[n_rows] != nnz" in str(ei.value)
+    with pytest.raises(ValueError):
+        loops_lib.Plan(W.CSR(30, 30, A.row_ptr, A.col_idx, A.vals[:-1]), 8, "f64", tau=2.0)
+    with pytest.raises(ValueError):
+        loops_lib.Plan(W.CSR(31, 30, A.row_ptr, A.col_idx, A.vals), 8, "f64", tau=2.0)
