@@ -236,7 +236,9 @@ loops_status loops_spmm_scaled(loops_plan_t plan, const void* B, int64_t ldb,
 
 /* End-to-end SpMM with HOST buffers: copies B (host, ideally pinned) to plan-owned device
  * memory, runs loops_spmm, copies C back to host, and synchronises `stream` before
- * returning. The staging buffers are allocated on the first call and kept by the plan. */
+ * returning. The staging buffers are allocated on the first call and kept by the plan. (The
+ * paper's method runs on CPU cores, Sec. 3, where the operands need no transfer; this call
+ * has no counterpart there.) */
 loops_status loops_spmm_host(loops_plan_t plan, const void* B_host, int64_t ldb, void* C_host,
                              int64_t ldc, loops_stream_t stream);
 
@@ -251,7 +253,7 @@ loops_status loops_spmm_host_async(loops_plan_t plan, const void* B_host, int64_
                                    int64_t ldc, loops_stream_t stream);
 
 /* Make `stream` wait for the copy-out of the last loops_spmm_host_async call on this plan
- * (stream-ordered, no host wait). */
+ * (stream-ordered, no host wait). No counterpart in the paper, as for loops_spmm_host. */
 loops_status loops_spmm_host_flush(loops_plan_t plan, loops_stream_t stream);
 
 /* Backward of C = A . B for a plan built with want_backward:
