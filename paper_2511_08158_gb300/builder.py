@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libloops.so")
 INCLUDE = os.path.join(ROOT, "include")
 
-SOURCES = ["capi.cpp", "partition.cpp", "layout.cpp", "csr_kernels.cu", "bcsr_kernels.cu", "csr_noalloc.cu",
+SOURCES = ["capi.cpp", "partition.cpp", "layout.cpp", "csr_kernels.cu", "sddmm_kernels.cu", "bcsr_kernels.cu", "csr_noalloc.cu",
            "batched.cu", "batched_plan.cpp", "plan_device.cu"]
 HEADERS = [os.path.join(CSRC, "loops_internal.h"), os.path.join(CSRC, "device_common.cuh"),
            os.path.join(INCLUDE, "loops.h")]
