@@ -159,11 +159,6 @@ __device__ __forceinline__ void ffma_block(const BatchDesc& d, int64_t u, int su
   }
 }
 
-// F16/BF16 BCSR tasks: load the next K-group's B-row pieces while the current one computes (1).
-#ifndef LOOPS_BHMMA_PREFETCH
-#define LOOPS_BHMMA_PREFETCH 1
-#endif
-
 // One F16/BF16 BCSR unit for the whole warp, in column chunks of up to 64: sB is the warp's
 // shared-memory slice holding the 16 gathered B-row pieces of the current K-group and chunk
 // (row stride 72 elements, conflict-free for ldmatrix).
@@ -191,40 +186,15 @@ __device__ __forceinline__ void hmma_block(const BatchDesc& d, int64_t u, T* sB,
     for (int f = 0; f < 8; ++f)
 #pragma unroll
       for (int i = 0; i < 4; ++i) acc[f][i] = 0.f;
-    // a lane's share of a K-group's B-row pieces: i = lane + 32 j, j < 4 (16 rows x at most 8
-    // vectors); the next group's pieces are loaded into registers while this group computes
-    uint4 pv[4];
-    auto load_group = [&](int g) {
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int i = lane + 32 * j;
-        if (i < 16 * vec_per_row) {
-          const int k = i / vec_per_row, qv = i % vec_per_row;
-          const int32_t c = __ldg(d.tile_col + t0 + g * 16 + k);
-          pv[j] = c >= 0 ? ldg16(Bp + (int64_t)c * d.ldb + c0 + qv * 8) : make_uint4(0, 0, 0, 0);
-        }
-      }
-    };
-    if (LOOPS_BHMMA_PREFETCH && n_groups > 0) load_group(0);
     for (int g = 0; g < n_groups; ++g) {
       __syncwarp();
-      if constexpr (LOOPS_BHMMA_PREFETCH) {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int i = lane + 32 * j;
-          if (i < 16 * vec_per_row)
-            *reinterpret_cast<uint4*>(sB + (i / vec_per_row) * kHStride + (i % vec_per_row) * 8) = pv[j];
-        }
-      } else {
-        for (int i = lane; i < 16 * vec_per_row; i += 32) {
-          const int k = i / vec_per_row, qv = i % vec_per_row;
-          const int32_t c = __ldg(d.tile_col + t0 + g * 16 + k);
-          const uint4 v = c >= 0 ? ldg16(Bp + (int64_t)c * d.ldb + c0 + qv * 8) : make_uint4(0, 0, 0, 0);
-          *reinterpret_cast<uint4*>(sB + k * kHStride + qv * 8) = v;
-        }
+      for (int i = lane; i < 16 * vec_per_row; i += 32) {
+        const int k = i / vec_per_row, qv = i % vec_per_row;
+        const int32_t c = __ldg(d.tile_col + t0 + g * 16 + k);
+        const uint4 v = c >= 0 ? ldg16(Bp + (int64_t)c * d.ldb + c0 + qv * 8) : make_uint4(0, 0, 0, 0);
+        *reinterpret_cast<uint4*>(sB + k * kHStride + qv * 8) = v;
       }
       __syncwarp();
-      if (LOOPS_BHMMA_PREFETCH && g + 1 < n_groups) load_group(g + 1);
       const uint4 af = __ldg(Af + (int64_t)g * 32 + lane);
       const int mi = lane >> 3, r = lane & 7;
 #pragma unroll
