@@ -53,8 +53,12 @@ def csr_from_coo(n_rows: int, n_cols: int, rows: np.ndarray, cols: np.ndarray,
     rows = np.asarray(rows, dtype=np.int64)
     cols = np.asarray(cols, dtype=np.int64)
     vals = np.asarray(vals, dtype=np.float64)
-    order = np.lexsort((cols, rows)) if sort_cols else np.argsort(rows, kind="stable")
-    rows, cols, vals = rows[order], cols[order], vals[order]
+    # one stable sort of the combined key gives the (row, column) order of a two-key lexsort;
+    # inputs already in that order (banded patterns) are taken as they are
+    key = rows * max(int(n_cols), 1) + cols if sort_cols else rows
+    if key.size > 1 and not np.all(key[1:] >= key[:-1]):
+        order = np.argsort(key, kind="stable")
+        rows, cols, vals = rows[order], cols[order], vals[order]
     counts = np.bincount(rows, minlength=n_rows)
     row_ptr = np.zeros(n_rows + 1, dtype=np.int64)
     np.cumsum(counts, out=row_ptr[1:])
@@ -71,10 +75,11 @@ def _distinct_cols_per_row(rng: np.random.Generator, counts: np.ndarray, n_cols:
     rows = np.repeat(np.arange(counts.size, dtype=np.int64), counts)
     cols = rng.integers(0, n_cols, size=rows.size, dtype=np.int64)
     while True:
-        order = np.lexsort((cols, rows))
-        r_s, c_s = rows[order], cols[order]
+        key = rows * n_cols + cols
+        order = np.argsort(key, kind="stable")   # the order of lexsort((cols, rows))
+        k_s = key[order]
         dup = np.zeros(rows.size, dtype=bool)
-        dup[1:] = (r_s[1:] == r_s[:-1]) & (c_s[1:] == c_s[:-1])
+        dup[1:] = k_s[1:] == k_s[:-1]
         if not dup.any():
             return cols
         bad = order[dup]
