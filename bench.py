@@ -1,15 +1,21 @@
 #!/usr/bin/env python
 """Benchmark of the LOOPS hybrid SpMM on GB300: SpMM GFLOP/s (2 * nnz * N per call) and the
-roofline fractions, hybrid vs CSR-only, on the FP64 hybrid-split workload: the 512 x 512
-five-point Laplacian with 4,096 random dense 8 x 8 diagonal blocks added (262,144 rows,
-1,480,704 nonzeros), B 262,144 x 64 in FP64 N(0, 1). Synthetic, seeded inputs.
+roofline fraction of the dominant kernel, hybrid vs CSR-only, at a stated rel-L2 against the
+FP64 oracle.
 
-One step is one C = A . B call of the whole hot path (CSR part and BCSR part) on inputs
-resident in HBM; the plan (the partition, built once, as the paper excludes format
-conversion from its timing) is made before timing. L2 is flushed (a 256 MiB write) before
-every timed step and each step is timed on the device with CUDA events.
+Default line: the largest single-GPU workload, a batch of 512 sparse matrices of 1,000 to
+65,536 rows (uniform rows, banded |i - j| <= 16, and two dense 16 x 16 blocks per 16-row
+block, by index mod 3; 275.7 M nonzeros, N drawn from {16, 32, 64, 128}) in FP32, run by one
+graph-captured batched call. One step is one C_m = A_m . B_m of every matrix of the batch on
+operands resident in HBM; the plan (partition and layout, built once, as the paper excludes
+format conversion from its timing) is made before timing. L2 is flushed (a 256 MiB write, then
+a read) before every timed step; every step is timed on the device with CUDA events. The line
+carries the other workloads as sub-lines (``workloads``): the FP64 Laplacian with dense blocks,
+the R-MAT graph in FP16 and BF16, the GCN layer forward and backward, and the small plain CSR
+case, each with its own roofline and error.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl loops|reference] [--N 64]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl loops|reference]
+                  [--workload batched|laplacian|rmat|gcn|uniform|mixed] [--dtype ...]
 
 Under torchrun each rank runs its own replica of the workload on its GPU (the path needs no
 exchange); rank 0 prints one JSON line with the whole-job throughput (max time over ranks).
@@ -25,6 +31,7 @@ import statistics
 import subprocess
 import sys
 import time
+from concurrent.futures import ThreadPoolExecutor
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
@@ -36,50 +43,49 @@ import workloads as W  # noqa: E402
 
 METRIC = "SpMM GFLOP/s (2·nnz·N) and % HBM roofline, hybrid vs CSR-only at stated rel-L2"
 HBM_NOMINAL_GBS = 8000.0
-# FP64 peak of GB300 from unit counts and clock: 152 SMs x 2 FP64 FMA/clk x 2 FLOP x 2.07 GHz
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-TOL_F64 = 1e-12
+# FP64 peak of this GPU, measured: 8 independent DFMA chains per thread, 8 blocks of 256
+# threads per SM, CUDA events, SM clock 2,070 MHz throughout (profiles/fp64_peak_probe.md).
+FP64_PEAK_TFLOPS = 1.2033
+FP64_PEAK_SOURCE = ("measured DFMA throughput, 1.2033 TFLOP/s at 2,070 MHz (profiles/fp64_peak_probe.md); "
+                    "nominal 152 SMs x 2 FMA/clk x 2 FLOP x 2.07 GHz = 1.259")
+TOL = {"f64": 1e-12, "f32": 1e-5, "f16": 2e-3, "bf16": 2e-3}
+BATCH_COUNT, BATCH_SEED = 512, 5
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["loops", "reference"], default="loops")
-    ap.add_argument("--N", type=int, default=64)
-    ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["laplacian", "rmat", "gcn", "batched", "uniform", "mixed"],
-                    default="laplacian",
-                    help="laplacian (default, the FP64 hybrid-split workload) or one of the other "
-                         "synthetic workloads, measured the same way")
-    ap.add_argument("--dtype", default=None, help="rmat: f16 or bf16; batched, mixed: f32 or bf16")
-    ap.add_argument("--batch-count", type=int, default=512,
+    ap.add_argument("--workload", choices=["batched", "laplacian", "rmat", "gcn", "uniform", "mixed"],
+                    default="batched",
+                    help="batched (default: the 512-matrix batch, with the other workloads as sub-lines) "
+                         "or one workload alone, measured the same way")
+    ap.add_argument("--dtype", default=None, help="batched: f32 (default) or bf16; rmat: f16 or bf16; "
+                                                  "mixed: f32 or bf16")
+    ap.add_argument("--N", type=int, default=64, help="laplacian: columns of B")
+    ap.add_argument("--batch-count", type=int, default=BATCH_COUNT,
                     help="batched: number of matrices (smaller counts give small profiling cases)")
-    return ap.parse_args()
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-sub", action="store_true", help="batched: skip the sub-line workloads")
+    return ap.parse_args(argv)
 
 
-def workload(N: int):
-    A, B = W.laplacian_blocks(grid=512, n_blocks=4096, block=8, seed=1, N=N)
-    return A, B
-
-
-def config(N: int):
-    return {"workload": f"laplacian512+4096x8x8 blocks, FP64, N={N}", "n_rows": 262144, "nnz": 1480704,
-            "N": N, "dtype": "f64",
-            "l2": "flushed before every timed step (256 MiB write, then a 256 MiB read to clean it)",
-            "plan": "built once before timing (conversion excluded as in the paper)"}
-
-
-def alg_bytes(A, N: int, eb: int = 8) -> int:
-    return (A.n_rows + 1) * 8 + A.nnz * (4 + eb) + A.n_cols * N * eb + A.n_rows * N * eb
-
-
+# ------------------------------------------------------------------ helpers
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def host_cores() -> int:
+    """Host threads available to this process."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
 
 
 class ClockSampler:
@@ -136,109 +142,25 @@ def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         d = json.load(open(p))
-        return float(d.get("hbm_gbs", 6800.0)), "measured"
+        return float(d.get("hbm_gbs", 6800.0)), "measured (MEASURED_PEAKS.json hbm_gbs, burst copy)"
     return 6800.0, "fallback"
 
 
 def traffic_for(kernel_key: str):
-    """DRAM bytes per launch of a kernel from the committed ncu summary, if the kernel's
-    source is unchanged since the capture (else None)."""
+    """DRAM bytes per launch of a kernel from the committed ncu summary, if the sources it was
+    captured from are unchanged since the capture (else None)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p)).get(kernel_key)
     if not d:
         return None
-    src = os.path.join(ROOT, d["source"])
-    if not os.path.exists(src):
-        return None
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    return d["dram_bytes_per_launch"] if sha == d["source_sha256"] else None
-
-
-def host_cores() -> int:
-    """Host threads available to this process."""
-    try:
-        return len(os.sched_getaffinity(0))
-    except AttributeError:
-        return os.cpu_count() or 1
-
-
-def oracle_spmm_on(A, B, threads: int):
-    """The oracle's row loop on `threads` host threads (bit-identical to one thread)."""
-    import oracle
-
-    return oracle.spmm(A, B) if threads == 1 else oracle.spmm_threads(A, B, threads)
-
-
-def cpu_baseline(A, B, threads: int = 1, budget_s: float = 12.0):
-    """The oracle as it stands on the full workload, on `threads` host threads, repeated for
-    about `budget_s` seconds. Returns (GFLOP/s, C_oracle, reps, seconds)."""
-    import oracle
-
-    oracle.build()
-    flops = 2.0 * A.nnz * B.shape[1]
-    reps, t_tot, C = 0, 0.0, None
-    while reps < 1 or (t_tot < budget_s and reps < 200):
-        t0 = time.perf_counter()
-        C = oracle_spmm_on(A, B, threads)
-        t_tot += time.perf_counter() - t0
-        reps += 1
-    return flops * reps / t_tot / 1e9, C, reps, t_tot
-
-
-def run_reference(args):
-    rank, world, local = dist_env()
-    if rank != 0:
-        return
-    import oracle
-
-    oracle.build()
-    A, B = workload(args.N)
-    flops = 2.0 * A.nnz * args.N
-    threads = host_cores()
-    for _ in range(args.warmup):
-        oracle_spmm_on(A, B, threads)
-    times = []
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        oracle_spmm_on(A, B, threads)
-        times.append(time.perf_counter() - t0)
-    t = sum(times) / len(times)
-    v = flops / t / 1e9
-    line = {"metric": METRIC, "value": v, "unit": "GFLOP/s", "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)", "config": config(args.N),
-            "impl": "reference",
-            "cpu_baseline": {"value": v, "unit": "GFLOP/s", "cores": threads, "kind": "oracle",
-                             "sample": f"full workload per step (FP64 C oracle, rows split over "
-                                       f"{threads} host threads)"},
-            "e2e": {"value": v, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
-
-
-def plan_build_compare(torch, lp, A, N, fmt, tau, reps=3):
-    """Wall time of building the same plan (fixed tau, no autotuning) on the host from host
-    arrays (loops_plan) and on the GPU from device-resident arrays (loops_plan_device), best of
-    `reps`; and whether the two partitions are identical."""
-    Ad = W.CSR(A.n_rows, A.n_cols, torch.as_tensor(A.row_ptr).cuda(), torch.as_tensor(A.col_idx).cuda(),
-               torch.as_tensor(A.vals).cuda())
-    out = {"tau": tau, "dtype": fmt}
-    plans = {}
-    for key, dev in (("host_s", False), ("device_s", True)):
-        best = math.inf
-        for _ in range(reps):
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            pl = lp.Plan(Ad if dev else A, N, fmt, tau=tau, build_on_device=dev)
-            torch.cuda.synchronize()
-            best = min(best, time.perf_counter() - t0)
-            plans[key] = pl
-        out[key] = best
-    ea, eb = plans["host_s"].export(), plans["device_s"].export()
-    out["identical"] = bool(all(np.array_equal(np.asarray(ea[k]), np.asarray(eb[k])) for k in ea))
-    out["speedup"] = out["host_s"] / out["device_s"]
-    return out
+    srcs = d["sources"] if "sources" in d else {d["source"]: d["source_sha256"]}
+    for src, sha in srcs.items():
+        path = os.path.join(ROOT, src)
+        if not os.path.exists(path) or hashlib.sha256(open(path, "rb").read()).hexdigest() != sha:
+            return None
+    return d["dram_bytes_per_launch"]
 
 
 def max_over_ranks(torch, x: float, world: int, device) -> float:
@@ -254,38 +176,413 @@ def whole_job_gflops(flops_per_rank_step: float, world: int, ms_step: float) -> 
     return world * flops_per_rank_step / (ms_step * 1e-3) / 1e9
 
 
-def time_plan(torch, plan, Bd, Cd, steps, warmup, flush, part_events=True):
-    """Per-step device times (ms) of plan.spmm, and of its CSR / BCSR parts."""
+def csr_alg_bytes(n_rows, n_cols, nnz, N, e, c) -> int:
+    """Algorithmic bytes of one SpMM: A once (row pointers, column indices, values in the
+    compute dtype), B once and C once (gathers and padding not counted)."""
+    return (n_rows + 1) * 8 + nnz * (4 + e) + n_cols * N * e + n_rows * N * c
+
+
+def rel_l2(got, ref) -> float:
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    nr = np.linalg.norm(ref)
+    if nr == 0.0:
+        return 0.0 if np.all(got == 0) else float("inf")
+    return float(np.linalg.norm(got - ref) / nr)
+
+
+def make_flush(torch):
+    """L2 flush: write a 256 MiB buffer (larger than the 126 MiB L2), then read another one so
+    the dirty lines are written back before the timed kernel starts, not during it."""
+    flush_w = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    flush_r = torch.ones(64 << 20, dtype=torch.float32, device="cuda")
+    flush_out = torch.empty((), dtype=torch.float32, device="cuda")
+
+    def flush():
+        flush_w.zero_()
+        torch.sum(flush_r, dim=0, out=flush_out)
+    return flush
+
+
+def new_events(torch, n):
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+    s = torch.cuda.current_stream()
+    for e in evs:                 # materialise the handles
+        e.record(s)
+    torch.cuda.synchronize()
+    return evs
+
+
+def time_steps(torch, fn, steps, warmup, flush, plan=None):
+    """Per-step device times (ms) of fn() with the L2 flushed before each step, and (with a
+    plan) the times between its timing events [0]-[1] and [2]-[3] in each step."""
     for _ in range(warmup):
-        plan.spmm(Bd, Cd)
+        fn()
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-    pev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+    pev = [new_events(torch, 4) for _ in range(steps)] if plan is not None else None
     stream = torch.cuda.current_stream()
-    if part_events:
-        for row in pev:           # materialise the events so their handles exist
-            for e in row:
-                e.record(stream)
-        torch.cuda.synchronize()
     for k in range(steps):
         flush()
-        if part_events:
+        if plan is not None:
             plan.set_timing_events([e.cuda_event for e in pev[k]])
         ev[k][0].record(stream)
-        plan.spmm(Bd, Cd)
+        fn()
         ev[k][1].record(stream)
     torch.cuda.synchronize()
-    plan.set_timing_events(None)
+    if plan is not None:
+        plan.set_timing_events(None)
     step = [a.elapsed_time(b) for a, b in ev]
-    csr = [r[0].elapsed_time(r[1]) for r in pev] if part_events else []
-    bcsr = [r[2].elapsed_time(r[3]) for r in pev] if part_events else []
-    return step, csr, bcsr
+    p01 = [r[0].elapsed_time(r[1]) for r in pev] if pev else []
+    p23 = [r[2].elapsed_time(r[3]) for r in pev] if pev else []
+    return step, p01, p23
+
+
+def rounded_matrix(A, fmt):
+    """A with the values the plan stores: round(s_A * a) / s_A in the format (s_A the plan's
+    power-of-two scale; exact undo)."""
+    import oracle
+
+    if fmt == "f64":
+        return A
+    s = oracle.plan_scale(A.vals, fmt)
+    return W.CSR(A.n_rows, A.n_cols, A.row_ptr, A.col_idx, oracle.round_to(A.vals * s, fmt) / s)
 
 
 def launches_per_step(info) -> int:
-    return int(info["n_csr_rows"] > 0) + int(info["n_split_rows"] > 0) + int(info["n_row_blocks"] > 0)
+    """Library kernels one single-matrix SpMM launches: CSR part, its split-row sums, BCSR part,
+    its split-block sums, the tile-level split's second CSR pass."""
+    return (int(info["n_csr_rows"] > 0) + int(info["n_split_rows"] > 0) + int(info["n_row_blocks"] > 0))
 
 
+def oracle_batch(mats, Bs, threads):
+    """The oracle (FP64 C row loop) on every matrix of a batch, matrices spread over host
+    threads (each matrix on one thread)."""
+    import oracle
+
+    with ThreadPoolExecutor(max(1, threads)) as ex:
+        return list(ex.map(lambda ab: oracle.spmm(ab[0], ab[1]), zip(mats, Bs)))
+
+
+# ------------------------------------------------------------------ the 512-matrix batch
+def batch_inputs(count: int, fmt: str):
+    """The batch (A_m, N_m) and its dense operands B_m (host, float32 N(0, 1), seeded per
+    matrix); for BF16 the values the GPU multiplies are the BF16 roundings."""
+    mats = W.batched_mix(count=count, seed=BATCH_SEED)
+    Bs = [W.dense_normal(A.n_cols, N, 10_000 + m).astype(np.float32) for m, (A, N) in enumerate(mats)]
+    return mats, Bs
+
+
+def batch_config(count: int, fmt: str, nnz: int) -> dict:
+    return {"workload": f"batch of {count} sparse matrices (1,000-65,536 rows; uniform 8-64 per row / banded "
+                        f"|i-j|<=16 / two dense 16x16 blocks per 16-row block, by index mod 3), "
+                        f"N in {{16,32,64,128}}, {fmt.upper()}",
+            "count": count, "nnz": int(nnz), "dtype": fmt,
+            "l2": "flushed before every timed step (256 MiB write, then a 256 MiB read); the batch's B and "
+                  "C (4 GB in FP32) exceed L2 as well",
+            "plan": "built once before timing (conversion excluded as in the paper)"}
+
+
+def run_batched(args, torch, lp, flush, rank, world, hbm_peak, hbm_src):
+    fmt = args.dtype or "f32"
+    e = 4 if fmt == "f32" else 2
+    dt = torch.float32 if fmt == "f32" else torch.bfloat16
+    t0 = time.perf_counter()
+    mats, Bh = batch_inputs(args.batch_count, fmt)
+    gen_s = time.perf_counter() - t0
+    As = [A for A, _ in mats]
+    Ns = [N for _, N in mats]
+    nnz = sum(A.nnz for A in As)
+    flops = sum(2.0 * A.nnz * N for A, N in mats)
+    alg = sum(csr_alg_bytes(A.n_rows, A.n_cols, A.nnz, N, e, 4) for A, N in mats)
+    Bd = [torch.as_tensor(B).to(dt).cuda() for B in Bh]
+    Cd = [torch.empty((A.n_rows, N), device="cuda") for A, N in mats]
+
+    t0 = time.perf_counter()
+    plan = lp.BatchedPlan(As, Ns, fmt, tau=-1.0)
+    plan_s = time.perf_counter() - t0
+    st = plan.stats()
+
+    # main timed region: K steps, barrier + synchronize on both sides, clocks sampled
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    for _ in range(args.warmup):
+        plan.spmm(Bd, Cd)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    sampler.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("timed")
+    step, kern, red = time_steps(torch, lambda: plan.spmm(Bd, Cd), args.steps, 0, flush, plan=plan)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    clocks = sampler.stop()
+    if world > 1:
+        torch.distributed.barrier()
+    ms_step = max_over_ranks(torch, sum(step), world, "cuda") / args.steps
+    value = whole_job_gflops(flops, world, ms_step)
+    kern_ms = statistics.mean(kern)
+    achieved = alg / (kern_ms * 1e-3) / 1e9
+
+    # parity of the timed plan's output: every matrix against the oracle (FP64, same rounded
+    # inputs); the max over matrices of the per-matrix rel-L2
+    plan.spmm(Bd, Cd)
+    torch.cuda.synchronize()
+    rel_max = None
+    if rank == 0:
+        Bq = [torch.as_tensor(B).to(dt).double().numpy() for B in Bh]   # the values the GPU multiplies
+        refs = oracle_batch([rounded_matrix(A, fmt) for A in As], Bq, host_cores())
+        rels = [rel_l2(C.double().cpu().numpy(), R) for C, R in zip(Cd, refs)]
+        rel_max = max(rels)
+        del refs, Bq
+
+    # hybrid vs CSR-only (same inputs, same accuracy), fewer steps
+    variants = {}
+    for name, tau in (("csr_only", math.inf), ("hybrid_tau2", 2.0)):
+        vp = lp.BatchedPlan(As, Ns, fmt, tau=tau)
+        torch.cuda.nvtx.range_push(f"variant:{name}")
+        s_v, k_v, _ = time_steps(torch, lambda: vp.spmm(Bd, Cd), max(5, args.steps // 2), 2, flush, plan=vp)
+        torch.cuda.nvtx.range_pop()
+        ms = statistics.mean(s_v)
+        variants[name] = {"tau": tau, "gflops": flops / (ms * 1e-3) / 1e9, "ms_per_step": ms,
+                          "kernel_ms": statistics.mean(k_v), "nnz_bcsr": vp.stats()["nnz_bcsr"]}
+        vp.destroy()
+    plan.spmm(Bd, Cd)
+
+    # end to end through the C ABI with pinned host buffers: every step copies all B_m in and
+    # all C_m out (loops_spmm_batched_host synchronises)
+    e2e = None
+    if not args.no_e2e:
+        Bp = [torch.as_tensor(B).to(dt).pin_memory() for B in Bh]
+        Cp = [torch.empty((A.n_rows, N), dtype=torch.float32).pin_memory() for A, N in mats]
+        k_e2e = max(3, min(args.steps, 10))
+        for _ in range(2):
+            plan.spmm_host(Bp, Cp)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(k_e2e):
+            plan.spmm_host(Bp, Cp)
+        t_e2e = (time.perf_counter() - t0) * 1e3 / k_e2e
+        h2d = int(sum(B.numel() * B.element_size() for B in Bp))
+        d2h = int(sum(C.numel() * 4 for C in Cp))
+        same = all(torch.equal(c.cpu(), h) for c, h in zip(Cd[:8], Cp[:8]))
+        e2e = {"value": world * flops / (t_e2e * 1e-3) / 1e9, "unit": "GFLOP/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": t_e2e,
+               "link_gbs": (h2d + d2h) / (t_e2e * 1e-3) / 1e9, "matches_device_call": bool(same),
+               "api": "loops_spmm_batched_host (pinned host B_m and C_m, copied in and out every step, "
+                      "host wall clock per synchronous call)"}
+        del Bp, Cp
+
+    cpu = None
+    if rank == 0 and world == 1:
+        cpu = batch_cpu_baseline(mats, Bh, budget_s=12.0)
+
+    line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": fmt,
+            "data": "synthetic (seeded: matrices of the batch recipe, B ~ N(0,1) per matrix)",
+            "config": dict(batch_config(args.batch_count, fmt, nnz), parallelism=f"replicas{world}",
+                           tau_autotuned=st["tau"], block_rows=st["block_rows"], plan_build_s=plan_s,
+                           input_generation_s=gen_s),
+            "roofline": {"bound": "hbm", "kernel": "batched persistent kernel(s) (one graph replay)",
+                         "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                         "traffic": traffic_for(f"batched_{fmt}_batch{args.batch_count}"),
+                         "peak_source": hbm_src, "alg_bytes_per_launch": alg, "kernel_ms": kern_ms,
+                         "partial_sum_ms": statistics.mean(red),
+                         "alg_bytes": "sum over matrices of A once (row_ptr 8 B/row, 4 B index + value per "
+                                      "nonzero) + B once + C once"},
+            "hbm": {"alg_bytes_per_step": alg, "achieved_gbs": alg / (ms_step * 1e-3) / 1e9,
+                    "frac_of_measured": alg / (ms_step * 1e-3) / 1e9 / hbm_peak,
+                    "frac_of_8tbs": alg / (ms_step * 1e-3) / 1e9 / HBM_NOMINAL_GBS},
+            "rel_l2_vs_oracle": rel_max, "rel_l2_what": "max over the 512 matrices of ||C - C_oracle|| / ||C_oracle||, "
+                                                        "oracle in FP64 on the same rounded inputs",
+            "rel_l2_tol": TOL[fmt],
+            "variants": variants, "hybrid_over_csr_only": variants["csr_only"]["ms_per_step"] / ms_step,
+            "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": st["n_kernels"] * args.steps, "plan": st}
+    return line
+
+
+def batch_cpu_baseline(mats, Bh, budget_s=12.0):
+    """The oracle as it stands on a bounded sample of the batch (every 8th matrix: all three
+    structures and all N), matrices spread over all host threads, repeated for about budget_s."""
+    import oracle
+
+    oracle.build()
+    threads = host_cores()
+    idx = list(range(0, len(mats), 8))
+    sub = [mats[i][0] for i in idx]
+    Bs = [Bh[i].astype(np.float64) for i in idx]
+    flops = sum(2.0 * mats[i][0].nnz * mats[i][1] for i in idx)
+    reps, t_tot = 0, 0.0
+    while reps < 1 or (t_tot < budget_s and reps < 50):
+        t0 = time.perf_counter()
+        oracle_batch(sub, Bs, threads)
+        t_tot += time.perf_counter() - t0
+        reps += 1
+    return {"value": flops * reps / t_tot / 1e9, "unit": "GFLOP/s", "cores": threads, "kind": "oracle",
+            "sample": f"every 8th matrix of the batch ({len(idx)} matrices, {flops / 1e9:.2f} GFLOP) x {reps} "
+                      f"runs ({t_tot:.1f} s); FP64 C oracle, one matrix per host thread"}
+
+
+# ------------------------------------------------------------------ single-matrix workloads
+def single_inputs(name: str, fmt: str | None, N: int = 64):
+    """(A, B, N, fmt, description, extra) of a single-matrix workload; extra holds the GCN dY."""
+    if name == "laplacian":
+        A, B = W.laplacian_blocks(grid=512, n_blocks=4096, block=8, seed=1, N=N)
+        return A, B, N, "f64", f"laplacian512+4096x8x8 blocks, FP64, N={N}", None
+    if name == "rmat":
+        fmt = fmt or "f16"
+        A, B = W.rmat_graph(scale=20, samples_per_node=8, seed=3, N=128)
+        return A, B, 128, fmt, (f"R-MAT 2^20 (a=0.57,b=0.19,c=0.19), avg degree 16, N=128, {fmt} with per-column "
+                                f"scaling"), None
+    if name == "gcn":
+        A, X, dY = W.gcn_graph(scale=18, samples_per_node=16, seed=4, N=256)
+        A = W.CSR(A.n_rows, A.n_cols, A.row_ptr, A.col_idx, A.vals.astype(np.float32))
+        return A, X, 256, "f32", "GCN layer: R-MAT 2^18 + I, D^-1/2 (A+I) D^-1/2, N=256, f32", dY
+    if name == "uniform":
+        A, B = W.uniform_rows(2000, 10, 32, seed=1)
+        return A, B, 32, "f32", "uniform 2,000 x 2,000, 10 nnz/row, N=32, f32", None
+    fmt = fmt or "f32"
+    A, B = W.block_mix(n=1 << 20, N=64)
+    return A, B, 64, fmt, (f"block mix 2^20: half the 16-row blocks two dense 16x16 blocks, the rest 16 uniform "
+                           f"columns per row, N=64, {fmt}"), None
+
+
+def run_single(name, args, torch, lp, flush, hbm_peak, hbm_src, steps, warmup, fmt=None, full=False):
+    """One single-matrix workload: autotuned plan timed (L2 flushed per step), its dominant part's
+    roofline, CSR-only and hybrid variants, rel-L2 against the oracle (and, for 16-bit formats,
+    against the unrounded FP64 problem); the GCN layer adds its backward pass."""
+    import oracle
+
+    A, B, N, fmt, desc, dY = single_inputs(name, fmt, args.N)
+    e = {"f64": 8, "f32": 4}.get(fmt, 2)
+    c = 8 if fmt == "f64" else 4
+    flops = 2.0 * A.nnz * N
+    alg = csr_alg_bytes(A.n_rows, A.n_cols, A.nnz, N, e, c)
+    A_r = rounded_matrix(A, fmt)
+    sc = None
+    if fmt in ("f16", "bf16"):
+        Bq, s = oracle.scale_round_columns(B, fmt)
+        B_eff = Bq * s[None, :]
+        Bd = torch.as_tensor(Bq).to(torch.float16 if fmt == "f16" else torch.bfloat16).cuda()
+        sc = torch.as_tensor(s, dtype=torch.float32).cuda()
+    else:
+        B_eff = B if fmt == "f64" else B.astype(np.float32).astype(np.float64)
+        Bd = torch.as_tensor(B_eff).to(torch.float64 if fmt == "f64" else torch.float32).cuda()
+    Cd = torch.empty((A.n_rows, N), dtype=torch.float64 if fmt == "f64" else torch.float32, device="cuda")
+    plan = lp.Plan(A, N, fmt, tau=-1.0, want_backward=(name == "gcn"))
+    inf = plan.info()
+    torch.cuda.nvtx.range_push(f"workload:{name}")
+    step, csr, bcsr = time_steps(torch, lambda: plan.spmm(Bd, Cd, col_scale=sc), steps, warmup, flush, plan=plan)
+    torch.cuda.nvtx.range_pop()
+    ms = statistics.mean(step)
+    csr_ms, bcsr_ms = statistics.mean(csr), statistics.mean(bcsr)
+    # dominant part: its algorithmic bytes (its rows, entries, B once, its C rows) over its time
+    if csr_ms >= bcsr_ms:
+        part, p_ms, rows, pnnz = "csr", csr_ms, inf["n_csr_rows"], inf["nnz_csr"]
+    else:
+        part, p_ms, rows, pnnz = "bcsr", bcsr_ms, inf["n_row_blocks"] * inf["block_rows"], inf["nnz_bcsr"]
+    p_bytes = rows * 8 + pnnz * (4 + e) + A.n_cols * N * e + rows * N * c
+    if fmt == "f64":
+        ach = 2.0 * pnnz * N / (p_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": f"{part} part", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "peak_source": FP64_PEAK_SOURCE,
+                "hbm_frac": p_bytes / (p_ms * 1e-3) / 1e9 / hbm_peak}
+        key = "csr_spmm_f64_n64" if (part == "csr" and N == 64) else None
+    else:
+        ach = p_bytes / (p_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": f"{part} part", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                "frac": ach / hbm_peak, "peak_source": hbm_src}
+        key = f"{part}_{name}_{fmt}"
+    roof.update(traffic=traffic_for(key) if key else None, kernel_ms=p_ms, alg_bytes_per_launch=p_bytes)
+    C = plan.spmm(Bd, Cd, col_scale=sc).double().cpu().numpy()
+    ref = oracle.spmm_threads(A_r, B_eff, host_cores())
+    out = {"workload": desc, "dtype": fmt, "nnz": int(A.nnz), "N": N, "value": flops / (ms * 1e-3) / 1e9,
+           "unit": "GFLOP/s", "ms_per_step": ms, "steps": steps, "roofline": roof,
+           "hbm": {"alg_bytes_per_step": alg, "frac_of_measured": alg / (ms * 1e-3) / 1e9 / hbm_peak},
+           "tau_autotuned": inf["tau"], "tile_min": inf["tile_min"], "part_ms": {"csr": csr_ms, "bcsr": bcsr_ms},
+           "rel_l2_vs_oracle": rel_l2(C, ref), "rel_l2_tol": TOL[fmt],
+           "gpu_launches_per_step": launches_per_step(inf)}
+    if fmt in ("f16", "bf16"):
+        out["rel_l2_vs_unrounded_fp64"] = rel_l2(C, oracle.spmm_threads(A, B, host_cores()))
+    if full or name in ("laplacian", "mixed"):
+        var = {}
+        for vname, tau in (("csr_only", math.inf), ("hybrid_tau2", 2.0)):
+            vp = lp.Plan(A, N, fmt, tau=tau)
+            s_v, _, _ = time_steps(torch, lambda: vp.spmm(Bd, Cd, col_scale=sc), max(5, steps // 2), 2, flush)
+            var[vname] = {"gflops": flops / (statistics.mean(s_v) * 1e-3) / 1e9, "ms_per_step": statistics.mean(s_v),
+                          "bcsr_row_blocks": vp.info()["n_row_blocks"]}
+            vp.destroy()
+        out["variants"] = var
+    if name == "gcn":
+        dYd = torch.as_tensor(dY, dtype=torch.float32).cuda()
+        dYq = dY.astype(np.float32).astype(np.float64)
+        dB = torch.empty((A.n_cols, N), dtype=torch.float32, device="cuda")
+        st_b, _, _ = time_steps(torch, lambda: plan.backward(dYd, Bd), steps, warmup, flush)
+        bms = statistics.mean(st_b)
+        dX, dv = plan.backward(dYd, Bd)
+        torch.cuda.synchronize()
+        bw_bytes = 2 * alg - (A.n_rows + 1) * 8       # A^T dY pass and the SDDMM pass over A's pattern
+        out["backward"] = {"ms_per_step": bms, "gflops": 2 * flops / (bms * 1e-3) / 1e9,
+                           "hbm_frac": bw_bytes / (bms * 1e-3) / 1e9 / hbm_peak,
+                           "what": "dX = A^T dY (transposed hybrid plan) + dvals = SDDMM(dY, X^T)",
+                           "rel_l2_dX_vs_oracle": rel_l2(dX.double().cpu().numpy(), oracle.spmm_t(A_r, dYq)),
+                           "rel_l2_dvals_vs_oracle": rel_l2(dv.double().cpu().numpy(),
+                                                            oracle.sddmm(A_r, dYq, B_eff)),
+                           "rel_l2_tol": TOL[fmt]}
+        del dB
+    plan.destroy()
+    return out
+
+
+# ------------------------------------------------------------------ reference arm (the oracle)
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    import oracle
+
+    oracle.build()
+    threads = host_cores()
+    if args.workload == "batched":
+        mats, Bh = batch_inputs(args.batch_count, args.dtype or "f32")
+        idx = list(range(0, len(mats), 8))
+        sub = [mats[i][0] for i in idx]
+        Bs = [Bh[i].astype(np.float64) for i in idx]
+        flops = sum(2.0 * mats[i][0].nnz * mats[i][1] for i in idx)
+        run = lambda: oracle_batch(sub, Bs, threads)  # noqa: E731
+        config = batch_config(args.batch_count, args.dtype or "f32", sum(A.nnz for A, _ in mats))
+        sample = (f"every 8th matrix of the batch ({len(idx)} matrices, {flops / 1e9:.2f} GFLOP) per step; FP64 C "
+                  f"oracle, one matrix per host thread")
+        dtype = args.dtype or "f32"
+    else:
+        A, B, N, fmt, desc, _ = single_inputs(args.workload, args.dtype, args.N)
+        flops = 2.0 * A.nnz * N
+        run = lambda: oracle.spmm_threads(A, B, threads)  # noqa: E731
+        config = {"workload": desc, "nnz": int(A.nnz), "N": N}
+        sample = f"full workload per step (FP64 C oracle, rows split over {threads} host threads)"
+        dtype = fmt
+    for _ in range(args.warmup):
+        run()
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        run()
+        times.append(time.perf_counter() - t0)
+    t = sum(times) / len(times)
+    v = flops / t / 1e9
+    line = {"metric": METRIC, "value": v, "unit": "GFLOP/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": dtype, "data": "synthetic (seeded)", "config": config,
+            "impl": "reference",
+            "cpu_baseline": {"value": v, "unit": "GFLOP/s", "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ main
 def run_loops(args):
     import torch
 
@@ -301,331 +598,43 @@ def run_loops(args):
     if world > 1:
         torch.distributed.barrier(device_ids=[local])
     lp.load()
-    N = args.N
-    A, B = workload(N)
-    flops = 2.0 * A.nnz * N
-    hbm_peak, hbm_src = peaks()
-
-    Bd = torch.as_tensor(B).cuda()
-    Cd = torch.empty((A.n_rows, N), dtype=torch.float64, device="cuda")
-    # L2 flush: write a 256 MiB buffer (larger than the 126 MiB L2), then read another one so
-    # the dirty lines are written back before the timed kernel starts, not during it
-    flush_w = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    flush_r = torch.ones(64 << 20, dtype=torch.float32, device="cuda")
-    flush_out = torch.empty((), dtype=torch.float32, device="cuda")
-
-    def flush():
-        flush_w.zero_()
-        torch.sum(flush_r, dim=0, out=flush_out)
-
-    t0 = time.perf_counter()
-    plan = lp.Plan(A, N, "f64", tau=-1.0)           # autotuned split
-    plan_s = time.perf_counter() - t0
-    info = plan.info()
-    variants = {"csr_only": (math.inf, 0), "hybrid_tau2": (2.0, 0), "hybrid_tau2_tile_split": (2.0, 2),
-                "bcsr_only": (0.0, 0)}
-    vplans = {k: lp.Plan(A, N, "f64", tau=t, tile_min=tm) for k, (t, tm) in variants.items()}
-    build_cmp = plan_build_compare(torch, lp, A, N, "f64", 2.0) if rank == 0 else None
-
-    # main timed region: K steps, barrier + synchronize on both sides
-    sampler = ClockSampler(local)
-    for _ in range(args.warmup):
-        plan.spmm(Bd, Cd)
-    torch.cuda.synchronize()
+    import oracle
+    if rank == 0:
+        oracle.build()
     if world > 1:
         torch.distributed.barrier(device_ids=[local])
-    sampler.start()
-    time.sleep(0.3)
-    torch.cuda.synchronize()
-    torch.cuda.nvtx.range_push("timed")
-    step, csr, bcsr = time_plan(torch, plan, Bd, Cd, args.steps, 0, flush)
-    torch.cuda.synchronize()
-    torch.cuda.nvtx.range_pop()
-    clocks = sampler.stop()
-    if world > 1:
-        torch.distributed.barrier(device_ids=[local])
-    total_ms = sum(step)
-    total_ms = max_over_ranks(torch, total_ms, world, "cuda")
-    ms_step = total_ms / args.steps
-    value = whole_job_gflops(flops, world, ms_step)
-
-    # variants (same inputs, same accuracy), fewer steps
-    var_out = {}
-    for k, p in vplans.items():
-        torch.cuda.nvtx.range_push(f"variant:{k}")  # lets a profiler select one variant's launches
-        s, c, b = time_plan(torch, p, Bd, Cd, max(10, args.steps // 2), 3, flush)
-        torch.cuda.nvtx.range_pop()
-        inf_ = p.info()
-        var_out[k] = {"tau": variants[k][0], "tile_min": variants[k][1],
-                      "gflops": flops / (statistics.mean(s) * 1e-3) / 1e9,
-                      "ms_per_step": statistics.mean(s), "bcsr_row_blocks": inf_["n_row_blocks"],
-                      "bcsr_tiles": inf_["n_tiles"], "csr_ms": statistics.mean(c), "bcsr_ms": statistics.mean(b)}
-    # restore the main plan's output for the parity check below
-    plan.spmm(Bd, Cd)
-    torch.cuda.synchronize()
-
-    # dominant kernel of the step and its roofline (FP64 here is bound by the FP64 pipe)
-    csr_ms, bcsr_ms = statistics.mean(csr), statistics.mean(bcsr)
-    if csr_ms >= bcsr_ms:
-        dom, dom_ms, dom_nnz = "csr_spmm_vec<TrF64,32,1,1>", csr_ms, info["nnz_csr"]
-        tkey = "csr_spmm_f64_n64"
-    else:
-        dom, dom_ms, dom_nnz = "bcsr_dmma<4>", bcsr_ms, info["nnz_bcsr"]
-        tkey = "bcsr_dmma_f64_n64"
-    dom_tflops = 2.0 * dom_nnz * N / (dom_ms * 1e-3) / 1e12
-    traffic = traffic_for(tkey) if N == 64 else None
-    roofline = {"bound": "alu", "kernel": dom, "achieved": dom_tflops, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": dom_tflops / FP64_PEAK_TFLOPS, "traffic": traffic,
-                "peak_source": "FP64: 152 SMs x 2 FMA/clk x 2 FLOP x 2.07 GHz (nominal unit count)",
-                "kernel_ms": dom_ms}
-    step_bytes = alg_bytes(A, N)
-    hbm = {"alg_bytes_per_step": step_bytes, "achieved_gbs": step_bytes / (ms_step * 1e-3) / 1e9,
-           "frac_of_measured": step_bytes / (ms_step * 1e-3) / 1e9 / hbm_peak,
-           "frac_of_8tbs": step_bytes / (ms_step * 1e-3) / 1e9 / HBM_NOMINAL_GBS, "peak_gbs": hbm_peak,
-           "peak_source": hbm_src}
-
-    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
-    e2e = None
-    if not args.no_e2e:
-        Bh = torch.as_tensor(B).pin_memory()
-        Ch = torch.empty((A.n_rows, N), dtype=torch.float64).pin_memory()
-        k_e2e = max(3, min(args.steps, 20))
-        stream = torch.cuda.current_stream()
-        # synchronous call: copy in, SpMM, copy out, wait -- one step at a time
-        for _ in range(2):
-            plan.spmm_host(Bh, Ch)
-        t0 = time.perf_counter()
-        for _ in range(k_e2e):
-            plan.spmm_host(Bh, Ch)
-        t_sync = (time.perf_counter() - t0) * 1e3 / k_e2e
-        # pipelined call: step k+1's copy in overlaps step k's copy out
-        for _ in range(2):
-            plan.spmm_host_async(Bh, Ch)
-        plan.host_flush()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(k_e2e):
-            plan.spmm_host_async(Bh, Ch)
-        plan.host_flush()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        t_e2e = e0.elapsed_time(e1) / k_e2e
-        e2e = {"value": world * flops / (t_e2e * 1e-3) / 1e9, "unit": "GFLOP/s",
-               "h2d_bytes_per_step": int(Bh.numel() * 8), "d2h_bytes_per_step": int(Ch.numel() * 8),
-               "ms_per_step": t_e2e, "api": "loops_spmm_host_async (pinned host B and C, every step copied in and out)",
-               "sync_call": {"api": "loops_spmm_host", "ms_per_step": t_sync,
-                             "value": world * flops / (t_sync * 1e-3) / 1e9}}
-
-    if rank != 0:
-        return
-    cpu = None
-    rel = None
-    if world == 1:
-        threads = host_cores()
-        v_cpu, C_ref, reps, t_tot = cpu_baseline(A, B, threads, budget_s=6.0)
-        v_one, _, reps1, t_one = cpu_baseline(A, B, 1, budget_s=8.0)
-        cpu = {"value": v_cpu, "unit": "GFLOP/s", "cores": threads, "kind": "oracle",
-               "sample": f"full workload x {reps} runs ({t_tot:.1f} s, FP64 C oracle, rows split over "
-                         f"{threads} host threads)",
-               "single_thread": {"value": v_one, "cores": 1, "sample": f"full workload x {reps1} runs "
-                                                                       f"({t_one:.1f} s)"}}
-        C = Cd.cpu().numpy()
-        rel = float(np.linalg.norm(C - C_ref) / np.linalg.norm(C_ref))
-    line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Laplacian + dense blocks, N(0,1) B)",
-            "config": dict(config(N), parallelism=f"replicas{world}", tau_autotuned=info["tau"],
-                           tile_min_autotuned=info["tile_min"],
-                           bcsr_row_blocks=info["n_row_blocks"], bcsr_tiles=info["n_tiles"],
-                           plan_build_s=plan_s),
-            "plan_build": build_cmp,
-            "roofline": roofline, "hbm": hbm, "variants": var_out,
-            "rel_l2_vs_oracle": rel, "rel_l2_tol": TOL_F64,
-            "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-            "gpu_launches": launches_per_step(info) * args.steps,
-            "part_ms": {"csr": csr_ms, "bcsr": bcsr_ms}}
-    print(json.dumps(line), flush=True)
-
-
-def make_flush(torch):
-    flush_w = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    flush_r = torch.ones(64 << 20, dtype=torch.float32, device="cuda")
-    flush_out = torch.empty((), dtype=torch.float32, device="cuda")
-
-    def flush():
-        flush_w.zero_()
-        torch.sum(flush_r, dim=0, out=flush_out)
-    return flush
-
-
-def part_bytes(info, N, e, c, part):
-    """Algorithmic bytes of one part of a plan: its rows' pointers, its stored entries
-    (column + value), B once and its rows of C."""
-    if part == "csr":
-        rows, nnz = info["n_csr_rows"], info["nnz_csr"]
-    else:
-        rows, nnz = info["n_row_blocks"] * info["block_rows"], info["nnz_bcsr"]
-    return rows * 8 + nnz * (4 + e) + info["n_cols"] * N * e + rows * N * c
-
-
-def time_fn(torch, fn, steps, warmup, flush):
-    for _ in range(warmup):
-        fn()
-    torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-    stream = torch.cuda.current_stream()
-    for k in range(steps):
-        flush()
-        ev[k][0].record(stream)
-        fn()
-        ev[k][1].record(stream)
-    torch.cuda.synchronize()
-    return [a.elapsed_time(b) for a, b in ev]
-
-
-def run_other(args):
-    """The other four workloads, one JSON line each (same keys; not the default bench line)."""
-    import torch
-
-    import paper_2511_08158_gb300 as lp
-
-    torch.cuda.set_device(0)
-    lp.build()
-    lp.load()
     flush = make_flush(torch)
     hbm_peak, hbm_src = peaks()
-    wl = args.workload
-    out = {"metric": METRIC, "unit": "GFLOP/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "data": "synthetic (seeded)"}
-    if wl == "batched":
-        fmt = args.dtype or "f32"
-        mats = W.batched_mix(count=args.batch_count, seed=5)
-        As = [A for A, _ in mats]
-        Ns = [N for _, N in mats]
-        flops = sum(2.0 * A.nnz * N for A, N in mats)
-        e = 4 if fmt == "f32" else 2
-        nbytes = sum((A.n_rows + 1) * 8 + A.nnz * (4 + e) + A.n_cols * N * e + A.n_rows * N * 4 for A, N in mats)
-        dt = torch.float32 if fmt == "f32" else torch.bfloat16
-        Bs = [torch.randn((A.n_cols, N), device="cuda").to(dt) for A, N in mats]
-        Cs = [torch.empty((A.n_rows, N), device="cuda") for A, N in mats]
-        res = {}
-        for name, tau in (("autotuned", -1.0), ("csr_only", math.inf), ("hybrid_tau2", 2.0)):
-            t0 = time.perf_counter()
-            bp = lp.BatchedPlan(As, Ns, fmt, tau=tau)
-            build_s = time.perf_counter() - t0
-            st = time_fn(torch, lambda: bp.spmm(Bs, Cs), args.steps, args.warmup, flush)
-            ms = statistics.mean(st)
-            res[name] = {"gflops": flops / (ms * 1e-3) / 1e9, "ms_per_step": ms, "plan_build_s": build_s,
-                         "hbm_gbs": nbytes / (ms * 1e-3) / 1e9, **bp.info()}
-            bp.destroy()
-        # the same fixed-tau batch converted on the GPU from device-resident matrices
-        Ads = [W.CSR(A.n_rows, A.n_cols, torch.as_tensor(A.row_ptr).cuda(), torch.as_tensor(A.col_idx).cuda(),
-                     torch.as_tensor(A.vals).cuda()) for A in As]
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        bpd = lp.BatchedPlan(Ads, Ns, fmt, tau=2.0, build_on_device=True)
-        torch.cuda.synchronize()
-        dev_s = time.perf_counter() - t0
-        Cd2 = bpd.spmm(Bs)
-        Ch2 = lp.BatchedPlan(As, Ns, fmt, tau=2.0).spmm(Bs)
-        same = all(torch.equal(x, y) for x, y in zip(Ch2, Cd2))
-        pbd = {"tau": 2.0, "host_s": res["hybrid_tau2"]["plan_build_s"], "device_s": dev_s,
-               "identical_outputs": bool(same)}
-        bpd.destroy()
-        del Ads, Cd2, Ch2
-        best = res["autotuned"]
-        out.update(value=best["gflops"], ms_per_step=best["ms_per_step"], dtype=fmt,
-                   config={"workload": f"batched {args.batch_count} matrices (1,000-65,536 rows, uniform/banded/16x16 blocks), "
-                                       f"N in {{16,32,64,128}}, {fmt}", "nnz": int(sum(A.nnz for A in As)),
+    if args.workload == "batched":
+        line = run_batched(args, torch, lp, flush, rank, world, hbm_peak, hbm_src)
+        if not args.no_sub and rank == 0 and world == 1:
+            subs = {}
+            k = max(5, min(args.steps, 10))
+            for name, fmt in (("laplacian", None), ("rmat", "f16"), ("rmat", "bf16"), ("gcn", None),
+                              ("uniform", None)):
+                key = name if fmt is None else f"{name}_{fmt}"
+                subs[key] = run_single(name, args, torch, lp, flush, hbm_peak, hbm_src, k, 3, fmt=fmt,
+                                       full=(name == "laplacian"))
+                torch.cuda.empty_cache()
+            line["workloads"] = subs
+    else:
+        out = run_single(args.workload, args, torch, lp, flush, hbm_peak, hbm_src, args.steps, args.warmup,
+                         fmt=args.dtype, full=True)
+        line = {"metric": METRIC, "value": out["value"], "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": out["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": out["dtype"], "data": "synthetic (seeded)",
+                "config": {"workload": out["workload"], "nnz": out["nnz"], "N": out["N"],
                            "l2": "flushed before every timed step"},
-                   roofline={"bound": "hbm", "kernel": "batched_persistent", "achieved": best["hbm_gbs"],
-                             "peak": hbm_peak, "unit": "GB/s", "frac": best["hbm_gbs"] / hbm_peak,
-                             "traffic": None, "peak_source": hbm_src},
-                   variants=res, plan_build=pbd, gpu_launches=args.steps)
-        print(json.dumps(out), flush=True)
-        return
-    if wl == "rmat":
-        fmt = args.dtype or "f16"
-        A, B = W.rmat_graph(scale=20, samples_per_node=8, seed=3, N=128)
-        N, e, c = 128, 2, 4
-        X = torch.as_tensor(B, dtype=torch.float32).cuda()
-        Bd, sc = lp.cast_scaled(X, fmt)
-        desc = f"R-MAT 2^20 (a=0.57,b=0.19,c=0.19), avg degree 16, N=128, {fmt} with per-column scaling"
-    elif wl == "mixed":
-        fmt = args.dtype or "f32"
-        A, B = W.block_mix(n=1 << 20, N=64)
-        N, e, c = 64, (4 if fmt == "f32" else 2), 4
-        if fmt == "f32":
-            Bd, sc = torch.as_tensor(B, dtype=torch.float32).cuda(), None
-        else:
-            Bd, sc = lp.cast_scaled(torch.as_tensor(B, dtype=torch.float32).cuda(), fmt)
-        desc = (f"block mix 2^20: half the 16-row blocks two dense 16x16 blocks, the rest 16 uniform "
-                f"columns per row, N=64, {fmt}")
-    elif wl == "uniform":
-        fmt = "f32"
-        A, B = W.uniform_rows(2000, 10, 32, seed=1)
-        N, e, c = 32, 4, 4
-        Bd, sc = torch.as_tensor(B, dtype=torch.float32).cuda(), None
-        desc = "uniform 2,000 x 2,000, 10 nnz/row, N=32, f32"
-    else:  # gcn: forward
-        fmt = "f32"
-        A, X, dY = W.gcn_graph(scale=18, samples_per_node=16, seed=4, N=256)
-        A = W.CSR(A.n_rows, A.n_cols, A.row_ptr, A.col_idx, A.vals.astype(np.float32))
-        N, e, c = 256, 4, 4
-        Bd, sc = torch.as_tensor(X, dtype=torch.float32).cuda(), None
-        desc = "GCN layer: R-MAT 2^18 + I, D^-1/2 (A+I) D^-1/2, N=256, f32 (forward, and backward below)"
-    flops = 2.0 * A.nnz * N
-    Cd = torch.empty((A.n_rows, N), dtype=torch.float32, device="cuda")
-    res = {}
-    plans = {}
-    for name, tau in (("autotuned", -1.0), ("csr_only", math.inf), ("hybrid_tau2", 2.0), ("bcsr_only", 0.0)):
-        p = lp.Plan(A, N, fmt, tau=tau, want_backward=(wl == "gcn" and name == "autotuned"))
-        plans[name] = p
-        torch.cuda.nvtx.range_push(f"variant:{name}")  # lets a profiler select one variant's launches
-        st = time_fn(torch, lambda: p.spmm(Bd, Cd, col_scale=sc), args.steps, args.warmup, flush)
-        torch.cuda.nvtx.range_pop()
-        inf = p.info()
-        ms = statistics.mean(st)
-        res[name] = {"tau": inf["tau"], "gflops": flops / (ms * 1e-3) / 1e9, "ms_per_step": ms,
-                     "bcsr_row_blocks": inf["n_row_blocks"], "nnz_bcsr": inf["nnz_bcsr"]}
-    build_cmp = plan_build_compare(torch, lp, A, N, fmt, 2.0)
-    p = plans["autotuned"]
-    inf = p.info()
-    step, csr, bcsr = time_plan(torch, p, Bd, Cd, args.steps, args.warmup, flush) if sc is None else (
-        None, None, None)
-    if step is None:
-        step = time_fn(torch, lambda: p.spmm(Bd, Cd, col_scale=sc), args.steps, args.warmup, flush)
-        csr, bcsr = step, [0.0]
-    ms = statistics.mean(step)
-    csr_ms, bcsr_ms = statistics.mean(csr), statistics.mean(bcsr)
-    part = "csr" if csr_ms >= bcsr_ms else "bcsr"
-    pb = part_bytes(inf, N, e, c, part)
-    ach = pb / (max(csr_ms, bcsr_ms) * 1e-3) / 1e9
-    alg = (A.n_rows + 1) * 8 + A.nnz * (4 + e) + A.n_cols * N * e + A.n_rows * N * c
-    out.update(value=flops / (ms * 1e-3) / 1e9, ms_per_step=ms, dtype=fmt,
-               config={"workload": desc, "nnz": int(A.nnz), "N": N, "l2": "flushed before every timed step"},
-               roofline={"bound": "hbm", "kernel": f"{part} part", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": ach / hbm_peak, "traffic": None, "peak_source": hbm_src},
-               hbm={"alg_bytes_per_step": alg, "achieved_gbs": alg / (ms * 1e-3) / 1e9,
-                    "frac_of_measured": alg / (ms * 1e-3) / 1e9 / hbm_peak},
-               variants=res, part_ms={"csr": csr_ms, "bcsr": bcsr_ms}, plan_build=build_cmp,
-               gpu_launches=launches_per_step(inf) * args.steps)
-    if wl == "gcn":
-        dYd = torch.as_tensor(dY, dtype=torch.float32).cuda()
-        st = time_fn(torch, lambda: p.backward(dYd, Bd), args.steps, args.warmup, flush)
-        bms = statistics.mean(st)
-        out["backward"] = {"ms_per_step": bms, "gflops": 2 * flops / (bms * 1e-3) / 1e9,
-                           "what": "dX = A^T dY (transposed hybrid plan) + dvals = SDDMM(dY, X^T)"}
-    print(json.dumps(out), flush=True)
+                "roofline": out["roofline"], "detail": out,
+                "gpu_launches": out["gpu_launches_per_step"] * args.steps}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
-    elif args.workload != "laplacian":
-        run_other(args)
     else:
         run_loops(args)
 

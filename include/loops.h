@@ -197,6 +197,18 @@ loops_status loops_plan_device(const loops_csr* A, int64_t N, loops_dtype dtype,
  * has no counterpart. Process-wide; not meant to be armed while other threads build plans. */
 int64_t loops_test_fail_alloc(int64_t n);
 
+/* Test hook for the bounded waits (not for production use): kernels launched from now on give
+ * up each shared-memory barrier wait of the F16/BF16 BCSR kernel after `polls` unsuccessful
+ * polls (0: at once), instead of the default 2^24. A wait that gives up sets the plan's error
+ * word (loops_plan_check then returns LOOPS_ERR_TIMEOUT), lets the copies already in flight
+ * into its CTA's shared memory land (with its own bound), and skips that CTA's store: the C
+ * rows of its block are then not written (or, for a block cut into several units, are summed
+ * from partials this call did not write) and must not be used. polls < 0 restores the
+ * default. Returns
+ * the previous limit. Process-wide. The paper has no counterpart: it is the failure-detection
+ * path of the GPU kernels, exercised without faulting or hanging the device. */
+int64_t loops_test_wait_limit(int64_t polls);
+
 /* Release a plan and its device memory (synchronises the device first). NULL is a no-op. A
  * handle that is not a live plan (never returned, or already destroyed) gives
  * LOOPS_ERR_STATE here and in every other call, without its memory being read. */
@@ -266,6 +278,20 @@ loops_status loops_spmm_backward(loops_plan_t plan, const void* dC, int64_t lddc
                                  int64_t ldb, void* dB, int64_t lddb, void* dvals,
                                  loops_stream_t stream);
 
+/* Backward with per-column power-of-two scales for the 16-bit dtypes (the precision pattern of
+ * loops_spmm_scaled applied to the gradients; the paper's FP16 mode has no backward):
+ * the true operands are dC diag(dc_scale) and B diag(b_scale), where dc_scale and b_scale
+ * (device f32[N], each optional, NULL = all ones) typically come from loops_cast_scaled, so
+ * that small or large gradients keep their precision in F16/BF16. Returns the true gradients:
+ *   dB = (A^T . dC) diag(dc_scale)
+ *   dvals[k] = sum_n dC[i_k, n] B[j_k, n] dc_scale[n] b_scale[n]  (in f32).
+ * Scales with F64/F32 plans give LOOPS_ERR_INVALID_ARG. Otherwise as loops_spmm_backward,
+ * which is this call with both scales NULL. */
+loops_status loops_spmm_backward_scaled(loops_plan_t plan, const void* dC, int64_t lddc,
+                                        const float* dc_scale, const void* B, int64_t ldb,
+                                        const float* b_scale, void* dB, int64_t lddb, void* dvals,
+                                        loops_stream_t stream);
+
 /* Per-column power-of-two scaling and cast for the 16-bit dtypes:
  *   s_j = 2^ceil(log2 max_i |X_ij|) (1 for an all-zero column), Y_ij = round(X_ij / s_j).
  * X: device f32, rows x cols (ldx); Y: device, y_dtype (LOOPS_F16 or LOOPS_BF16), ldy;
@@ -277,7 +303,10 @@ loops_status loops_cast_scaled(const float* X, int64_t rows, int64_t cols, int64
 /* Profiling hook: events[0..3] are caller-owned cudaEvent_t handles (timing enabled). Every
  * later loops_spmm* call on this plan records events[0]/events[1] around the CSR-part
  * launches (on the call's stream) and events[2]/events[3] around the BCSR-part launch (on the
- * stream that runs it), back to back when a part is empty. NULL disables the hook. Host only. */
+ * stream that runs it), back to back when a part is empty. For a batched plan the events are
+ * recorded inside its captured graph (which is rebuilt): events[0]/events[1] around the
+ * persistent kernel, events[2]/events[3] around the launches that add partial sums. NULL
+ * disables the hook. Host only. */
 loops_status loops_plan_set_timing_events(loops_plan_t plan, void* const* events);
 
 /* Read and clear the plan's device error word (synchronises `stream`): LOOPS_OK, or
@@ -313,9 +342,41 @@ loops_status loops_spmm_batched(loops_plan_t plan, const void* const* Bs, const 
                                 void* const* Cs, const int64_t* ldcs, const float* const* col_scales,
                                 loops_stream_t stream);
 
+/* End-to-end batched SpMM with HOST buffers: copies every B_m (host, n_cols x N_m, ldbs[m],
+ * in the plan dtype; pinned memory makes the copies asynchronous and fast) into one
+ * plan-owned device staging area, runs the batch (loops_spmm_batched, no column scales),
+ * copies every C_m (f32, n_rows x N_m, ldcs[m]) back to the host and synchronises `stream`.
+ * The staging area (all B and C of the batch, dense) is allocated on the first call and kept
+ * until the plan is destroyed. No counterpart in the paper (its operands never leave the
+ * CPU's memory). */
+loops_status loops_spmm_batched_host(loops_plan_t plan, const void* const* Bs_host, const int64_t* ldbs,
+                                     void* const* Cs_host, const int64_t* ldcs, loops_stream_t stream);
+
 /* Counts of a batched plan: matrices, tasks of the persistent launch, tuned tau and B_r. */
 loops_status loops_plan_batched_info(loops_plan_t plan, int32_t* count, int64_t* n_tasks, double* tau,
                                      int32_t* block_rows);
+
+/* Totals of a batched plan (loops_plan_batched_stats). */
+typedef struct {
+  int32_t count;           /* matrices */
+  int32_t block_rows;      /* B_r of the BCSR tasks */
+  double tau;              /* the split threshold, or NaN when the matrices use different ones */
+  int64_t n_tasks;         /* tasks of the persistent launches */
+  int32_t n_kernels;       /* library kernels launched by one loops_spmm_batched call */
+  int32_t n_classes;       /* task classes, one persistent kernel each */
+  int64_t n_split_rows;    /* CSR rows cut into segments (their sums are a follow-up launch) */
+  int64_t n_split_blocks;  /* BCSR blocks cut into units (likewise) */
+  int64_t n_rows, nnz, nnz_bcsr;
+  int64_t device_bytes;    /* device memory owned by the plan (staging areas included) */
+  int32_t reserved[8];
+} loops_batched_info;
+
+/* Totals of a batched plan, for reporting (host only, no device access). */
+loops_status loops_plan_batched_stats(loops_plan_t plan, loops_batched_info* out);
+
+/* The loops_plan_info of matrix m (0 <= m < count) of a batched plan: its threshold, tile
+ * height and the sizes of its two parts, as the batch's autotuner left them. Host only. */
+loops_status loops_plan_batched_matrix_info(loops_plan_t plan, int32_t m, loops_plan_info* out);
 
 /* ---------------------------------------------------------------------------------------- */
 /* Allocation-free CSR SpMM. The paper has no counterpart: it serves callers that must not

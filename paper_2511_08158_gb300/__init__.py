@@ -34,7 +34,9 @@ EXPORTED = ["loops_version", "loops_status_str", "loops_last_error", "loops_plan
             "loops_plan_check", "loops_plan_set_timing_events", "loops_plan_set_values",
             "loops_csr_spmm_noalloc", "loops_plan_batched", "loops_spmm_batched", "loops_plan_batched_info",
             "loops_spmm_host_async", "loops_spmm_host_flush", "loops_plan_device",
-            "loops_plan_batched_device", "loops_test_fail_alloc"]
+            "loops_plan_batched_device", "loops_test_fail_alloc", "loops_spmm_backward_scaled",
+            "loops_test_wait_limit", "loops_spmm_batched_host", "loops_plan_batched_stats",
+            "loops_plan_batched_matrix_info"]
 
 
 class LoopsError(RuntimeError):
@@ -65,6 +67,14 @@ class _Info(ctypes.Structure):
                 ("n_split_rows", ctypes.c_int64), ("n_segments", ctypes.c_int64),
                 ("n_subnormal_vals", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
                 ("r_boundary", ctypes.c_int64), ("tile_min", ctypes.c_int64)]
+
+
+class _BatchedInfo(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int32), ("block_rows", ctypes.c_int32), ("tau", ctypes.c_double),
+                ("n_tasks", ctypes.c_int64), ("n_kernels", ctypes.c_int32), ("n_classes", ctypes.c_int32),
+                ("n_split_rows", ctypes.c_int64), ("n_split_blocks", ctypes.c_int64), ("n_rows", ctypes.c_int64),
+                ("nnz", ctypes.c_int64), ("nnz_bcsr", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+                ("reserved", ctypes.c_int32 * 8)]
 
 
 class _Part(ctypes.Structure):
@@ -106,6 +116,8 @@ def load():
     L.loops_plan.argtypes = [ctypes.POINTER(_Csr), i64, ctypes.c_int, ctypes.POINTER(_Opts), vp, ctypes.POINTER(vp)]
     L.loops_test_fail_alloc.argtypes = [i64]
     L.loops_test_fail_alloc.restype = i64
+    L.loops_test_wait_limit.argtypes = [i64]
+    L.loops_test_wait_limit.restype = i64
     L.loops_plan_device.argtypes = [ctypes.POINTER(_Csr), i64, ctypes.c_int, ctypes.POINTER(_Opts), vp,
                                     ctypes.POINTER(vp)]
     L.loops_plan_destroy.argtypes = [vp]
@@ -118,6 +130,7 @@ def load():
     L.loops_spmm_host_async.argtypes = [vp, vp, i64, vp, i64, vp]
     L.loops_spmm_host_flush.argtypes = [vp, vp]
     L.loops_spmm_backward.argtypes = [vp, vp, i64, vp, i64, vp, i64, vp, vp]
+    L.loops_spmm_backward_scaled.argtypes = [vp, vp, i64, vp, vp, i64, vp, vp, i64, vp, vp]
     L.loops_cast_scaled.argtypes = [vp, i64, i64, i64, ctypes.c_int, vp, i64, vp, vp]
     L.loops_plan_check.argtypes = [vp, vp]
     L.loops_plan_set_values.argtypes = [vp, vp, ctypes.c_int, vp]
@@ -128,13 +141,17 @@ def load():
                                      ctypes.POINTER(_Opts), vp, ctypes.POINTER(vp)]
     L.loops_spmm_batched.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(vp),
                                      ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(vp), vp]
+    L.loops_spmm_batched_host.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(vp),
+                                          ctypes.POINTER(ctypes.c_int64), vp]
+    L.loops_plan_batched_stats.argtypes = [vp, ctypes.POINTER(_BatchedInfo)]
+    L.loops_plan_batched_matrix_info.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(_Info)]
     L.loops_plan_batched_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64),
                                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)]
     L.loops_plan_set_timing_events.argtypes = [vp, ctypes.POINTER(ctypes.c_void_p)]
     for name in EXPORTED:
         fn = getattr(L, name)
         if name not in ("loops_version", "loops_status_str", "loops_last_error", "loops_plan_opts_default",
-                        "loops_partition_free"):
+                        "loops_partition_free", "loops_test_fail_alloc", "loops_test_wait_limit"):
             fn.restype = ctypes.c_int
     _lib = L
     return L
@@ -375,19 +392,27 @@ class Plan:
         """Make the stream wait for the last pipelined call's copy-out."""
         _check(self._L.loops_spmm_host_flush(self._h, _stream_handle(stream)))
 
-    def backward(self, dC, B, need_dB=True, need_dvals=True, stream=None):
-        """(dB, dvals) = (A^T . dC, <dC[i_k], B[j_k]> per stored entry in input order)."""
+    def backward(self, dC, B, need_dB=True, need_dvals=True, dc_scale=None, b_scale=None, stream=None):
+        """(dB, dvals) = (A^T . dC, <dC[i_k], B[j_k]> per stored entry in input order).
+        dc_scale / b_scale: optional f32[N] CUDA tensors of per-column scales of dC and B (16-bit
+        plans, e.g. from cast_scaled): the gradients of the true operands dC diag(dc_scale) and
+        B diag(b_scale) are returned (``loops_spmm_backward_scaled``)."""
         torch = _torch()
         self._check_dense(dC, self.n_rows, "dC")
+        for name, sc in (("dc_scale", dc_scale), ("b_scale", b_scale)):
+            if sc is not None and not (isinstance(sc, torch.Tensor) and sc.is_cuda and sc.dtype == torch.float32
+                                       and sc.dim() == 1 and sc.numel() == self.N and sc.is_contiguous()):
+                raise ValueError(f"{name} must be a contiguous float32 CUDA tensor of N entries")
         dB = dv = None
         if need_dB:
             dB = torch.empty((self.n_cols, self.N), dtype=self.out_dtype(), device=dC.device)
         if need_dvals:
             self._check_dense(B, self.n_cols, "B")
             dv = torch.empty((self.nnz,), dtype=self.out_dtype(), device=dC.device)
-        _check(self._L.loops_spmm_backward(
-            self._h, dC.data_ptr(), dC.stride(0), B.data_ptr() if B is not None else 0,
-            B.stride(0) if B is not None else self.N, dB.data_ptr() if dB is not None else 0,
+        _check(self._L.loops_spmm_backward_scaled(
+            self._h, dC.data_ptr(), dC.stride(0), 0 if dc_scale is None else dc_scale.data_ptr(),
+            B.data_ptr() if B is not None else 0, B.stride(0) if B is not None else self.N,
+            0 if b_scale is None else b_scale.data_ptr(), dB.data_ptr() if dB is not None else 0,
             dB.stride(0) if dB is not None else self.N, dv.data_ptr() if dv is not None else 0,
             _stream_handle(stream)))
         return dB, dv
@@ -427,6 +452,18 @@ class BatchedPlan:
                                                ctypes.byref(br)))
         return {"count": c.value, "n_tasks": t.value, "tau": tau.value, "block_rows": br.value}
 
+    def stats(self) -> dict:
+        """Totals of the plan (``loops_plan_batched_stats``)."""
+        inf = _BatchedInfo()
+        _check(self._L.loops_plan_batched_stats(self._h, ctypes.byref(inf)))
+        return {name: getattr(inf, name) for name, _ in _BatchedInfo._fields_ if name != "reserved"}
+
+    def matrix_info(self, m: int) -> dict:
+        """The plan info of matrix m (``loops_plan_batched_matrix_info``)."""
+        inf = _Info()
+        _check(self._L.loops_plan_batched_matrix_info(self._h, int(m), ctypes.byref(inf)))
+        return {name: getattr(inf, name) for name, _ in _Info._fields_}
+
     def spmm(self, Bs, Cs=None, col_scales=None, stream=None):
         torch = _torch()
         if Cs is None:
@@ -442,6 +479,30 @@ class BatchedPlan:
             sp = (ctypes.c_void_p * n)(*[0 if s is None else s.data_ptr() for s in col_scales])
         _check(self._L.loops_spmm_batched(self._h, bp, lb, cp, lc, sp, _stream_handle(stream)))
         return Cs
+
+    def spmm_host(self, Bs_host, Cs_host, stream=None):
+        """End-to-end batch with host (ideally pinned) CPU tensors: B_m copied in, the batch run,
+        C_m (f32) copied out; synchronises (``loops_spmm_batched_host``)."""
+        n = max(1, self.count)
+        for (r, c), N, B, C in zip(self.shapes, self.Ns, Bs_host, Cs_host):
+            if B.is_cuda or C.is_cuda or B.dim() != 2 or C.dim() != 2 or B.shape != (c, N) or C.shape != (r, N) \
+                    or B.stride(1) != 1 or C.stride(1) != 1:
+                raise ValueError("host operands must be CPU tensors of n_cols x N and n_rows x N, unit column stride")
+        bp = (ctypes.c_void_p * n)(*[B.data_ptr() for B in Bs_host])
+        cp = (ctypes.c_void_p * n)(*[C.data_ptr() for C in Cs_host])
+        lb = (ctypes.c_int64 * n)(*[B.stride(0) for B in Bs_host])
+        lc = (ctypes.c_int64 * n)(*[C.stride(0) for C in Cs_host])
+        _check(self._L.loops_spmm_batched_host(self._h, bp, lb, cp, lc, _stream_handle(stream)))
+        return Cs_host
+
+    def set_timing_events(self, events):
+        """events: 4 raw cudaEvent_t handles recorded around the persistent kernel ([0], [1]) and
+        the partial-sum launches ([2], [3]) of every later call, or None to stop."""
+        if events is None:
+            _check(self._L.loops_plan_set_timing_events(self._h, None))
+            return
+        arr = (ctypes.c_void_p * 4)(*[ctypes.c_void_p(int(e)) for e in events])
+        _check(self._L.loops_plan_set_timing_events(self._h, arr))
 
     def destroy(self):
         if getattr(self, "_h", None) is not None and self._h.value:
@@ -470,13 +531,38 @@ def cast_scaled(X, dtype: str = "f16", stream=None):
 
 
 def csr_spmm_noalloc(row_ptr, col_idx, vals, n_cols, B, C, stream=None):
-    """C = A . B from device CSR tensors (int64 row_ptr, int32 col_idx, vals of B's dtype)
-    without any device allocation (``loops_csr_spmm_noalloc``); C must be preallocated."""
+    """C = A . B from device CSR tensors without any device allocation
+    (``loops_csr_spmm_noalloc``). row_ptr: int64 [n_rows + 1]; col_idx: int32 [nnz]; vals: nnz
+    values in B's dtype (float64, float32, float16 or bfloat16); B: n_cols x N; C: n_rows x N,
+    preallocated, float64 for float64 inputs and float32 for every other input dtype. All on
+    one CUDA device, 1-D arrays contiguous, B and C with unit column stride."""
     torch = _torch()
-    dt = {torch.float64: F64, torch.float32: F32, torch.float16: F16, torch.bfloat16: BF16}[B.dtype]
+    dts = {torch.float64: F64, torch.float32: F32, torch.float16: F16, torch.bfloat16: BF16}
+    for name, t in (("row_ptr", row_ptr), ("col_idx", col_idx), ("vals", vals), ("B", B), ("C", C)):
+        if not isinstance(t, torch.Tensor):
+            raise TypeError(f"{name} must be a torch tensor")
+    if B.dtype not in dts:
+        raise TypeError("B must be float64, float32, float16 or bfloat16")
+    c_dtype = torch.float64 if B.dtype == torch.float64 else torch.float32
+    if row_ptr.dtype != torch.int64 or row_ptr.dim() != 1 or not row_ptr.is_contiguous() or row_ptr.numel() < 1:
+        raise TypeError("row_ptr must be a contiguous 1-D int64 tensor of n_rows + 1 entries")
+    if col_idx.dtype != torch.int32 or col_idx.dim() != 1 or not col_idx.is_contiguous():
+        raise TypeError("col_idx must be a contiguous 1-D int32 tensor")
+    if vals.dtype != B.dtype or vals.dim() != 1 or not vals.is_contiguous() or vals.numel() != col_idx.numel():
+        raise TypeError("vals must be a contiguous 1-D tensor of B's dtype with one value per column index")
+    n_rows = row_ptr.numel() - 1
+    if B.dim() != 2 or B.shape[0] != int(n_cols) or B.stride(1) != 1:
+        raise ValueError("B must be n_cols x N with unit column stride")
+    N = B.shape[1]
+    if C.dtype != c_dtype or C.dim() != 2 or C.shape[0] != n_rows or C.shape[1] != N or C.stride(1) != 1:
+        raise ValueError(f"C must be a {c_dtype} tensor of n_rows x N with unit column stride")
+    if not all(t.is_cuda for t in (row_ptr, col_idx, vals, B, C)):
+        raise TypeError("all operands must be CUDA tensors")
+    if len({t.device for t in (row_ptr, col_idx, vals, B, C)}) != 1:
+        raise ValueError("all operands must be on one device")
     _check(load().loops_csr_spmm_noalloc(
-        row_ptr.numel() - 1, n_cols, col_idx.numel(), row_ptr.data_ptr(), col_idx.data_ptr(), vals.data_ptr(), dt,
-        B.data_ptr(), B.stride(0), B.shape[1], C.data_ptr(), C.stride(0), _stream_handle(stream)))
+        n_rows, int(n_cols), col_idx.numel(), row_ptr.data_ptr(), col_idx.data_ptr(), vals.data_ptr(),
+        dts[B.dtype], B.data_ptr(), B.stride(0), N, C.data_ptr(), C.stride(0), _stream_handle(stream)))
     return C
 
 
@@ -486,24 +572,36 @@ def _autograd_fn():
     class LoopsSpMM(torch.autograd.Function):
         """C = A(vals) . B with the plan's pattern. Backward: dB = A^T . dC (transposed hybrid
         SpMM), dvals = SDDMM(dC, B^T) on A's pattern. The forward refreshes the plan's stored
-        values from ``vals`` on the device (plan built with want_backward)."""
+        values from ``vals`` on the device (plan built with want_backward); ``vals`` is saved
+        for the backward, which stores it into the plan again, so another forward on the same
+        plan in between (shared weights) does not change this call's gradients, and autograd's
+        version check refuses an in-place edit of ``vals`` after the forward. For FP16/BF16
+        plans dC (f32) is scaled per column by a power of two before its cast (as the forward
+        operands of loops_spmm_scaled are), and the scales are undone on dB and dvals."""
 
         @staticmethod
         def forward(ctx, vals, B, plan):
             ctx.plan = plan
-            ctx.save_for_backward(B)
+            ctx.save_for_backward(vals, B)
             plan.set_values(vals.detach())
             return plan.spmm(B.contiguous())
 
         @staticmethod
         def backward(ctx, dC):
-            (B,) = ctx.saved_tensors
+            vals, B = ctx.saved_tensors
             plan = ctx.plan
-            dC = dC.to(plan.in_dtype()).contiguous()
+            plan.set_values(vals.detach())
+            dc_scale = None
+            if plan.dtype in (F16, BF16):
+                dC, dc_scale = cast_scaled(dC.float().contiguous(), plan.dtype_name)
+            else:
+                dC = dC.to(plan.in_dtype()).contiguous()
             dB, dv = plan.backward(dC, B.contiguous(), need_dB=ctx.needs_input_grad[1],
-                                   need_dvals=ctx.needs_input_grad[0])
+                                   need_dvals=ctx.needs_input_grad[0], dc_scale=dc_scale)
             if dB is not None:
                 dB = dB.to(B.dtype)
+            if dv is not None:
+                dv = dv.to(vals.dtype)
             return dv, dB, None
 
     return LoopsSpMM

@@ -248,15 +248,28 @@ __device__ __forceinline__ void hmma_block(const BatchDesc& d, int64_t u, T* sB,
   }
 }
 
+// Next task of a warp: with `counter` (zeroed before the launch) the warp takes the next
+// unclaimed task of the list, so all warps stay within a short window of it (the list is
+// ordered matrix by matrix, and the window's B operands stay in L2); without it, warp w takes
+// tasks w, w + W, w + 2W, ... Every task writes its own outputs, so either way the result does
+// not depend on which warp runs which task.
+__device__ __forceinline__ int64_t next_task(unsigned long long* counter, int64_t prev, int64_t W, int lane) {
+  if (counter == nullptr) return prev + W;
+  unsigned long long t = 0;
+  if (lane == 0) t = atomicAdd(counter, 1ull);
+  return (int64_t)__shfl_sync(0xffffffffu, t, 0);
+}
+
 template <class Tr, int BR>
 __global__ void __launch_bounds__(256, LOOPS_BATCHED_MIN_BLOCKS) batched_persistent(const BatchDesc* __restrict__ descs,
                                                           const BatchTask* __restrict__ tasks, int64_t n_tasks,
-                                                          int smem_per_warp) {
+                                                          int smem_per_warp, unsigned long long* counter) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; t < n_tasks; t += W) {
+  const int64_t first = counter ? next_task(counter, 0, W, lane) : (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+  for (int64_t t = first; t < n_tasks; t = next_task(counter, t, W, lane)) {
     const BatchTask task = tasks[t];
     const BatchDesc& d = descs[task.m];
     if (task.kind == 2) {
@@ -325,9 +338,26 @@ cudaError_t launch_batched_t(const BatchLaunch& L, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
   }
+  // timing events become event nodes of the captured graph (external records)
+  auto rec = [&](int i) {
+    return L.tev ? cudaEventRecordWithFlags(L.tev[i], s, cudaEventRecordExternal) : cudaSuccess;
+  };
+  {
+    cudaError_t e = rec(0);
+    if (e != cudaSuccess) return e;
+  }
   if (L.n_tasks > 0) {
-    kern<<<L.grid, 256, smem, s>>>(L.descs, L.tasks, L.n_tasks, L.smem_per_warp);
+    if (L.counter) {
+      cudaError_t e = cudaMemsetAsync(L.counter, 0, sizeof(unsigned long long), s);
+      if (e != cudaSuccess) return e;
+    }
+    kern<<<L.grid, 256, smem, s>>>(L.descs, L.tasks, L.n_tasks, L.smem_per_warp, L.counter);
     cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  {
+    cudaError_t e = rec(1);
+    if (e == cudaSuccess) e = rec(2);
     if (e != cudaSuccess) return e;
   }
   if (L.n_splits > 0) {
@@ -337,9 +367,10 @@ cudaError_t launch_batched_t(const BatchLaunch& L, cudaStream_t s) {
   }
   if (L.n_bsplits > 0) {
     batched_bsplit_reduce<Tr><<<(unsigned)L.n_bsplits, 256, 0, s>>>(L.descs, L.bsplits);
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
   }
-  return cudaSuccess;
+  return rec(3);
 }
 
 }  // namespace

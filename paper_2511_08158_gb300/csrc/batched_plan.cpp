@@ -2,6 +2,7 @@
 // persistent kernel launch that is captured in a CUDA graph on the first call and replayed.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <functional>
 
@@ -22,6 +23,7 @@ struct BatchState {
   int2* d_bsplits = nullptr;
   int64_t n_tasks = 0, n_splits = 0, n_bsplits = 0;
   int grid = 0, smem_per_warp = 0;
+  unsigned long long* d_counter = nullptr;  // task counter of the dynamic schedule
   cudaStream_t cap = nullptr;         // capture stream
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -29,7 +31,22 @@ struct BatchState {
   bool copied_once = false;
   int64_t device_bytes = 0;
   int64_t total_nnz = 0, total_rows = 0;
+  cudaEvent_t tev[4] = {nullptr, nullptr, nullptr, nullptr};  // caller's timing events
+  bool timing = false;
+  // loops_spmm_batched_host: one device staging area (every B, then every C, dense rows)
+  void* stage = nullptr;
+  int64_t stage_bytes = 0;
 };
+
+void batch_set_timing(BatchState* b, const cudaEvent_t* ev) {
+  b->timing = ev != nullptr;
+  for (int i = 0; i < 4; ++i) b->tev[i] = ev ? ev[i] : nullptr;
+  // the next call captures the graph again, with or without the event nodes
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+}
 
 void destroy_batch(BatchState* b) {
   if (!b) return;
@@ -37,7 +54,7 @@ void destroy_batch(BatchState* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   if (b->h_desc) cudaFreeHost(b->h_desc);
-  void* ptrs[] = {b->d_desc, b->d_tasks, b->d_splits, b->d_bsplits};
+  void* ptrs[] = {b->d_desc, b->d_tasks, b->d_splits, b->d_bsplits, b->d_counter, b->stage};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (b->cap) cudaStreamDestroy(b->cap);
@@ -45,9 +62,25 @@ void destroy_batch(BatchState* b) {
   delete b;
 }
 
+// Library kernels one call launches, and the task classes (one persistent kernel each).
+int batch_classes(const BatchState* b) { return b->n_tasks > 0 ? 1 : 0; }
+int batch_kernels_per_call(const BatchState* b) {
+  return batch_classes(b) + (b->n_splits > 0) + (b->n_bsplits > 0);
+}
+
 namespace {
 
 int elems_per_16b(loops_dtype d) { return d == LOOPS_F32 ? 4 : 8; }
+
+// Schedule of the persistent batched launch: task order (1 matrix by matrix, 0 by cost) and
+// task claiming (1 dynamic, from a counter; 0 static round-robin). LOOPS_BATCH_ORDER and
+// LOOPS_BATCH_DYNAMIC in the environment override the defaults (for measurement).
+int env_int(const char* name, int dflt) {
+  const char* v = std::getenv(name);
+  return v && *v ? std::atoi(v) : dflt;
+}
+int batch_order() { return env_int("LOOPS_BATCH_ORDER", 1); }
+int batch_dynamic() { return env_int("LOOPS_BATCH_DYNAMIC", 1); }
 
 // Builds the sub-plan of matrix m for the given options, tile height and threshold.
 using SubBuilder = std::function<loops_status(int32_t m, const loops_plan_opts& o, int32_t br, double tau,
@@ -114,10 +147,16 @@ loops_status build_batch(const loops_csr* As, const int64_t* Ns, int32_t count, 
     for (int64_t sidx = 0; sidx < c.n_split; ++sidx) splits.push_back(make_int2(m, (int)sidx));
   }
   if (st) { destroy_batch(b); return st; }
-  // longest tasks first; warps take tasks round-robin
+  // Task order. Matrix by matrix (tasks of a matrix in decreasing cost): the warps then work
+  // on one or a few matrices at a time, whose B operands stay in L2 while their rows gather
+  // from them. Or (order 0) all tasks by decreasing cost, interleaving the matrices.
   std::vector<int64_t> idx(tasks.size());
   for (size_t i = 0; i < idx.size(); ++i) idx[i] = (int64_t)i;
-  std::stable_sort(idx.begin(), idx.end(), [&](int64_t x, int64_t y) { return cost[(size_t)x] > cost[(size_t)y]; });
+  const int order = batch_order();
+  std::stable_sort(idx.begin(), idx.end(), [&](int64_t x, int64_t y) {
+    if (order == 1 && tasks[(size_t)x].m != tasks[(size_t)y].m) return tasks[(size_t)x].m < tasks[(size_t)y].m;
+    return cost[(size_t)x] > cost[(size_t)y];
+  });
   std::vector<BatchTask> sorted(tasks.size());
   for (size_t i = 0; i < idx.size(); ++i) sorted[i] = tasks[(size_t)idx[i]];
   b->n_tasks = (int64_t)sorted.size();
@@ -137,6 +176,7 @@ loops_status build_batch(const loops_csr* As, const int64_t* Ns, int32_t count, 
   if (e == cudaSuccess && b->n_bsplits) e = dev_malloc((void**)&b->d_bsplits, sizeof(int2) * (size_t)b->n_bsplits);
   if (e == cudaSuccess && b->n_bsplits)
     e = cudaMemcpy(b->d_bsplits, bsplits.data(), sizeof(int2) * (size_t)b->n_bsplits, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && batch_dynamic()) e = dev_malloc((void**)&b->d_counter, sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_copied, cudaEventDisableTiming);
   if (e != cudaSuccess) { st = cuda_status(e, "batched plan setup"); destroy_batch(b); return st; }
@@ -186,6 +226,8 @@ cudaError_t run_batch(BatchState* b, cudaStream_t s) {
   L.n_bsplits = b->n_bsplits;
   L.grid = b->grid;
   L.smem_per_warp = b->smem_per_warp;
+  L.counter = b->d_counter;
+  L.tev = b->timing ? b->tev : nullptr;
   return launch_batched(b->dtype, b->br, L, s);
 }
 
@@ -334,6 +376,7 @@ static loops_status plan_batched(const loops_csr* As, const int64_t* Ns, int32_t
       ld[(size_t)m] = Ns[m];
     }
     st = cuda_status(e, "autotune buffers");
+    L2Flush flush;
     for (const Cand& c : cands) {
       if (st) break;
       loops_plan_opts oc = o;
@@ -342,7 +385,10 @@ static loops_status plan_batched(const loops_csr* As, const int64_t* Ns, int32_t
       if ((st = build_batch(As, Ns, count, dtype, oc, c.br, c.tau, sub, &b))) break;
       float ms = INFINITY;
       for (int it = 0; it < 5 && !st; ++it) {
-        if (it >= 2) cudaEventRecord(e0, s);
+        if (it >= 2) {
+          if ((st = cuda_status(flush.run(s), "L2 flush"))) break;
+          cudaEventRecord(e0, s);
+        }
         st = spmm_batch(b, Bs.data(), ld.data(), Cs.data(), ld.data(), nullptr, s);
         if (it >= 2) {
           cudaEventRecord(e1, s);
@@ -450,6 +496,72 @@ loops_status loops_spmm_batched(loops_plan_t p, const void* const* Bs, const int
   return spmm_batch(b, Bs, ldbs, Cs, ldcs, col_scales, (cudaStream_t)stream);
 }
 
+loops_status loops_spmm_batched_host(loops_plan_t p, const void* const* Bs_host, const int64_t* ldbs,
+                                     void* const* Cs_host, const int64_t* ldcs, loops_stream_t stream) {
+  clear_error();
+  NvtxScope nvtx("loops_spmm_batched_host");
+  loops_status st = check_plan(p);
+  if (st) return st;
+  if (!p->batch) { set_error("not a batched plan"); return LOOPS_ERR_STATE; }
+  BatchState* b = p->batch;
+  if (b->count && (!Bs_host || !Cs_host || !ldbs || !ldcs)) { set_error("NULL batch array"); return LOOPS_ERR_INVALID_ARG; }
+  const int64_t eb = b->dtype == LOOPS_F32 ? 4 : 2;
+  // staging layout: B of every matrix (n_cols x N, dense), then C of every matrix, each
+  // starting on a 256-byte boundary
+  std::vector<int64_t> boff((size_t)b->count), coff((size_t)b->count);
+  int64_t off = 0;
+  for (int32_t m = 0; m < b->count; ++m) {
+    const loops_plan_s* sp = b->subs[(size_t)m];
+    if (ldbs[m] < sp->N || ldcs[m] < sp->N || (!Bs_host[m] && sp->n_cols > 0) || (!Cs_host[m] && sp->n_rows > 0)) {
+      set_error("bad host operand of matrix " + std::to_string(m));
+      return LOOPS_ERR_INVALID_ARG;
+    }
+    boff[(size_t)m] = off;
+    off += (sp->n_cols * sp->N * eb + 255) / 256 * 256;
+  }
+  for (int32_t m = 0; m < b->count; ++m) {
+    const loops_plan_s* sp = b->subs[(size_t)m];
+    coff[(size_t)m] = off;
+    off += (sp->n_rows * sp->N * 4 + 255) / 256 * 256;
+  }
+  if (off > b->stage_bytes) {
+    if (b->stage) {
+      cudaDeviceSynchronize();
+      cudaFree(b->stage);
+      b->stage = nullptr;
+      b->stage_bytes = 0;
+    }
+    cudaError_t e = dev_malloc(&b->stage, (size_t)std::max<int64_t>(off, 256));
+    if (e != cudaSuccess) return cuda_status(e, "batched staging buffer");
+    b->stage_bytes = off;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<const void*> dB((size_t)b->count);
+  std::vector<void*> dC((size_t)b->count);
+  std::vector<int64_t> ldB((size_t)b->count), ldC((size_t)b->count);
+  char* base = static_cast<char*>(b->stage);
+  cudaError_t e = cudaSuccess;
+  for (int32_t m = 0; m < b->count && e == cudaSuccess; ++m) {
+    const loops_plan_s* sp = b->subs[(size_t)m];
+    dB[(size_t)m] = base + boff[(size_t)m];
+    dC[(size_t)m] = base + coff[(size_t)m];
+    ldB[(size_t)m] = ldC[(size_t)m] = sp->N;
+    if (sp->n_cols > 0)
+      e = cudaMemcpy2DAsync(base + boff[(size_t)m], (size_t)(sp->N * eb), Bs_host[m], (size_t)(ldbs[m] * eb),
+                            (size_t)(sp->N * eb), (size_t)sp->n_cols, cudaMemcpyHostToDevice, s);
+  }
+  if (e != cudaSuccess) return cuda_status(e, "copy of B to the device");
+  if ((st = spmm_batch(b, dB.data(), ldB.data(), dC.data(), ldC.data(), nullptr, s))) return st;
+  for (int32_t m = 0; m < b->count && e == cudaSuccess; ++m) {
+    const loops_plan_s* sp = b->subs[(size_t)m];
+    if (sp->n_rows > 0)
+      e = cudaMemcpy2DAsync(Cs_host[m], (size_t)(ldcs[m] * 4), base + coff[(size_t)m], (size_t)(sp->N * 4),
+                            (size_t)(sp->N * 4), (size_t)sp->n_rows, cudaMemcpyDeviceToHost, s);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return cuda_status(e, "copy of C to the host");
+}
+
 loops_status loops_plan_batched_info(loops_plan_t p, int32_t* count, int64_t* n_tasks, double* tau,
                                      int32_t* block_rows) {
   clear_error();
@@ -461,6 +573,40 @@ loops_status loops_plan_batched_info(loops_plan_t p, int32_t* count, int64_t* n_
   if (tau) *tau = p->batch->tau;
   if (block_rows) *block_rows = p->batch->br;
   return LOOPS_OK;
+}
+
+loops_status loops_plan_batched_stats(loops_plan_t p, loops_batched_info* out) {
+  clear_error();
+  loops_status st = check_plan(p);
+  if (st) return st;
+  if (!p->batch) { set_error("not a batched plan"); return LOOPS_ERR_STATE; }
+  if (!out) { set_error("out is NULL"); return LOOPS_ERR_INVALID_ARG; }
+  std::memset(out, 0, sizeof(*out));
+  const BatchState* b = p->batch;
+  out->count = b->count;
+  out->block_rows = b->br;
+  out->tau = b->tau;
+  for (const loops_plan_s* sp : b->subs)
+    if (!(sp->tau == b->subs[0]->tau)) out->tau = NAN;
+  out->n_tasks = b->n_tasks;
+  out->n_kernels = batch_kernels_per_call(b);
+  out->n_classes = batch_classes(b);
+  out->n_split_rows = b->n_splits;
+  out->n_split_blocks = b->n_bsplits;
+  out->n_rows = b->total_rows;
+  out->nnz = b->total_nnz;
+  out->nnz_bcsr = p->nnz_bcsr;
+  out->device_bytes = b->device_bytes + b->stage_bytes;
+  return LOOPS_OK;
+}
+
+loops_status loops_plan_batched_matrix_info(loops_plan_t p, int32_t m, loops_plan_info* out) {
+  clear_error();
+  loops_status st = check_plan(p);
+  if (st) return st;
+  if (!p->batch) { set_error("not a batched plan"); return LOOPS_ERR_STATE; }
+  if (m < 0 || m >= p->batch->count) { set_error("matrix index out of range"); return LOOPS_ERR_INVALID_ARG; }
+  return plan_info_of(p->batch->subs[(size_t)m], out);
 }
 
 }  // extern "C"

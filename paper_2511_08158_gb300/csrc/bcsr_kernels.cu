@@ -43,6 +43,7 @@ struct BcsrKArgs {
   int64_t N;
   int64_t n_rows;
   int32_t* err;
+  long long max_polls;     // bound of each mbarrier wait (kMaxWaitPolls unless a test lowers it)
 };
 
 // ------------------------------------------------------------------ F16 / BF16: m16n8k16
@@ -149,7 +150,7 @@ __global__ void __launch_bounds__(WARPS * 32) bcsr_hmma(BcsrKArgs a) {
     if (g + kStages - 1 < n_groups) issue(g + kStages - 1);
     if (!BULK) __syncthreads();
     const int s = g % kStages;
-    if (BULK && !mbar_wait_bounded(&bar[s], (uint32_t)((g / kStages) & 1), kMaxWaitPolls)) {
+    if (BULK && !mbar_wait_bounded(&bar[s], (uint32_t)((g / kStages) & 1), a.max_polls)) {
       failed = true;
       atomicOr(a.err, kErrWaitTimeout);
       continue;
@@ -517,6 +518,7 @@ cudaError_t launch_bcsr(const loops_plan_s* p, const BcsrDev& d, const DenseArgs
   a.N = da.N;
   a.n_rows = da.n_rows;
   a.err = p->d_error;
+  a.max_polls = wait_poll_limit();
   cudaError_t e = cudaErrorInvalidValue;
   switch (p->dtype) {
     case LOOPS_F64: e = launch_dmma(a, s); break;

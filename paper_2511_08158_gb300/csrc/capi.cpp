@@ -72,6 +72,11 @@ static bool alloc_should_fail() {
   return false;
 }
 
+// ------------------------------------------------------------------ wait-bound hook
+static std::atomic<int64_t> g_wait_polls{(int64_t)kMaxWaitPolls};
+
+long long wait_poll_limit() { return (long long)g_wait_polls.load(std::memory_order_relaxed); }
+
 cudaError_t dev_malloc_raw(void** p, size_t bytes) {
   if (alloc_should_fail()) {
     *p = nullptr;
@@ -412,6 +417,25 @@ static cudaError_t fill_finite(void* p, int64_t bytes, cudaStream_t s) {
   return cudaMemsetAsync(p, 0x3C, (size_t)bytes, s);
 }
 
+}  // namespace loops
+
+namespace loops {
+
+// Candidates are timed the way SpMM runs in a sequence of calls on fresh operands: with the
+// L2 holding none of them (a write of a buffer twice the L2 size before each timed call).
+L2Flush::L2Flush() {
+  if (dev_malloc(&buf, kL2FlushBytes) != cudaSuccess) {
+    buf = nullptr;
+    cudaGetLastError();
+  }
+}
+L2Flush::~L2Flush() {
+  if (buf) cudaFree(buf);
+}
+cudaError_t L2Flush::run(cudaStream_t s) {
+  return buf ? cudaMemsetAsync(buf, ++n & 0xff, kL2FlushBytes, s) : cudaSuccess;
+}
+
 // Autotuner (replaces the paper's Eq. 2/Eq. 3 CPU model): times C = A.B for candidate split
 // thresholds on synthetic B and keeps the fastest. Candidates that give the same row-block
 // split as an earlier one are skipped.
@@ -435,6 +459,7 @@ loops_status autotune_tau(const PlanBuilder& build, int64_t n_rows, int64_t n_co
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   loops_status st = cuda_status(e, "autotune setup");
+  L2Flush flush;
   double best = INFINITY;
   std::vector<std::pair<int64_t, int64_t>> seen;
   loops_plan_opts o;
@@ -453,6 +478,7 @@ loops_status autotune_tau(const PlanBuilder& build, int64_t n_rows, int64_t n_co
     for (int it = 0; it < 7 && !st; ++it) {
       if ((st = run_spmm(p, dB, N, nullptr, dC, N, s))) break;  // it 0, 1: warm-up
       if (it < 2) continue;
+      if ((st = cuda_status(flush.run(s), "L2 flush"))) break;
       cudaEventRecord(e0, s);
       st = run_spmm(p, dB, N, nullptr, dC, N, s);
       cudaEventRecord(e1, s);
@@ -488,6 +514,7 @@ loops_status model_boundary(const PlanBuilder& build, int64_t n_rows, int64_t n_
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   loops_status st = cuda_status(e, "model setup");
+  L2Flush flush;
   float t[2] = {INFINITY, INFINITY};
   for (int which = 0; which < 2 && !st; ++which) {
     loops_plan_opts o;
@@ -498,7 +525,10 @@ loops_status model_boundary(const PlanBuilder& build, int64_t n_rows, int64_t n_
     loops_plan_s* p = nullptr;
     if ((st = build(o, INFINITY, &p))) break;
     for (int it = 0; it < 7 && !st; ++it) {
-      if (it >= 2) cudaEventRecord(e0, s);
+      if (it >= 2) {
+        if ((st = cuda_status(flush.run(s), "L2 flush"))) break;
+        cudaEventRecord(e0, s);
+      }
       st = run_spmm(p, dB, N, nullptr, dC, N, s);
       if (it >= 2) {
         cudaEventRecord(e1, s);
@@ -736,6 +766,10 @@ loops_status loops_plan_device(const loops_csr* A, int64_t N, loops_dtype dtype,
   return LOOPS_OK;
 }
 
+int64_t loops_test_wait_limit(int64_t polls) {
+  return g_wait_polls.exchange(polls >= 0 ? polls : (int64_t)kMaxWaitPolls);
+}
+
 int64_t loops_test_fail_alloc(int64_t n) {
   const int64_t seen = g_alloc_seen.exchange(0);
   g_alloc_countdown.store(n > 0 ? n : 0);
@@ -757,6 +791,14 @@ loops_status loops_plan_info_get(loops_plan_t p, loops_plan_info* out) {
   clear_error();
   loops_status st = check_plan(p);
   if (st) return st;
+  return plan_info_of(p, out);
+}
+
+}  // extern "C"
+
+namespace loops {
+
+loops_status plan_info_of(const loops_plan_s* p, loops_plan_info* out) {
   if (!out) { set_error("out is NULL"); return LOOPS_ERR_INVALID_ARG; }
   std::memset(out, 0, sizeof(*out));
   out->dtype = p->dtype;
@@ -784,6 +826,10 @@ loops_status loops_plan_info_get(loops_plan_t p, loops_plan_info* out) {
     out->device_bytes += p->transposed->dev.device_bytes + p->transposed->other_bytes + p->transposed->vmap.bytes;
   return LOOPS_OK;
 }
+
+}  // namespace loops
+
+extern "C" {
 
 loops_status loops_plan_export(loops_plan_t p, loops_partition* out) {
   clear_error();
@@ -1001,8 +1047,9 @@ loops_status loops_spmm_host_flush(loops_plan_t p, loops_stream_t stream) {
                      "host pipeline flush");
 }
 
-loops_status loops_spmm_backward(loops_plan_t p, const void* dC, int64_t lddc, const void* B, int64_t ldb,
-                                 void* dB, int64_t lddb, void* dvals, loops_stream_t stream) {
+loops_status loops_spmm_backward_scaled(loops_plan_t p, const void* dC, int64_t lddc, const float* dc_scale,
+                                        const void* B, int64_t ldb, const float* b_scale, void* dB, int64_t lddb,
+                                        void* dvals, loops_stream_t stream) {
   clear_error();
   NvtxScope nvtx("loops_spmm_backward");
   loops_status st = check_single(p);
@@ -1011,17 +1058,29 @@ loops_status loops_spmm_backward(loops_plan_t p, const void* dC, int64_t lddc, c
     set_error("plan was built without want_backward");
     return LOOPS_ERR_STATE;
   }
+  if ((dc_scale || b_scale) && p->dtype != LOOPS_F16 && p->dtype != LOOPS_BF16) {
+    set_error("dc_scale and b_scale are only defined for the 16-bit dtypes");
+    return LOOPS_ERR_INVALID_ARG;
+  }
   if ((st = check_dense(dC, p->n_rows, p->N, lddc, "dC"))) return st;
   cudaStream_t s = (cudaStream_t)stream;
   if (dB) {
     if ((st = check_dense(dB, p->n_cols, p->N, lddb, "dB"))) return st;
-    if ((st = run_spmm(p->transposed, dC, lddc, nullptr, dB, lddb, s))) return st;
+    // dB = A^T . (dC diag(dc_scale)) = (A^T . dC) diag(dc_scale): the column scales of the
+    // transposed SpMM's epilogue
+    if ((st = run_spmm(p->transposed, dC, lddc, dc_scale, dB, lddb, s))) return st;
   }
   if (dvals && p->nnz > 0) {
     if ((st = check_dense(B, p->n_cols, p->N, ldb, "B"))) return st;
-    if ((st = cuda_status(launch_sddmm(p, dC, lddc, B, ldb, dvals, s), "SDDMM launch"))) return st;
+    if ((st = cuda_status(launch_sddmm(p, dC, lddc, B, ldb, dvals, dc_scale, b_scale, s), "SDDMM launch")))
+      return st;
   }
   return LOOPS_OK;
+}
+
+loops_status loops_spmm_backward(loops_plan_t p, const void* dC, int64_t lddc, const void* B, int64_t ldb,
+                                 void* dB, int64_t lddb, void* dvals, loops_stream_t stream) {
+  return loops_spmm_backward_scaled(p, dC, lddc, nullptr, B, ldb, nullptr, dB, lddb, dvals, stream);
 }
 
 loops_status loops_cast_scaled(const float* X, int64_t rows, int64_t cols, int64_t ldx, loops_dtype yd,
@@ -1037,11 +1096,12 @@ loops_status loops_cast_scaled(const float* X, int64_t rows, int64_t cols, int64
 
 loops_status loops_plan_set_timing_events(loops_plan_t p, void* const* events) {
   clear_error();
-  loops_status st = check_single(p);
+  loops_status st = check_plan(p);
   if (st) return st;
   if (!events) {
     p->timing = false;
     for (auto& ev : p->tev) ev = nullptr;
+    if (p->batch) batch_set_timing(p->batch, nullptr);
     return LOOPS_OK;
   }
   for (int i = 0; i < 4; ++i) {
@@ -1049,6 +1109,7 @@ loops_status loops_plan_set_timing_events(loops_plan_t p, void* const* events) {
     p->tev[i] = (cudaEvent_t)events[i];
   }
   p->timing = true;
+  if (p->batch) batch_set_timing(p->batch, p->tev);
   return LOOPS_OK;
 }
 

@@ -193,11 +193,18 @@ extern "C" loops_status loops_csr_spmm_noalloc(int64_t n_rows, int64_t n_cols, i
   }
   const int64_t n_chunks = nnz > 0 ? (nnz + kChunk - 1) / kChunk : 1;
   const int64_t acc_bytes = dtype == LOOPS_F64 ? 8 : 4;
-  const int64_t need = 2 * n_chunks * N * acc_bytes;
-  if (need > (int64_t)LOOPS_NOALLOC_SCRATCH_BYTES) {
-    set_error("problem too large for the allocation-free path: needs " + std::to_string(need) +
-              " bytes of scratch (2 * ceil(nnz / 128) * N * accumulator size), the static array holds " +
+  // the scratch test divides instead of multiplying, so no product of caller sizes can wrap
+  const int64_t per_chunk = 2 * acc_bytes;  // head and tail accumulators per chunk and column
+  if (N > (int64_t)LOOPS_NOALLOC_SCRATCH_BYTES / per_chunk ||
+      n_chunks > (int64_t)LOOPS_NOALLOC_SCRATCH_BYTES / (per_chunk * N)) {
+    set_error("problem too large for the allocation-free path: its scratch needs 2 * ceil(nnz / 128) * N * " +
+              std::to_string((long long)acc_bytes) + " bytes (nnz " + std::to_string((long long)nnz) + ", N " +
+              std::to_string((long long)N) + "), the static array holds " +
               std::to_string((long long)LOOPS_NOALLOC_SCRATCH_BYTES));
+    return LOOPS_ERR_UNSUPPORTED;
+  }
+  if ((N + 31) / 32 > 65535 || (n_chunks * 32 + 255) / 256 > 0x7fffffffLL) {
+    set_error("N too large for the allocation-free path's launch shape (at most 65535 * 32 columns)");
     return LOOPS_ERR_UNSUPPORTED;
   }
   int dev = 0;

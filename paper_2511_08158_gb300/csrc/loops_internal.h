@@ -45,6 +45,8 @@ constexpr int32_t kErrWaitTimeout = 1;
 
 // Bound on mbarrier polls before a kernel records kErrWaitTimeout and leaves its loop.
 constexpr long long kMaxWaitPolls = 1ll << 24;
+// The bound kernels launched now use: kMaxWaitPolls, or what loops_test_wait_limit set.
+long long wait_poll_limit();
 
 // ------------------------------------------------------------------ dtypes
 inline int dense_elem_bytes(loops_dtype d) {  // B / dC element size
@@ -257,6 +259,9 @@ struct BatchLaunch {
   int64_t n_bsplits;
   int grid;
   int smem_per_warp;
+  unsigned long long* counter;         // task counter of the dynamic schedule (null: static)
+  const cudaEvent_t* tev;              // optional timing events: [0]/[1] around the persistent
+                                       // kernel, [2]/[3] around the partial-sum launches
 };
 
 struct BatchState;
@@ -347,7 +352,7 @@ cudaError_t launch_csr(const loops_plan_s* p, const CsrDev& d, const DenseArgs& 
                        cudaStream_t s);
 cudaError_t launch_bcsr(const loops_plan_s* p, const BcsrDev& d, const DenseArgs& a, cudaStream_t s);
 cudaError_t launch_sddmm(const loops_plan_s* p, const void* dC, int64_t lddc, const void* B,
-                         int64_t ldb, void* dvals, cudaStream_t s);
+                         int64_t ldb, void* dvals, const float* dc_scale, const float* b_scale, cudaStream_t s);
 cudaError_t launch_batched(loops_dtype dtype, int32_t br, const BatchLaunch& L, cudaStream_t s);
 int batched_grid_blocks(loops_dtype dtype, int32_t br, int smem_per_warp);
 
@@ -360,6 +365,12 @@ loops_status cuda_status(cudaError_t e, const char* what);
 loops_status resolve_block_rows(loops_dtype dtype, const loops_plan_opts& o, int32_t* br);
 loops_status check_plan(loops_plan_t p);
 void destroy_batch(BatchState* b);
+int batch_classes(const BatchState* b);
+int batch_kernels_per_call(const BatchState* b);
+// Fills *out from a plan (single or a batch's sub-plan).
+loops_status plan_info_of(const loops_plan_s* p, loops_plan_info* out);
+// Timing events of a batched plan (null: none); the captured graph is rebuilt with them.
+void batch_set_timing(BatchState* b, const cudaEvent_t* ev);
 
 // ------------------------------------------------------------------ device-side plan build
 // A CSR matrix whose arrays are in device memory (values binary64, or binary32 when vals_f32).
@@ -389,6 +400,19 @@ loops_status make_plan_device(const DevCsrIn& A, const int64_t* remap, double sc
 // Host copies of the work-item offsets and unit lengths of a device-built plan (the batched
 // task list is formed from them on the host).
 loops_status download_mirrors(loops_plan_s* p);
+
+// A device buffer whose write evicts the L2 (timed autotuning). Allocation failure leaves it
+// empty (run() then does nothing): tuning still works, on a warmer cache.
+constexpr size_t kL2FlushBytes = (size_t)256 << 20;
+struct L2Flush {
+  void* buf = nullptr;
+  int n = 0;
+  L2Flush();
+  ~L2Flush();
+  L2Flush(const L2Flush&) = delete;
+  L2Flush& operator=(const L2Flush&) = delete;
+  cudaError_t run(cudaStream_t s);
+};
 
 cudaError_t launch_set_values(const loops_plan_s* p, const void* vals, loops_dtype vd, cudaStream_t s);
 cudaError_t launch_cast_scaled(const float* X, int64_t rows, int64_t cols, int64_t ldx,

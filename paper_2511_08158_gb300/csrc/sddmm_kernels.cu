@@ -43,7 +43,15 @@ struct SddmmKArgs {
   int64_t ldb;
   void* dvals;
   int64_t N;
+  const float* dc_scale;   // optional per-column scales of dC and of B (16-bit dtypes): the
+  const float* b_scale;    // sum runs over dC[i, n] * B[j, n] * dc_scale[n] * b_scale[n]
 };
+
+// Per-column weight of the dot product (product of the two optional scales; exact for powers
+// of two).
+__device__ __forceinline__ float col_weight(const SddmmKArgs& a, int64_t n) {
+  return (a.dc_scale ? a.dc_scale[n] : 1.f) * (a.b_scale ? a.b_scale[n] : 1.f);
+}
 
 template <class Tr, int G, int VPL>
 __global__ void __launch_bounds__(256) sddmm_vec(SddmmKArgs a) {
@@ -69,6 +77,12 @@ __global__ void __launch_bounds__(256) sddmm_vec(SddmmKArgs a) {
     colok[p] = coff[p] < a.N;
     uint4 v = colok[p] ? ldg16(dcrow + coff[p]) : make_uint4(0, 0, 0, 0);
     unpack16<Tr>(v, g[p]);
+    if constexpr (Tr::kScaled) {
+      if (colok[p] && (a.dc_scale || a.b_scale)) {
+#pragma unroll
+        for (int e = 0; e < VE; ++e) g[p][e] *= col_weight(a, coff[p] + e);
+      }
+    }
   }
   constexpr int U = 4;
   // one batch of U entries from k0; TAIL: the batch may run past the segment's end (bounds
@@ -140,7 +154,11 @@ __global__ void __launch_bounds__(256) sddmm_scalar(SddmmKArgs a) {
   for (int64_t k = a.item_beg[item]; k < a.item_end[item]; ++k) {
     const int32_t c = __ldg(a.col + k);
     TAcc s = TAcc(0);
-    for (int64_t n = lane; n < a.N; n += 32) s = fma(Tr::to_acc(dcrow[n]), Tr::to_acc(Bp[(int64_t)c * a.ldb + n]), s);
+    for (int64_t n = lane; n < a.N; n += 32) {
+      TAcc g = Tr::to_acc(dcrow[n]);
+      if constexpr (Tr::kScaled) g *= col_weight(a, n);
+      s = fma(g, Tr::to_acc(Bp[(int64_t)c * a.ldb + n]), s);
+    }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
     if (lane == 0) reinterpret_cast<TC*>(a.dvals)[k] = (TC)s;
@@ -149,7 +167,7 @@ __global__ void __launch_bounds__(256) sddmm_scalar(SddmmKArgs a) {
 
 template <class Tr>
 cudaError_t launch_sddmm_t(const loops_plan_s* p, const void* dC, int64_t lddc, const void* B, int64_t ldb,
-                           void* dvals, cudaStream_t s) {
+                           void* dvals, const float* dc_scale, const float* b_scale, cudaStream_t s) {
   SddmmKArgs a;
   a.item_row = p->sddmm.item_row;
   a.item_beg = p->sddmm.item_beg;
@@ -162,6 +180,8 @@ cudaError_t launch_sddmm_t(const loops_plan_s* p, const void* dC, int64_t lddc, 
   a.ldb = ldb;
   a.dvals = dvals;
   a.N = p->N;
+  a.dc_scale = dc_scale;
+  a.b_scale = b_scale;
   if (a.n_items == 0) return cudaSuccess;
   using TB = typename Tr::TB;
   constexpr int VE = Tr::kVE;
@@ -291,12 +311,12 @@ cudaError_t launch_set_values(const loops_plan_s* p, const void* vals, loops_dty
 }
 
 cudaError_t launch_sddmm(const loops_plan_s* p, const void* dC, int64_t lddc, const void* B, int64_t ldb,
-                         void* dvals, cudaStream_t s) {
+                         void* dvals, const float* dc_scale, const float* b_scale, cudaStream_t s) {
   switch (p->dtype) {
-    case LOOPS_F64: return launch_sddmm_t<TrF64>(p, dC, lddc, B, ldb, dvals, s);
-    case LOOPS_F32: return launch_sddmm_t<TrF32>(p, dC, lddc, B, ldb, dvals, s);
-    case LOOPS_F16: return launch_sddmm_t<TrF16>(p, dC, lddc, B, ldb, dvals, s);
-    case LOOPS_BF16: return launch_sddmm_t<TrBF16>(p, dC, lddc, B, ldb, dvals, s);
+    case LOOPS_F64: return launch_sddmm_t<TrF64>(p, dC, lddc, B, ldb, dvals, dc_scale, b_scale, s);
+    case LOOPS_F32: return launch_sddmm_t<TrF32>(p, dC, lddc, B, ldb, dvals, dc_scale, b_scale, s);
+    case LOOPS_F16: return launch_sddmm_t<TrF16>(p, dC, lddc, B, ldb, dvals, dc_scale, b_scale, s);
+    case LOOPS_BF16: return launch_sddmm_t<TrBF16>(p, dC, lddc, B, ldb, dvals, dc_scale, b_scale, s);
   }
   return cudaErrorInvalidValue;
 }

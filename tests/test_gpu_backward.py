@@ -146,3 +146,71 @@ def test_autograd_fp32_matches_oracle(lp):
     assert rel_l2(Y.detach().double().cpu().numpy(), oracle.spmm(A_r, Xq)) <= TOL["f32"]
     assert rel_l2(Xt.grad.double().cpu().numpy(), oracle.spmm_t(A_r, dYq)) <= TOL["f32"]
     assert rel_l2(vals.grad.double().cpu().numpy(), oracle.sddmm(A_r, dYq, Xq)) <= TOL["f32"]
+
+
+def test_two_forwards_one_backward_use_each_calls_values(lp):
+    # weights shared by two calls on one plan: the first call's backward must see its own values
+    A = W.random_csr(80, 70, 0.08, 12, duplicates=True)
+    plan = lp.Plan(A, 16, "f64", tau=1.0, want_backward=True)
+    v1 = torch.as_tensor(A.vals).cuda().requires_grad_(True)
+    v2 = torch.as_tensor(W.dense_normal(1, A.nnz, 13)[0]).cuda().requires_grad_(True)
+    B = torch.as_tensor(W.dense_normal(70, 16, 14)).cuda().requires_grad_(True)
+    dC = W.dense_normal(80, 16, 15)
+    Y1 = lp.spmm(plan, v1, B)
+    Y2 = lp.spmm(plan, v2, B)
+    Y1.backward(torch.as_tensor(dC).cuda())
+    assert rel_l2(B.grad.cpu().numpy(), oracle.spmm_t(A, dC)) <= TOL["f64"]
+    assert rel_l2(v1.grad.cpu().numpy(), oracle.sddmm(A, dC, B.detach().cpu().numpy())) <= TOL["f64"]
+    B.grad = None
+    Y2.backward(torch.as_tensor(dC).cuda())
+    A2 = W.CSR(A.n_rows, A.n_cols, A.row_ptr, A.col_idx, v2.detach().cpu().numpy())
+    assert rel_l2(B.grad.cpu().numpy(), oracle.spmm_t(A2, dC)) <= TOL["f64"]
+
+
+def test_in_place_edit_of_values_after_forward_is_refused(lp):
+    A = W.random_csr(40, 30, 0.1, 16)
+    plan = lp.Plan(A, 8, "f64", tau=1.0, want_backward=True)
+    v = torch.as_tensor(A.vals).cuda().requires_grad_(True)
+    w = v * 1.0                      # a non-leaf the caller could edit in place
+    Y = lp.spmm(plan, w, torch.as_tensor(W.dense_normal(30, 8, 17)).cuda())
+    with torch.no_grad():
+        w.mul_(2.0)
+    with pytest.raises(RuntimeError):
+        Y.sum().backward()
+
+
+@pytest.mark.parametrize("fmt", ["f16", "bf16"])
+def test_half_backward_keeps_small_gradients(lp, fmt):
+    # dC of magnitude ~1e-9 lies below the smallest FP16 subnormal (6e-8): cast as it is, it
+    # would flush to zero; scaled per column first, dB and dvals keep the 2e-3 bound
+    A = W.random_csr(120, 100, 0.06, 18, duplicates=True)
+    A_r = _rounded(A, fmt)
+    N = 32
+    B = oracle.round_to(W.dense_normal(100, N, 19), fmt)
+    # binary32 values (the library's cast starts from f32), so both sides round the same numbers
+    dC = (W.dense_normal(120, N, 20) * 1e-9).astype(np.float32).astype(np.float64)
+    dCq, s = oracle.scale_round_columns(dC, fmt)
+    dC_eff = dCq * s[None, :]
+    plan = lp.Plan(A, N, fmt, tau=1.0, want_backward=True)
+    # through the C ABI with the library's own scaled cast
+    dC16, sd = lp.cast_scaled(torch.as_tensor(dC, dtype=torch.float32).cuda(), fmt)
+    assert np.array_equal(sd.double().cpu().numpy(), s)
+    dB, dv = plan.backward(dC16, to_device(torch, B, fmt), dc_scale=sd)
+    torch.cuda.synchronize()
+    ref_dB, ref_dv = oracle.spmm_t(A_r, dC_eff), oracle.sddmm(A_r, dC_eff, B)
+    assert rel_l2(dB.double().cpu().numpy(), ref_dB) <= TOL[fmt]
+    assert rel_l2(dv.double().cpu().numpy(), ref_dv) <= TOL[fmt]
+    # against the unrounded problem (information: the inputs' own rounding dominates)
+    err_raw = rel_l2(dv.double().cpu().numpy(), oracle.sddmm(A_r, dC, B))
+    print(f"{fmt} half backward: dvals rel-L2 vs unrounded dC {err_raw:.2e}")
+    assert err_raw <= 1e-2
+    # the autograd function scales dC itself
+    vals = torch.as_tensor(A.vals).cuda().requires_grad_(True)
+    Bt = to_device(torch, B, fmt)
+    Y = lp.spmm(plan, vals, Bt)
+    Y.backward(torch.as_tensor(dC, dtype=torch.float32).cuda())
+    assert rel_l2(vals.grad.double().cpu().numpy(), ref_dv) <= TOL[fmt]
+    # scales are refused for plans without a 16-bit dtype
+    p32 = lp.Plan(A, N, "f32", tau=1.0, want_backward=True)
+    with pytest.raises(lp.LoopsError):
+        p32.backward(torch.as_tensor(dC, dtype=torch.float32).cuda(), to_device(torch, B, "f32"), dc_scale=sd)
