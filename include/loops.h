@@ -72,7 +72,8 @@ typedef struct {
 /* Plan options; loops_plan_opts_default() fills the defaults.
  * tau: split threshold on row-block density d = nnz_rb / distinct columns of the block
  *      (nnz per B_r x 1 tile, the paper's block density, Sec. 4.2/4.5). A block with
- *      nnz_rb >= tau * distinct_cols goes to the BCSR part. tau < 0: autotune (time
+ *      nnz_rb >= tau * distinct_cols goes to the BCSR part. LOOPS_TAU_MODEL (-2): the
+ *      performance model picks tau (see LOOPS_TAU_MODEL). Other tau < 0: autotune (time
  *      candidate thresholds on the plan's stream); +inf: CSR only (the pure vector-unit
  *      configuration of Sec. 4.3); 0: every non-empty block BCSR (pure matrix unit).
  * block_rows: B_r (tile height); 0 = default (8 for F64, 16 otherwise); F64 needs 8,
@@ -102,6 +103,12 @@ typedef struct {
 
 typedef struct loops_plan_s* loops_plan_t;
 
+/* tau value selecting the performance model (Sec. 3.5, Eq. 2 and Eq. 3, restated for the GPU):
+ * warm-up plans at a few thresholds are timed, the quadratic of Eq. 2 is fitted to their
+ * throughput as a function of the CSR-part and BCSR-part work, and the threshold of highest
+ * predicted throughput (Eq. 3) is used -- among +inf, 0 and the matrix's block densities. */
+#define LOOPS_TAU_MODEL (-2.0)
+
 /* Counts describing a plan (loops_plan_info). */
 typedef struct {
   loops_dtype dtype;
@@ -118,6 +125,11 @@ typedef struct {
   int64_t device_bytes;    /* device memory owned by the plan */
   int64_t r_boundary;      /* paper mode: the boundary used (Eq. 1 when derived); else -1 */
   int64_t tile_min;        /* tile-level split threshold in effect (0: off) */
+  int32_t tau_source;      /* 0 given, 1 timed autotuner, 2 performance model (Eq. 2/3),
+                              3 contiguous split (paper mode) */
+  int32_t reserved0;
+  double model_gflops;     /* tau_source 2: the Eq. 2 prediction for the chosen split; else NaN */
+  double model_coef[5];    /* tau_source 2: the fitted a0..a4 of Eq. 2 */
 } loops_plan_info;
 
 /* Canonical partition (host arrays, malloc'ed by the library; release with
@@ -208,6 +220,19 @@ int64_t loops_test_fail_alloc(int64_t n);
  * the previous limit. Process-wide. The paper has no counterpart: it is the failure-detection
  * path of the GPU kernels, exercised without faulting or hanging the device. */
 int64_t loops_test_wait_limit(int64_t polls);
+
+/* The performance model of Sec. 3.5 restated for the GPU (host only, no device access).
+ * Eq. 2: perf(x, y) = a0 + a1 x + a2 y + a3 x^2 + a4 y^2, where x is the CSR-part work
+ * (stored entries of the CSR part x N) and y the BCSR-part work (tiles x B_r x N, padding
+ * included) of a split, and perf its throughput. loops_perf_model_fit computes the five
+ * coefficients coef[0..4] by least squares over n samples (x[i], y[i], perf[i]); samples on a
+ * line (one matrix, whose x and y move together) still give a solution (a tiny ridge).
+ * LOOPS_ERR_STATE if the system has no finite solution. loops_perf_model_argmax is Eq. 3:
+ * the index of the candidate (x[i], y[i]) of highest predicted perf, and that prediction.
+ * Plans use them with tau = LOOPS_TAU_MODEL (loops_plan) and in the batched autotuner. */
+loops_status loops_perf_model_fit(const double* x, const double* y, const double* perf, int32_t n, double* coef);
+loops_status loops_perf_model_argmax(const double* coef, const double* x, const double* y, int32_t n,
+                                     int32_t* best, double* best_perf);
 
 /* Release a plan and its device memory (synchronises the device first). NULL is a no-op. A
  * handle that is not a live plan (never returned, or already destroyed) gives
@@ -317,10 +342,14 @@ loops_status loops_plan_check(loops_plan_t plan, loops_stream_t stream);
  * counterpart there): `count` matrices As[m] (host CSR, as for loops_plan) with their own
  * N = Ns[m], in one dtype
  * (LOOPS_F32, LOOPS_F16 or LOOPS_BF16). Each N must be a multiple of the elements of a 16-byte
- * vector (4 for F32, 8 otherwise) and at most 128 (F32: 128, 16-bit: 128). opts->tau < 0 autotunes the
- * split threshold (and, for F32 with block_rows 0, the tile height) by timing the whole batch
- * on `stream` (synchronises it). One persistent launch serves every matrix; it is captured in
- * a CUDA graph by the first loops_spmm_batched call and replayed by later ones. */
+ * vector (4 for F32, 8 otherwise) and at most 128. opts->tau < 0 autotunes on `stream`
+ * (synchronises it): candidates with one split threshold for all matrices (and, for F32 with
+ * block_rows 0, either tile height) are timed as whole batches; then the performance model
+ * (Eq. 2 fitted to those timings, Eq. 3 applied per matrix) proposes a threshold and tile
+ * height per matrix, which is timed too, and the fastest candidate is kept
+ * (loops_plan_batched_stats reports which, with the prediction). The tasks of the batch fall
+ * into classes by kind and lane-group width, one persistent kernel each; the launches are
+ * captured in a CUDA graph by the first loops_spmm_batched call and replayed by later ones. */
 loops_status loops_plan_batched(const loops_csr* As, const int64_t* Ns, int32_t count, loops_dtype dtype,
                                 const loops_plan_opts* opts, loops_stream_t stream, loops_plan_t* out);
 
@@ -368,14 +397,21 @@ typedef struct {
   int64_t n_split_blocks;  /* BCSR blocks cut into units (likewise) */
   int64_t n_rows, nnz, nnz_bcsr;
   int64_t device_bytes;    /* device memory owned by the plan (staging areas included) */
-  int32_t reserved[8];
+  int32_t tau_source;      /* 0 given; 1 autotuned, one threshold for all matrices; 2 autotuned,
+                              a threshold and tile height per matrix from the performance model */
+  int32_t reserved0;
+  double model_gflops;           /* autotuned: Eq. 2 prediction for the per-matrix choice (NaN if none) */
+  double model_measured_gflops;  /* autotuned: that choice, timed (NaN if it equalled a timed one) */
+  double timed_best_gflops;      /* autotuned: the best single-threshold candidate, timed */
+  int32_t reserved[2];
 } loops_batched_info;
 
 /* Totals of a batched plan, for reporting (host only, no device access). */
 loops_status loops_plan_batched_stats(loops_plan_t plan, loops_batched_info* out);
 
 /* The loops_plan_info of matrix m (0 <= m < count) of a batched plan: its threshold, tile
- * height and the sizes of its two parts, as the batch's autotuner left them. Host only. */
+ * height and the sizes of its two parts, as the batch's autotuner left them (with the
+ * performance model, thresholds and tile heights can differ between matrices). Host only. */
 loops_status loops_plan_batched_matrix_info(loops_plan_t plan, int32_t m, loops_plan_info* out);
 
 /* ---------------------------------------------------------------------------------------- */

@@ -36,7 +36,7 @@ EXPORTED = ["loops_version", "loops_status_str", "loops_last_error", "loops_plan
             "loops_spmm_host_async", "loops_spmm_host_flush", "loops_plan_device",
             "loops_plan_batched_device", "loops_test_fail_alloc", "loops_spmm_backward_scaled",
             "loops_test_wait_limit", "loops_spmm_batched_host", "loops_plan_batched_stats",
-            "loops_plan_batched_matrix_info"]
+            "loops_plan_batched_matrix_info", "loops_perf_model_fit", "loops_perf_model_argmax"]
 
 
 class LoopsError(RuntimeError):
@@ -66,7 +66,38 @@ class _Info(ctypes.Structure):
                 ("n_row_blocks", ctypes.c_int64), ("n_tiles", ctypes.c_int64), ("nnz_bcsr", ctypes.c_int64),
                 ("n_split_rows", ctypes.c_int64), ("n_segments", ctypes.c_int64),
                 ("n_subnormal_vals", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
-                ("r_boundary", ctypes.c_int64), ("tile_min", ctypes.c_int64)]
+                ("r_boundary", ctypes.c_int64), ("tile_min", ctypes.c_int64), ("tau_source", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32), ("model_gflops", ctypes.c_double),
+                ("model_coef", ctypes.c_double * 5)]
+
+
+TAU_MODEL = -2.0   # tau value of LOOPS_TAU_MODEL: the performance model (Eq. 2/3) picks the split
+
+
+def _info_dict(inf) -> dict:
+    out = {name: getattr(inf, name) for name, _ in _Info._fields_ if name != "reserved0"}
+    out["model_coef"] = list(out["model_coef"])
+    return out
+
+
+def perf_model_fit(x, y, perf):
+    """Eq. 2 coefficients a0..a4 by least squares (``loops_perf_model_fit``; host only)."""
+    x, y, p = (np.ascontiguousarray(v, dtype=np.float64) for v in (x, y, perf))
+    coef = np.zeros(5)
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(load().loops_perf_model_fit(x.ctypes.data_as(dp), y.ctypes.data_as(dp), p.ctypes.data_as(dp), x.size,
+                                       coef.ctypes.data_as(dp)))
+    return coef
+
+
+def perf_model_argmax(coef, x, y):
+    """Eq. 3: (index, predicted perf) of the best candidate (``loops_perf_model_argmax``)."""
+    c, x, y = (np.ascontiguousarray(v, dtype=np.float64) for v in (coef, x, y))
+    dp = ctypes.POINTER(ctypes.c_double)
+    best, bp = ctypes.c_int32(), ctypes.c_double()
+    _check(load().loops_perf_model_argmax(c.ctypes.data_as(dp), x.ctypes.data_as(dp), y.ctypes.data_as(dp), x.size,
+                                          ctypes.byref(best), ctypes.byref(bp)))
+    return best.value, bp.value
 
 
 class _BatchedInfo(ctypes.Structure):
@@ -74,7 +105,9 @@ class _BatchedInfo(ctypes.Structure):
                 ("n_tasks", ctypes.c_int64), ("n_kernels", ctypes.c_int32), ("n_classes", ctypes.c_int32),
                 ("n_split_rows", ctypes.c_int64), ("n_split_blocks", ctypes.c_int64), ("n_rows", ctypes.c_int64),
                 ("nnz", ctypes.c_int64), ("nnz_bcsr", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
-                ("reserved", ctypes.c_int32 * 8)]
+                ("tau_source", ctypes.c_int32), ("reserved0", ctypes.c_int32), ("model_gflops", ctypes.c_double),
+                ("model_measured_gflops", ctypes.c_double), ("timed_best_gflops", ctypes.c_double),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class _Part(ctypes.Structure):
@@ -143,6 +176,9 @@ def load():
                                      ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(vp), vp]
     L.loops_spmm_batched_host.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(vp),
                                           ctypes.POINTER(ctypes.c_int64), vp]
+    dp = ctypes.POINTER(ctypes.c_double)
+    L.loops_perf_model_fit.argtypes = [dp, dp, dp, ctypes.c_int32, dp]
+    L.loops_perf_model_argmax.argtypes = [dp, dp, dp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), dp]
     L.loops_plan_batched_stats.argtypes = [vp, ctypes.POINTER(_BatchedInfo)]
     L.loops_plan_batched_matrix_info.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(_Info)]
     L.loops_plan_batched_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64),
@@ -308,7 +344,7 @@ class Plan:
     def info(self) -> dict:
         inf = _Info()
         _check(self._L.loops_plan_info_get(self._h, ctypes.byref(inf)))
-        return {name: getattr(inf, name) for name, _ in _Info._fields_}
+        return _info_dict(inf)
 
     def export(self) -> dict:
         part = _Part()
@@ -456,13 +492,13 @@ class BatchedPlan:
         """Totals of the plan (``loops_plan_batched_stats``)."""
         inf = _BatchedInfo()
         _check(self._L.loops_plan_batched_stats(self._h, ctypes.byref(inf)))
-        return {name: getattr(inf, name) for name, _ in _BatchedInfo._fields_ if name != "reserved"}
+        return {name: getattr(inf, name) for name, _ in _BatchedInfo._fields_ if not name.startswith("reserved")}
 
     def matrix_info(self, m: int) -> dict:
         """The plan info of matrix m (``loops_plan_batched_matrix_info``)."""
         inf = _Info()
         _check(self._L.loops_plan_batched_matrix_info(self._h, int(m), ctypes.byref(inf)))
-        return {name: getattr(inf, name) for name, _ in _Info._fields_}
+        return _info_dict(inf)
 
     def spmm(self, Bs, Cs=None, col_scales=None, stream=None):
         torch = _torch()

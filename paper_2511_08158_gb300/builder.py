@@ -20,11 +20,13 @@ LIB = os.path.join(HERE, "libloops.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 SOURCES = ["capi.cpp", "partition.cpp", "layout.cpp", "csr_kernels.cu", "sddmm_kernels.cu", "bcsr_kernels.cu", "csr_noalloc.cu",
-           "batched.cu", "batched_plan.cpp", "plan_device.cu"]
+           "batched.cu", "batched_plan.cpp", "plan_device.cu", "perf_model.cpp"]
 HEADERS = [os.path.join(CSRC, "loops_internal.h"), os.path.join(CSRC, "device_common.cuh"),
            os.path.join(INCLUDE, "loops.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE] + ARCH
+# extra nvcc flags for tuning builds (e.g. "-DLOOPS_BATCHED_CSR_LOADS=4"); part of the stamp
+FLAGS += os.environ.get("LOOPS_NVCC_FLAGS", "").split()
 
 
 def nvcc() -> str:

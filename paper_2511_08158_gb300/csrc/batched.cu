@@ -1,27 +1,48 @@
-// Batched hybrid SpMM: many sparse matrices of uneven size and N in one persistent launch.
+// Batched hybrid SpMM: many sparse matrices of uneven size and N in a few persistent launches.
 //
 // Each matrix has its own plan (partition and device layout as for a single SpMM). A static
-// task list covers every matrix's CSR items (in groups of consecutive items) and BCSR row
-// blocks, sorted by estimated cost; warp w of the persistent grid runs tasks w, w + W, ...
-// (no atomics, no inter-block waits, so the launch is deterministic and graph-stable).
-//   CSR task   (kind 0): items [first, first + count); a group of G = N / VE lanes per item,
-//              32 / G items at a time per warp (VE elements of a 16-byte B vector per lane).
-//   BCSR task  (kind 1): F32 units [first, first + count) (a unit is a row block, or a K-aligned
-//              range of a block with very many tiles), one group of G lanes per unit,
-//              register-blocked outer product.
-//   BCSR task  (kind 2): one F16/BF16 unit per warp, in 64-column chunks: the 16 B-row pieces
-//              of each K-group are staged in the warp's own shared-memory slice and fed to
-//              mma.sync m16n8k16.
+// task list covers every matrix's CSR items (in groups of consecutive items) and BCSR work
+// units. Tasks fall into classes by kind and by the lane-group width their N needs; each class
+// is a contiguous run of the list, ordered matrix by matrix, and runs as one persistent kernel
+// specialised for it (its own register budget, compile-time group width). The warps of a
+// class kernel claim its tasks in list order from a counter, so at any time they work on one
+// or a few matrices, whose B operands stay in L2 while their rows gather from them. Every
+// task writes its own outputs (C rows, or partial-sum slots), so the result does not depend on
+// which warp runs which task.
+//   CSR class   (kind 0, <G, VPL>): a group of G lanes per item, each lane VPL 16-byte column
+//               vectors of the row; 32 / G items at a time per warp.
+//   FFMA class  (kind 1, <B_r, G>): F32 BCSR units of one tile height, a group of G lanes per
+//               unit (4 columns per lane), register-blocked outer products with several
+//               tiles' loads in flight.
+//   HMMA class  (kind 2): one F16/BF16 BCSR unit per warp, in 64-column chunks; the 16 B-row
+//               pieces of each K-group are copied into the warp's shared-memory ring by
+//               cp.async (two groups in flight while one is multiplied) and fed to mma.sync
+//               m16n8k16.
 // Rows split in segments and blocks cut into units get small follow-up launches that add
 // their partial sums in a fixed order.
+#include <algorithm>
 #include <type_traits>
 
 #include "device_common.cuh"
 #include "loops_internal.h"
 
-// Minimum resident blocks per SM for the persistent kernel (register cap; tuning knob).
-#ifndef LOOPS_BATCHED_MIN_BLOCKS
-#define LOOPS_BATCHED_MIN_BLOCKS 3
+// Tuning knobs (compile time): resident blocks per SM the CSR and FFMA class kernels must
+// allow (their register caps), B-row loads in flight per lane in FP32 CSR items, tiles in
+// flight in B_r = 8 FFMA units, and cp.async stages of the HMMA units.
+#ifndef LOOPS_BATCHED_CSR_MIN_BLOCKS
+#define LOOPS_BATCHED_CSR_MIN_BLOCKS 3
+#endif
+#ifndef LOOPS_BATCHED_CSR_LOADS
+#define LOOPS_BATCHED_CSR_LOADS 8
+#endif
+#ifndef LOOPS_BATCHED_FFMA_TILES
+#define LOOPS_BATCHED_FFMA_TILES 4
+#endif
+#ifndef LOOPS_BATCHED_HMMA_STAGES
+#define LOOPS_BATCHED_HMMA_STAGES 3
+#endif
+#ifndef LOOPS_BATCHED_FFMA_MIN_BLOCKS
+#define LOOPS_BATCHED_FFMA_MIN_BLOCKS 2
 #endif
 
 namespace loops {
@@ -41,108 +62,220 @@ __device__ __forceinline__ void mma16816_b(float (&d)[4], const uint4& a, uint32
         : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b0), "r"(b1));
 }
 
+// 16-byte global -> shared copy that holds no registers while in flight (the asynchronous
+// copy, completed by commit groups). src_bytes 0 fills the 16 bytes with zeros and reads
+// nothing.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
+               ::"r"(smem_addr(dst)), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 template <class Tr>
 __device__ __forceinline__ float col_mult(const BatchDesc& d, int64_t n) {
   if (!Tr::kScaled) return 1.f;
   return d.col_scale ? d.col_scale[n] * d.inv_scale : d.inv_scale;
 }
 
-// One CSR item for a group of G lanes (runtime G): row or segment partial.
-template <class Tr>
-__device__ __forceinline__ void csr_item(const BatchDesc& d, int64_t item, int G, int sub, unsigned gmask) {
+// Next task of a warp: the next unclaimed one of the class's run of the list (the counter is
+// zeroed before the launch).
+__device__ __forceinline__ int64_t claim(unsigned long long* counter, int lane) {
+  unsigned long long t = 0;
+  if (lane == 0) t = atomicAdd(counter, 1ull);
+  return (int64_t)__shfl_sync(0xffffffffu, t, 0);
+}
+
+// ------------------------------------------------------------------ CSR items
+// One CSR item (a row, or a segment of a split row) for a group of G lanes; lane `sub` owns
+// the 16-byte column vectors p * G + sub (p < VPL). Entries are read R per lane at a time
+// (chunks of G * R entries, broadcast by shuffles), and the next chunk's entries are loaded
+// while the current chunk's B rows are in flight.
+template <class Tr, int G, int VPL>
+__device__ __forceinline__ void csr_item(const BatchDesc& d, int64_t item, int sub, unsigned gmask) {
   using TB = typename Tr::TB;
   using TAcc = typename Tr::TAcc;
   using TC = typename Tr::TC;
   constexpr int VE = Tr::kVE;
-  constexpr int U = 4;
+  constexpr int R = G >= 8 ? 1 : (G >= 2 ? 8 / G : 4);  // chunks of at least 4-8 entries
+  constexpr int CH = G * R;                             // entries per chunk
+  // B loads in flight per lane: 8 for FP32 rows, 4 for 16-bit (whose unpacked vectors take
+  // twice the registers), half that with two vectors per lane
+  constexpr int UMAX = (VE == 8 ? LOOPS_BATCHED_CSR_LOADS / 2 : LOOPS_BATCHED_CSR_LOADS) / VPL;
+  constexpr int U = UMAX < CH ? UMAX : CH;
   const int64_t beg = d.item_ptr[item], end = d.item_ptr[item + 1];
   const int32_t row = d.item_row[item];
-  const int64_t coff = (int64_t)sub * VE;
-  const TB* Bp = reinterpret_cast<const TB*>(d.B);
-  const TB* vals = reinterpret_cast<const TB*>(d.val);
-  TAcc acc[VE];
+  const TB* __restrict__ Bp = reinterpret_cast<const TB*>(d.B);
+  const TB* __restrict__ vals = reinterpret_cast<const TB*>(d.val);
+  int64_t coff[VPL];
+  bool colok[VPL];
 #pragma unroll
-  for (int e = 0; e < VE; ++e) acc[e] = TAcc(0);
-  for (int64_t k0 = beg; k0 < end; k0 += G) {
-    const int64_t k = k0 + sub;
-    int32_t c = 0;
-    TAcc v = TAcc(0);
-    if (k < end) {
-      c = __ldg(d.col + k);
-      v = Tr::to_acc(vals[k]);
-    }
-    const int cnt = (int)(end - k0 < (int64_t)G ? end - k0 : (int64_t)G);
-    int j0 = 0;
-    for (; j0 + U <= cnt; j0 += U) {
-      uint4 bv[U];
-      TAcc av[U];
+  for (int p = 0; p < VPL; ++p) {
+    coff[p] = (int64_t)(p * G + sub) * VE;
+    colok[p] = coff[p] < d.N;
+  }
+  TAcc acc[VPL][VE];
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int cj = __shfl_sync(gmask, c, j0 + u, G);
-        av[u] = __shfl_sync(gmask, v, j0 + u, G);
-        bv[u] = ldg16(Bp + (int64_t)cj * d.ldb + coff);
-      }
+  for (int p = 0; p < VPL; ++p)
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        TAcc b[VE];
-        unpack16<Tr>(bv[u], b);
+    for (int e = 0; e < VE; ++e) acc[p][e] = TAcc(0);
+
+  auto fetch = [&](int64_t k0, int32_t (&c)[R], TAcc (&v)[R]) {
 #pragma unroll
-        for (int e = 0; e < VE; ++e) acc[e] = fma(av[u], b[e], acc[e]);
+    for (int r = 0; r < R; ++r) {
+      const int64_t k = k0 + r * G + sub;
+      c[r] = 0;
+      v[r] = TAcc(0);
+      if (k < end) {
+        c[r] = __ldg(d.col + k);
+        v[r] = Tr::to_acc(vals[k]);
       }
     }
-    for (; j0 < cnt; ++j0) {
-      const int cj = __shfl_sync(gmask, c, j0, G);
-      const TAcc aj = __shfl_sync(gmask, v, j0, G);
-      TAcc b[VE];
-      unpack16<Tr>(ldg16(Bp + (int64_t)cj * d.ldb + coff), b);
+  };
+  auto fma_vec = [&](int p, const uint4& bv, TAcc a) {
+    TAcc b[VE];
+    unpack16<Tr>(bv, b);
 #pragma unroll
-      for (int e = 0; e < VE; ++e) acc[e] = fma(aj, b[e], acc[e]);
+    for (int e = 0; e < VE; ++e) acc[p][e] = fma(a, b[e], acc[p][e]);
+  };
+  int32_t c[R];
+  TAcc v[R];
+  fetch(beg, c, v);
+  for (int64_t k0 = beg; k0 < end; k0 += CH) {
+    int32_t cn[R];
+    TAcc vn[R];
+    fetch(k0 + CH, cn, vn);                             // next chunk's entries, in flight now
+    if (k0 + CH <= end) {                               // full chunk: batches of U loads, then FMAs
+#pragma unroll
+      for (int e0 = 0; e0 < CH; e0 += U) {
+        uint4 bv[U][VPL];
+        TAcc av[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int e = e0 + u;
+          const int cj = __shfl_sync(gmask, c[e / G], e % G, G);
+          av[u] = __shfl_sync(gmask, v[e / G], e % G, G);
+          const TB* brow = Bp + (int64_t)cj * d.ldb;
+#pragma unroll
+          for (int p = 0; p < VPL; ++p) bv[u][p] = colok[p] ? ldg16(brow + coff[p]) : make_uint4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+          for (int p = 0; p < VPL; ++p) fma_vec(p, bv[u][p], av[u]);
+      }
+    } else {                                            // the last, partial chunk
+      const int cnt = (int)(end - k0);
+#pragma unroll
+      for (int e = 0; e < CH; ++e) {
+        if (e < cnt) {
+          const int cj = __shfl_sync(gmask, c[e / G], e % G, G);
+          const TAcc a = __shfl_sync(gmask, v[e / G], e % G, G);
+          const TB* brow = Bp + (int64_t)cj * d.ldb;
+#pragma unroll
+          for (int p = 0; p < VPL; ++p)
+            if (colok[p]) fma_vec(p, ldg16(brow + coff[p]), a);
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      c[r] = cn[r];
+      v[r] = vn[r];
     }
   }
   if (row >= 0) {
-    TC* crow = reinterpret_cast<TC*>(d.C) + (int64_t)row * d.ldc + coff;
-    TC o[VE];
+    TC* crow = reinterpret_cast<TC*>(d.C) + (int64_t)row * d.ldc;
 #pragma unroll
-    for (int e = 0; e < VE; ++e) o[e] = Tr::kScaled ? (TC)(acc[e] * col_mult<Tr>(d, coff + e)) : (TC)acc[e];
+    for (int p = 0; p < VPL; ++p) {
+      if (!colok[p]) continue;
+      TC o[VE];
 #pragma unroll
-    for (int q = 0; q < (int)(VE * sizeof(TC) / 16); ++q)
-      *reinterpret_cast<uint4*>(crow + q * (16 / sizeof(TC))) = *reinterpret_cast<const uint4*>(&o[q * (16 / sizeof(TC))]);
+      for (int e = 0; e < VE; ++e) o[e] = Tr::kScaled ? (TC)(acc[p][e] * col_mult<Tr>(d, coff[p] + e)) : (TC)acc[p][e];
+#pragma unroll
+      for (int q = 0; q < (int)(VE * sizeof(TC) / 16); ++q)
+        *reinterpret_cast<uint4*>(crow + coff[p] + q * (16 / sizeof(TC))) =
+            *reinterpret_cast<const uint4*>(&o[q * (16 / sizeof(TC))]);
+    }
   } else {
-    TAcc* srow = reinterpret_cast<TAcc*>(d.scratch) + (int64_t)(-1 - row) * d.N + coff;
+    TAcc* srow = reinterpret_cast<TAcc*>(d.scratch) + (int64_t)(-1 - row) * d.N;
 #pragma unroll
-    for (int e = 0; e < VE; ++e) srow[e] = acc[e];
+    for (int p = 0; p < VPL; ++p) {
+      if (!colok[p]) continue;
+#pragma unroll
+      for (int e = 0; e < VE; ++e) srow[coff[p] + e] = acc[p][e];
+    }
   }
 }
 
-// One F32 BCSR unit (B_r rows, tile-major values) for a group of G lanes.
-template <int BR>
-__device__ __forceinline__ void ffma_block(const BatchDesc& d, int64_t u, int sub) {
+template <class Tr, int G, int VPL>
+__global__ void __launch_bounds__(256, LOOPS_BATCHED_CSR_MIN_BLOCKS) batched_csr(const BatchDesc* __restrict__ descs,
+                                                      const BatchTask* __restrict__ tasks, int64_t n_tasks,
+                                                      unsigned long long* counter) {
+  const int lane = threadIdx.x & 31;
+  const int grp = lane / G, sub = lane % G;
+  const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (grp * G));
+  for (int64_t t = claim(counter, lane); t < n_tasks; t = claim(counter, lane)) {
+    const BatchTask task = tasks[t];
+    const BatchDesc& d = descs[task.m];
+    for (int32_t i = grp; i < task.count; i += 32 / G) csr_item<Tr, G, VPL>(d, task.first + i, sub, gmask);
+  }
+}
+
+// ------------------------------------------------------------------ F32 BCSR units
+// One F32 BCSR unit (B_r rows, tile-major values) for a group of G lanes, 4 columns per lane;
+// T tiles' B vectors and A values are loaded before their FMAs.
+template <int BR, int G>
+__device__ __forceinline__ void ffma_unit(const BatchDesc& d, int64_t u, int sub) {
+  constexpr int T = BR == 8 ? LOOPS_BATCHED_FFMA_TILES : 2;
   const int32_t b = d.unit_block[u];
   const int64_t rb = d.rb_id[b];
   const int64_t t0 = d.unit_t0[u], t1 = d.unit_t1[u];
   const int32_t slot = d.unit_slot[u];
-  const float* Av = reinterpret_cast<const float*>(d.tile_val);
-  const float* Bp = reinterpret_cast<const float*>(d.B);
+  const float* __restrict__ Av = reinterpret_cast<const float*>(d.tile_val);
+  const float* __restrict__ Bp = reinterpret_cast<const float*>(d.B);
   const int64_t n = (int64_t)sub * 4;
+  const bool colok = n < d.N;
   float acc[BR][4];
 #pragma unroll
   for (int r = 0; r < BR; ++r)
 #pragma unroll
     for (int e = 0; e < 4; ++e) acc[r][e] = 0.f;
-  for (int64_t tt = t0; tt < t1; ++tt) {
-    const int32_t c = __ldg(d.tile_col + tt);
-    const uint4 v = c >= 0 ? ldg16(Bp + (int64_t)c * d.ldb + n) : make_uint4(0, 0, 0, 0);
+  auto tile_fma = [&](const uint4& v, const uint4 (&w)[BR / 4]) {
     const float bv[4] = {__uint_as_float(v.x), __uint_as_float(v.y), __uint_as_float(v.z), __uint_as_float(v.w)};
 #pragma unroll
     for (int r4 = 0; r4 < BR / 4; ++r4) {
-      const uint4 w = ldg16(Av + tt * BR + r4 * 4);
-      const float a4[4] = {__uint_as_float(w.x), __uint_as_float(w.y), __uint_as_float(w.z), __uint_as_float(w.w)};
+      const float a4[4] = {__uint_as_float(w[r4].x), __uint_as_float(w[r4].y), __uint_as_float(w[r4].z),
+                           __uint_as_float(w[r4].w)};
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int e = 0; e < 4; ++e) acc[r4 * 4 + i][e] = fmaf(a4[i], bv[e], acc[r4 * 4 + i][e]);
     }
+  };
+  auto load_tile = [&](int64_t tt, uint4& v, uint4 (&w)[BR / 4]) {
+    const int32_t c = __ldg(d.tile_col + tt);
+    v = (c >= 0 && colok) ? ldg16(Bp + (int64_t)c * d.ldb + n) : make_uint4(0, 0, 0, 0);
+#pragma unroll
+    for (int r4 = 0; r4 < BR / 4; ++r4) w[r4] = ldg16(Av + tt * BR + r4 * 4);
+  };
+  int64_t tt = t0;
+  for (; tt + T <= t1; tt += T) {
+    uint4 v[T];
+    uint4 w[T][BR / 4];
+#pragma unroll
+    for (int q = 0; q < T; ++q) load_tile(tt + q, v[q], w[q]);
+#pragma unroll
+    for (int q = 0; q < T; ++q) tile_fma(v[q], w[q]);
   }
+  for (; tt < t1; ++tt) {
+    uint4 v;
+    uint4 w[BR / 4];
+    load_tile(tt, v, w);
+    tile_fma(v, w);
+  }
+  if (!colok) return;
   if (slot >= 0) {  // unit of a split block: partial sums
     float* P = reinterpret_cast<float*>(d.bscratch) + (int64_t)slot * BR * d.N;
 #pragma unroll
@@ -159,15 +292,34 @@ __device__ __forceinline__ void ffma_block(const BatchDesc& d, int64_t u, int su
   }
 }
 
-// One F16/BF16 BCSR unit for the whole warp, in column chunks of up to 64: sB is the warp's
-// shared-memory slice holding the 16 gathered B-row pieces of the current K-group and chunk
-// (row stride 72 elements, conflict-free for ldmatrix).
+template <int BR, int G>
+__global__ void __launch_bounds__(256, LOOPS_BATCHED_FFMA_MIN_BLOCKS) batched_ffma(const BatchDesc* __restrict__ descs,
+                                                       const BatchTask* __restrict__ tasks, int64_t n_tasks,
+                                                       unsigned long long* counter) {
+  const int lane = threadIdx.x & 31;
+  const int grp = lane / G, sub = lane % G;
+  for (int64_t t = claim(counter, lane); t < n_tasks; t = claim(counter, lane)) {
+    const BatchTask task = tasks[t];
+    const BatchDesc& d = descs[task.m];
+    for (int32_t i = grp; i < task.count; i += 32 / G) ffma_unit<BR, G>(d, task.first + i, sub);
+  }
+}
+
+// ------------------------------------------------------------------ F16/BF16 BCSR units
+// One F16/BF16 BCSR unit for the whole warp, in column chunks of up to 64. The 16 gathered
+// B-row pieces of each K-group go into the warp's ring of kHStages shared-memory stages by
+// cp.async (padding tiles, column -1, are zero-filled without a read); kHStages - 1 groups
+// are in flight while the oldest one is multiplied. Row stride 72 elements: conflict-free
+// ldmatrix.
 constexpr int kHChunk = 64;
 constexpr int kHStride = kHChunk + 8;
+constexpr int kHStages = LOOPS_BATCHED_HMMA_STAGES;
+constexpr int kHStageElems = 16 * kHStride;
+constexpr int kHmmaSmemPerWarp = kHStages * kHStageElems * 2;  // bytes
 
 template <class T>
-__device__ __forceinline__ void hmma_block(const BatchDesc& d, int64_t u, T* sB, int lane) {
-  constexpr bool kBF16 = sizeof(T) == 2 && !std::is_same<T, __half>::value;
+__device__ __forceinline__ void hmma_unit(const BatchDesc& d, int64_t u, T* sB, int lane) {
+  constexpr bool kBF16 = std::is_same<T, __nv_bfloat16>::value;
   const int32_t b = d.unit_block[u];
   const int64_t rb = d.rb_id[b];
   const int64_t t0 = d.unit_t0[u];
@@ -180,42 +332,57 @@ __device__ __forceinline__ void hmma_block(const BatchDesc& d, int64_t u, T* sB,
   for (int c0 = 0; c0 < N; c0 += kHChunk) {
     const int NC = min(kHChunk, N - c0);   // columns of this chunk (a multiple of 8)
     const int NF = NC / 8;
-    const int vec_per_row = NC / 8;        // 16-byte vectors per staged row piece
+    // stage of group g: this lane copies the vectors i = lane, lane + 32, ... of its 16 x NF
+    // piece (column -1: zero-filled, nothing read)
+    auto issue = [&](int g) {
+      T* st = sB + (g % kHStages) * kHStageElems;
+      for (int i = lane; i < 16 * NF; i += 32) {
+        const int k = i / NF, qv = i - k * NF;
+        const int32_t c = __ldg(d.tile_col + t0 + g * 16 + k);
+        const T* src = c >= 0 ? Bp + (int64_t)c * d.ldb + c0 + qv * 8 : Bp;
+        cp_async16(st + k * kHStride + qv * 8, src, c >= 0 ? 16 : 0);
+      }
+    };
     float acc[8][4];
 #pragma unroll
     for (int f = 0; f < 8; ++f)
 #pragma unroll
       for (int i = 0; i < 4; ++i) acc[f][i] = 0.f;
+    __syncwarp();                           // every lane is done with the ring's last contents
+#pragma unroll
+    for (int g = 0; g < kHStages - 1; ++g) {
+      if (g < n_groups) issue(g);
+      cp_async_commit();
+    }
     for (int g = 0; g < n_groups; ++g) {
-      __syncwarp();
-      for (int i = lane; i < 16 * vec_per_row; i += 32) {
-        const int k = i / vec_per_row, qv = i % vec_per_row;
-        const int32_t c = __ldg(d.tile_col + t0 + g * 16 + k);
-        const uint4 v = c >= 0 ? ldg16(Bp + (int64_t)c * d.ldb + c0 + qv * 8) : make_uint4(0, 0, 0, 0);
-        *reinterpret_cast<uint4*>(sB + k * kHStride + qv * 8) = v;
-      }
-      __syncwarp();
+      if (g + kHStages - 1 < n_groups) issue(g + kHStages - 1);
+      cp_async_commit();
+      cp_async_wait<kHStages - 1>();        // this lane's copies of group g have landed
+      __syncwarp();                         // ... and every lane's
       const uint4 af = __ldg(Af + (int64_t)g * 32 + lane);
+      const T* st = sB + (g % kHStages) * kHStageElems;
       const int mi = lane >> 3, r = lane & 7;
 #pragma unroll
       for (int f = 0; f < 8; f += 2) {
         if (f >= NF) break;
         if (f + 1 < NF) {
-          const uint32_t addr = smem_addr(sB + (r + 8 * (mi & 1)) * kHStride + f * 8 + 8 * (mi >> 1));
+          const uint32_t addr = smem_addr(st + (r + 8 * (mi & 1)) * kHStride + f * 8 + 8 * (mi >> 1));
           uint32_t b0, b1, b2, b3;
           asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
                        : "=r"(b0), "=r"(b1), "=r"(b2), "=r"(b3) : "r"(addr));
           mma16816_b(acc[f], af, b0, b1, kBF16);
           mma16816_b(acc[f + 1], af, b2, b3, kBF16);
         } else {
-          const uint32_t addr = smem_addr(sB + (r + 8 * (mi & 1)) * kHStride + f * 8);
+          const uint32_t addr = smem_addr(st + (r + 8 * (mi & 1)) * kHStride + f * 8);
           uint32_t b0, b1;
           asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];"
                        : "=r"(b0), "=r"(b1) : "r"(addr));
           mma16816_b(acc[f], af, b0, b1, kBF16);
         }
       }
+      __syncwarp();                         // stage g % kHStages may be refilled next
     }
+    cp_async_wait<0>();
     if (slot >= 0) {  // unit of a split block: unscaled partial sums
       float* P = reinterpret_cast<float*>(d.bscratch) + (int64_t)slot * 16 * d.N;
 #pragma unroll
@@ -248,49 +415,20 @@ __device__ __forceinline__ void hmma_block(const BatchDesc& d, int64_t u, T* sB,
   }
 }
 
-// Next task of a warp: with `counter` (zeroed before the launch) the warp takes the next
-// unclaimed task of the list, so all warps stay within a short window of it (the list is
-// ordered matrix by matrix, and the window's B operands stay in L2); without it, warp w takes
-// tasks w, w + W, w + 2W, ... Every task writes its own outputs, so either way the result does
-// not depend on which warp runs which task.
-__device__ __forceinline__ int64_t next_task(unsigned long long* counter, int64_t prev, int64_t W, int lane) {
-  if (counter == nullptr) return prev + W;
-  unsigned long long t = 0;
-  if (lane == 0) t = atomicAdd(counter, 1ull);
-  return (int64_t)__shfl_sync(0xffffffffu, t, 0);
-}
-
-template <class Tr, int BR>
-__global__ void __launch_bounds__(256, LOOPS_BATCHED_MIN_BLOCKS) batched_persistent(const BatchDesc* __restrict__ descs,
-                                                          const BatchTask* __restrict__ tasks, int64_t n_tasks,
-                                                          int smem_per_warp, unsigned long long* counter) {
+template <class T>
+__global__ void __launch_bounds__(256, 3) batched_hmma(const BatchDesc* __restrict__ descs,
+                                                       const BatchTask* __restrict__ tasks, int64_t n_tasks,
+                                                       unsigned long long* counter) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int lane = threadIdx.x & 31;
-  const int warp = threadIdx.x >> 5;
-  const int64_t W = (int64_t)gridDim.x * (blockDim.x >> 5);
-  const int64_t first = counter ? next_task(counter, 0, W, lane) : (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
-  for (int64_t t = first; t < n_tasks; t = next_task(counter, t, W, lane)) {
+  T* sB = reinterpret_cast<T*>(smem + (threadIdx.x >> 5) * kHmmaSmemPerWarp);
+  for (int64_t t = claim(counter, lane); t < n_tasks; t = claim(counter, lane)) {
     const BatchTask task = tasks[t];
-    const BatchDesc& d = descs[task.m];
-    if (task.kind == 2) {
-      if constexpr (sizeof(typename Tr::TB) == 2)
-        hmma_block<typename Tr::TB>(d, task.first, reinterpret_cast<typename Tr::TB*>(smem + warp * smem_per_warp), lane);
-      continue;
-    }
-    const int G = d.G;
-    const int grp = lane / G, sub = lane % G;
-    const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (grp * G));
-    const int per_round = 32 / G;
-    for (int32_t i = grp; i < task.count; i += per_round) {
-      if (task.kind == 0) {
-        csr_item<Tr>(d, task.first + i, G, sub, gmask);
-      } else if constexpr (std::is_same<Tr, TrF32>::value) {
-        ffma_block<BR>(d, task.first + i, sub);
-      }
-    }
+    hmma_unit<T>(descs[task.m], task.first, sB, lane);
   }
 }
 
+// ------------------------------------------------------------------ partial sums
 // Sum of split-row partials: one block per (matrix, split row).
 template <class Tr>
 __global__ void __launch_bounds__(128) batched_split_reduce(const BatchDesc* __restrict__ descs,
@@ -330,36 +468,65 @@ __global__ void __launch_bounds__(256) batched_bsplit_reduce(const BatchDesc* __
   }
 }
 
-template <class Tr, int BR>
-cudaError_t launch_batched_t(const BatchLaunch& L, cudaStream_t s) {
-  const int smem = L.smem_per_warp * 8;
-  auto kern = batched_persistent<Tr, BR>;
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-  }
-  // timing events become event nodes of the captured graph (external records)
-  auto rec = [&](int i) {
-    return L.tev ? cudaEventRecordWithFlags(L.tev[i], s, cudaEventRecordExternal) : cudaSuccess;
-  };
-  {
-    cudaError_t e = rec(0);
-    if (e != cudaSuccess) return e;
-  }
-  if (L.n_tasks > 0) {
-    if (L.counter) {
-      cudaError_t e = cudaMemsetAsync(L.counter, 0, sizeof(unsigned long long), s);
-      if (e != cudaSuccess) return e;
+// ------------------------------------------------------------------ class dispatch
+using ClassKernel = void (*)(const BatchDesc*, const BatchTask*, int64_t, unsigned long long*);
+
+template <class Tr>
+ClassKernel csr_kernel(int G, int VPL) {
+  if (VPL == 2) {
+    switch (G) {
+      case 8: return batched_csr<Tr, 8, 2>;
+      case 16: return batched_csr<Tr, 16, 2>;
+      default: return nullptr;
     }
-    kern<<<L.grid, 256, smem, s>>>(L.descs, L.tasks, L.n_tasks, L.smem_per_warp, L.counter);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
   }
-  {
-    cudaError_t e = rec(1);
-    if (e == cudaSuccess) e = rec(2);
-    if (e != cudaSuccess) return e;
+  switch (G) {
+    case 1: return batched_csr<Tr, 1, 1>;
+    case 2: return batched_csr<Tr, 2, 1>;
+    case 4: return batched_csr<Tr, 4, 1>;
+    case 8: return batched_csr<Tr, 8, 1>;
+    case 16: return batched_csr<Tr, 16, 1>;
+    case 32: return batched_csr<Tr, 32, 1>;
+    default: return nullptr;
   }
+}
+
+template <int BR>
+ClassKernel ffma_kernel(int G) {
+  switch (G) {
+    case 1: return batched_ffma<BR, 1>;
+    case 2: return batched_ffma<BR, 2>;
+    case 4: return batched_ffma<BR, 4>;
+    case 8: return batched_ffma<BR, 8>;
+    case 16: return batched_ffma<BR, 16>;
+    case 32: return batched_ffma<BR, 32>;
+    default: return nullptr;
+  }
+}
+
+// The kernel of a class, with its dynamic shared memory per block.
+ClassKernel class_kernel(loops_dtype dtype, const BatchClass& c, int* smem) {
+  *smem = 0;
+  if (c.kind == 0) {
+    switch (dtype) {
+      case LOOPS_F32: return csr_kernel<TrF32>(c.G, c.vpl);
+      case LOOPS_F16: return csr_kernel<TrF16>(c.G, c.vpl);
+      case LOOPS_BF16: return csr_kernel<TrBF16>(c.G, c.vpl);
+      default: return nullptr;
+    }
+  }
+  if (c.kind == 1) {
+    if (dtype != LOOPS_F32) return nullptr;
+    return c.br == 8 ? ffma_kernel<8>(c.G) : ffma_kernel<16>(c.G);
+  }
+  *smem = kHmmaSmemPerWarp * 8;
+  if (dtype == LOOPS_F16) return batched_hmma<__half>;
+  if (dtype == LOOPS_BF16) return batched_hmma<__nv_bfloat16>;
+  return nullptr;
+}
+
+template <class Tr>
+cudaError_t launch_reduces(const BatchLaunch& L, cudaStream_t s) {
   if (L.n_splits > 0) {
     batched_split_reduce<Tr><<<(unsigned)L.n_splits, 128, 0, s>>>(L.descs, L.splits);
     cudaError_t e = cudaGetLastError();
@@ -367,43 +534,64 @@ cudaError_t launch_batched_t(const BatchLaunch& L, cudaStream_t s) {
   }
   if (L.n_bsplits > 0) {
     batched_bsplit_reduce<Tr><<<(unsigned)L.n_bsplits, 256, 0, s>>>(L.descs, L.bsplits);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
   }
-  return rec(3);
+  return cudaSuccess;
 }
 
 }  // namespace
 
-cudaError_t launch_batched(loops_dtype dtype, int32_t br, const BatchLaunch& L, cudaStream_t s) {
-  switch (dtype) {
-    case LOOPS_F32: return br == 8 ? launch_batched_t<TrF32, 8>(L, s) : launch_batched_t<TrF32, 16>(L, s);
-    case LOOPS_F16: return launch_batched_t<TrF16, 16>(L, s);
-    case LOOPS_BF16: return launch_batched_t<TrBF16, 16>(L, s);
-    default: return cudaErrorInvalidValue;
-  }
-}
-
-int batched_grid_blocks(loops_dtype dtype, int32_t br, int smem_per_warp) {
+int batched_class_grid(loops_dtype dtype, const BatchClass& c) {
+  int smem = 0;
+  ClassKernel k = class_kernel(dtype, c, &smem);
+  if (!k) return 0;
   int dev = 0, sms = 152, per_sm = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int smem = smem_per_warp * 8;
-  cudaError_t e = cudaSuccess;
-  switch (dtype) {
-    case LOOPS_F32:
-      e = br == 8 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_persistent<TrF32, 8>, 256, smem)
-                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_persistent<TrF32, 16>, 256, smem);
-      break;
-    case LOOPS_F16:
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_persistent<TrF16, 16>, 256, smem);
-      break;
-    default:
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_persistent<TrBF16, 16>, 256, smem);
-      break;
+  if (smem > 48 * 1024 && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
   }
-  if (e != cudaSuccess || per_sm < 1) per_sm = 1;
-  return sms * per_sm;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, smem) != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  // no more blocks than the class has tasks for their warps
+  const int64_t need = (c.n_tasks + 7) / 8;
+  return (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * per_sm, need));
+}
+
+cudaError_t launch_batched(loops_dtype dtype, const BatchLaunch& L, cudaStream_t s) {
+  // timing events become event nodes of the captured graph (external records)
+  auto rec = [&](int i) {
+    return L.tev ? cudaEventRecordWithFlags(L.tev[i], s, cudaEventRecordExternal) : cudaSuccess;
+  };
+  cudaError_t e = rec(0);
+  if (e == cudaSuccess && L.n_classes > 0)
+    e = cudaMemsetAsync(L.counters, 0, sizeof(unsigned long long) * (size_t)L.n_classes, s);
+  for (int i = 0; i < L.n_classes && e == cudaSuccess; ++i) {
+    const BatchClass& c = L.classes[i];
+    int smem = 0;
+    ClassKernel k = class_kernel(dtype, c, &smem);
+    if (!k) return cudaErrorInvalidValue;
+    if (smem > 48 * 1024) {
+      e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      if (e != cudaSuccess) break;
+    }
+    k<<<c.grid, 256, smem, s>>>(L.descs, L.tasks + c.first, c.n_tasks, L.counters + i);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = rec(1);
+  if (e == cudaSuccess) e = rec(2);
+  if (e != cudaSuccess) return e;
+  switch (dtype) {
+    case LOOPS_F32: e = launch_reduces<TrF32>(L, s); break;
+    case LOOPS_F16: e = launch_reduces<TrF16>(L, s); break;
+    case LOOPS_BF16: e = launch_reduces<TrBF16>(L, s); break;
+    default: return cudaErrorInvalidValue;
+  }
+  if (e != cudaSuccess) return e;
+  return rec(3);
 }
 
 }  // namespace loops

@@ -22,8 +22,8 @@ struct BatchState {
   int2* d_splits = nullptr;
   int2* d_bsplits = nullptr;
   int64_t n_tasks = 0, n_splits = 0, n_bsplits = 0;
-  int grid = 0, smem_per_warp = 0;
-  unsigned long long* d_counter = nullptr;  // task counter of the dynamic schedule
+  std::vector<BatchClass> classes;    // task classes, one persistent kernel each
+  unsigned long long* d_counters = nullptr;  // one task counter per class
   cudaStream_t cap = nullptr;         // capture stream
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -31,6 +31,11 @@ struct BatchState {
   bool copied_once = false;
   int64_t device_bytes = 0;
   int64_t total_nnz = 0, total_rows = 0;
+  std::vector<uint8_t> owned;         // subs[m] is owned (freed with the batch) or borrowed
+  int32_t tau_source = 0;             // 0 given, 1 timed autotuner, 2 performance model
+  double model_gflops = NAN;          // Eq. 2 prediction for the per-matrix choice
+  double model_measured_gflops = NAN; // the per-matrix choice, measured
+  double timed_best_gflops = NAN;     // the best single-threshold candidate, measured
   cudaEvent_t tev[4] = {nullptr, nullptr, nullptr, nullptr};  // caller's timing events
   bool timing = false;
   // loops_spmm_batched_host: one device staging area (every B, then every C, dense rows)
@@ -50,11 +55,12 @@ void batch_set_timing(BatchState* b, const cudaEvent_t* ev) {
 
 void destroy_batch(BatchState* b) {
   if (!b) return;
-  for (auto* s : b->subs) destroy_plan(s);
+  for (size_t m = 0; m < b->subs.size(); ++m)
+    if (b->subs[m] && (m >= b->owned.size() || b->owned[m])) destroy_plan(b->subs[m]);
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   if (b->h_desc) cudaFreeHost(b->h_desc);
-  void* ptrs[] = {b->d_desc, b->d_tasks, b->d_splits, b->d_bsplits, b->d_counter, b->stage};
+  void* ptrs[] = {b->d_desc, b->d_tasks, b->d_splits, b->d_bsplits, b->d_counters, b->stage};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (b->cap) cudaStreamDestroy(b->cap);
@@ -63,7 +69,7 @@ void destroy_batch(BatchState* b) {
 }
 
 // Library kernels one call launches, and the task classes (one persistent kernel each).
-int batch_classes(const BatchState* b) { return b->n_tasks > 0 ? 1 : 0; }
+int batch_classes(const BatchState* b) { return (int)b->classes.size(); }
 int batch_kernels_per_call(const BatchState* b) {
   return batch_classes(b) + (b->n_splits > 0) + (b->n_bsplits > 0);
 }
@@ -72,35 +78,50 @@ namespace {
 
 int elems_per_16b(loops_dtype d) { return d == LOOPS_F32 ? 4 : 8; }
 
-// Schedule of the persistent batched launch: task order (1 matrix by matrix, 0 by cost) and
-// task claiming (1 dynamic, from a counter; 0 static round-robin). LOOPS_BATCH_ORDER and
-// LOOPS_BATCH_DYNAMIC in the environment override the defaults (for measurement).
-int env_int(const char* name, int dflt) {
-  const char* v = std::getenv(name);
-  return v && *v ? std::atoi(v) : dflt;
+int next_pow2(int64_t x) {
+  int p = 1;
+  while (p < x && p < 32) p <<= 1;
+  return p;
 }
-int batch_order() { return env_int("LOOPS_BATCH_ORDER", 1); }
-int batch_dynamic() { return env_int("LOOPS_BATCH_DYNAMIC", 1); }
+
+// Class of a matrix's CSR items: G lanes per item with VPL 16-byte column vectors each (two
+// vectors per lane once a row has at least 16 of them, as in the single-plan kernel).
+void csr_shape(loops_dtype dtype, int64_t N, int32_t* G, int32_t* vpl) {
+  const int64_t nvec = N / elems_per_16b(dtype);
+  *vpl = nvec >= 16 ? 2 : 1;
+  *G = next_pow2(*vpl == 2 ? (nvec + 1) / 2 : nvec);
+}
+
+// Class key: kind, then group width, then vectors per lane (CSR) or tile height (F32 BCSR,
+// 8 or 16, stored as 8 -> 8, 16 -> 0 in the low four bits).
+int64_t class_key(int32_t kind, int32_t G, int32_t low) { return ((int64_t)kind << 16) | (G << 4) | (low & 0xf); }
 
 // Builds the sub-plan of matrix m for the given options, tile height and threshold.
 using SubBuilder = std::function<loops_status(int32_t m, const loops_plan_opts& o, int32_t br, double tau,
                                               loops_plan_s** out)>;
 
-// Build the sub-plans, task list and descriptor tables for a fixed tau.
+// Build the sub-plans (matrix m with tile height brs[m] and threshold taus[m]; or, with
+// `borrowed`, take those sub-plans without owning them), the task list and the descriptor
+// tables.
 loops_status build_batch(const loops_csr* As, const int64_t* Ns, int32_t count, loops_dtype dtype,
-                         const loops_plan_opts& o, int32_t br, double tau, const SubBuilder& sub,
-                         BatchState** out) {
+                         const loops_plan_opts& o, const std::vector<int32_t>& brs, const std::vector<double>& taus,
+                         const SubBuilder& sub, const std::vector<loops_plan_s*>* borrowed, BatchState** out) {
   *out = nullptr;
   BatchState* b = new (std::nothrow) BatchState();
   if (!b) { set_error("host allocation failed"); return LOOPS_ERR_OOM; }
   b->count = count;
   b->dtype = dtype;
-  b->br = br;
-  b->tau = tau;
+  b->br = count > 0 ? brs[0] : 16;
+  b->tau = count > 0 ? taus[0] : 2.0;
+  for (int32_t m = 1; m < count; ++m) {
+    if (brs[(size_t)m] != b->br) b->br = 0;
+    if (!(taus[(size_t)m] == b->tau)) b->tau = NAN;
+  }
   loops_status st = LOOPS_OK;
   const int VE = elems_per_16b(dtype);
   std::vector<BatchTask> tasks;
   std::vector<double> cost;
+  std::vector<int64_t> cls;                       // class key of each task
   std::vector<int2> splits, bsplits;
   for (int32_t m = 0; m < count && !st; ++m) {
     const int64_t N = Ns[m];
@@ -110,12 +131,21 @@ loops_status build_batch(const loops_csr* As, const int64_t* Ns, int32_t count, 
       st = LOOPS_ERR_UNSUPPORTED;
       break;
     }
+    const int32_t br = brs[(size_t)m];
     loops_plan_s* p = nullptr;
-    if ((st = sub(m, o, br, tau, &p))) break;
+    if (borrowed) {
+      p = (*borrowed)[(size_t)m];
+    } else {
+      loops_plan_opts om = o;
+      om.block_rows = br;
+      if ((st = sub(m, om, br, taus[(size_t)m], &p))) break;
+    }
     b->subs.push_back(p);
+    b->owned.push_back(borrowed ? 0 : 1);
     b->total_nnz += As[m].nnz;
     b->total_rows += As[m].n_rows;
-    const int G = (int)(N / VE);
+    int32_t G = 0, vpl = 0;
+    csr_shape(dtype, N, &G, &vpl);
     const int per_round = 32 / G;
     // CSR items: consecutive items (similar length, longest first) up to ~1024 entries
     const CsrDev& c = p->dev.csr;
@@ -127,43 +157,68 @@ loops_status build_batch(const loops_csr* As, const int64_t* Ns, int32_t count, 
       }
       tasks.push_back({m, 0, i, (int32_t)(j - i), 0});
       cost.push_back((double)(nnz + (j - i)) * (double)N);
+      cls.push_back(class_key(0, G, vpl));
       i = j;
     }
-    // BCSR units (most tiles first)
+    // BCSR units (most tiles first): F32 in groups of G lanes (4 columns each), 16-bit one per warp
     const BcsrDev& bd = p->dev.bcsr;
     if (dtype == LOOPS_F32) {
-      for (int64_t q = 0; q < bd.n_units; q += per_round) {
-        const int32_t cnt = (int32_t)std::min<int64_t>(per_round, bd.n_units - q);
+      const int32_t Gf = next_pow2(N / VE);
+      const int rf = 32 / Gf;
+      for (int64_t q = 0; q < bd.n_units; q += rf) {
+        const int32_t cnt = (int32_t)std::min<int64_t>(rf, bd.n_units - q);
         tasks.push_back({m, 1, q, cnt, 0});
         cost.push_back((double)bd.h_unit_tiles[(size_t)q] * br * (double)N);
+        cls.push_back(class_key(1, Gf, br));
       }
     } else {
       for (int64_t q = 0; q < bd.n_units; ++q) {
         tasks.push_back({m, 2, q, 1, 0});
         cost.push_back((double)bd.h_unit_tiles[(size_t)q] * br * (double)N);
+        cls.push_back(class_key(2, 0, 0));
       }
     }
     for (int64_t sidx = 0; sidx < bd.n_split; ++sidx) bsplits.push_back(make_int2(m, (int)sidx));
     for (int64_t sidx = 0; sidx < c.n_split; ++sidx) splits.push_back(make_int2(m, (int)sidx));
   }
   if (st) { destroy_batch(b); return st; }
-  // Task order. Matrix by matrix (tasks of a matrix in decreasing cost): the warps then work
-  // on one or a few matrices at a time, whose B operands stay in L2 while their rows gather
-  // from them. Or (order 0) all tasks by decreasing cost, interleaving the matrices.
+  // Task order: by class (each class is one kernel's contiguous run of the list), then matrix
+  // by matrix, and within a matrix by decreasing cost. The warps of a class kernel claim
+  // tasks in this order, so they work on one or a few matrices at a time, whose B operands
+  // stay in L2 while their rows gather from them.
   std::vector<int64_t> idx(tasks.size());
   for (size_t i = 0; i < idx.size(); ++i) idx[i] = (int64_t)i;
-  const int order = batch_order();
   std::stable_sort(idx.begin(), idx.end(), [&](int64_t x, int64_t y) {
-    if (order == 1 && tasks[(size_t)x].m != tasks[(size_t)y].m) return tasks[(size_t)x].m < tasks[(size_t)y].m;
+    if (cls[(size_t)x] != cls[(size_t)y]) return cls[(size_t)x] < cls[(size_t)y];
+    if (tasks[(size_t)x].m != tasks[(size_t)y].m) return tasks[(size_t)x].m < tasks[(size_t)y].m;
     return cost[(size_t)x] > cost[(size_t)y];
   });
   std::vector<BatchTask> sorted(tasks.size());
   for (size_t i = 0; i < idx.size(); ++i) sorted[i] = tasks[(size_t)idx[i]];
+  for (size_t i = 0; i < idx.size();) {
+    size_t j = i;
+    const int64_t key = cls[(size_t)idx[i]];
+    while (j < idx.size() && cls[(size_t)idx[j]] == key) ++j;
+    BatchClass bc;
+    bc.kind = (int32_t)(key >> 16);
+    bc.G = (int32_t)((key >> 4) & 0xfff);
+    bc.vpl = bc.kind == 0 ? (int32_t)(key & 0xf) : 1;
+    bc.br = (bc.kind == 1 && (key & 0xf) == 8) ? 8 : 16;
+    bc.first = (int64_t)i;
+    bc.n_tasks = (int64_t)(j - i);
+    bc.grid = batched_class_grid(dtype, bc);
+    if (bc.grid <= 0) {
+      set_error("no batched kernel for a task class (kind " + std::to_string(bc.kind) + ", G " +
+                std::to_string(bc.G) + ")");
+      destroy_batch(b);
+      return LOOPS_ERR_STATE;
+    }
+    b->classes.push_back(bc);
+    i = j;
+  }
   b->n_tasks = (int64_t)sorted.size();
   b->n_splits = (int64_t)splits.size();
   b->n_bsplits = (int64_t)bsplits.size();
-  b->smem_per_warp = dtype == LOOPS_F32 ? 0 : (16 * (64 + 8) * 2 + 127) / 128 * 128;  // one 64-column chunk
-  b->grid = batched_grid_blocks(dtype, br, b->smem_per_warp);
   // descriptors (static parts now; B/C pointers per call)
   cudaError_t e = host_malloc((void**)&b->h_desc, sizeof(BatchDesc) * (size_t)std::max(count, 1));
   if (e == cudaSuccess) e = dev_malloc((void**)&b->d_desc, sizeof(BatchDesc) * (size_t)std::max(count, 1));
@@ -176,7 +231,8 @@ loops_status build_batch(const loops_csr* As, const int64_t* Ns, int32_t count, 
   if (e == cudaSuccess && b->n_bsplits) e = dev_malloc((void**)&b->d_bsplits, sizeof(int2) * (size_t)b->n_bsplits);
   if (e == cudaSuccess && b->n_bsplits)
     e = cudaMemcpy(b->d_bsplits, bsplits.data(), sizeof(int2) * (size_t)b->n_bsplits, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && batch_dynamic()) e = dev_malloc((void**)&b->d_counter, sizeof(unsigned long long));
+  if (e == cudaSuccess && !b->classes.empty())
+    e = dev_malloc((void**)&b->d_counters, sizeof(unsigned long long) * b->classes.size());
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_copied, cudaEventDisableTiming);
   if (e != cudaSuccess) { st = cuda_status(e, "batched plan setup"); destroy_batch(b); return st; }
@@ -208,7 +264,6 @@ loops_status build_batch(const loops_csr* As, const int64_t* Ns, int32_t count, 
     d.N = p->N;
     d.n_rows = p->n_rows;
     d.inv_scale = (float)(1.0 / p->scale);
-    d.G = (int32_t)(p->N / VE);
     b->device_bytes += p->dev.device_bytes;
   }
   *out = b;
@@ -219,16 +274,15 @@ cudaError_t run_batch(BatchState* b, cudaStream_t s) {
   BatchLaunch L;
   L.descs = b->d_desc;
   L.tasks = b->d_tasks;
-  L.n_tasks = b->n_tasks;
+  L.classes = b->classes.data();
+  L.n_classes = (int)b->classes.size();
+  L.counters = b->d_counters;
   L.splits = b->d_splits;
   L.n_splits = b->n_splits;
   L.bsplits = b->d_bsplits;
   L.n_bsplits = b->n_bsplits;
-  L.grid = b->grid;
-  L.smem_per_warp = b->smem_per_warp;
-  L.counter = b->d_counter;
   L.tev = b->timing ? b->tev : nullptr;
-  return launch_batched(b->dtype, b->br, L, s);
+  return launch_batched(b->dtype, L, s);
 }
 
 // Per call: refresh the descriptors' dense pointers if they changed (one upload from the
@@ -275,6 +329,198 @@ loops_status spmm_batch(BatchState* b, const void* const* Bs, const int64_t* ldb
     }
   }
   return cuda_status(cudaGraphLaunch(b->exec, s), "graph launch");
+}
+
+// Whole-batch time of one candidate (the L2 flushed before each of three timed calls, best
+// kept), on the autotuner's operands.
+loops_status time_batch(BatchState* b, const std::vector<const void*>& Bs, const std::vector<void*>& Cs,
+                        const std::vector<int64_t>& ld, L2Flush& flush, cudaEvent_t e0, cudaEvent_t e1,
+                        cudaStream_t s, float* ms_out) {
+  loops_status st = LOOPS_OK;
+  float ms = INFINITY;
+  for (int it = 0; it < 5 && !st; ++it) {
+    if (it >= 2) {
+      if ((st = cuda_status(flush.run(s), "L2 flush"))) break;
+      cudaEventRecord(e0, s);
+    }
+    st = spmm_batch(b, Bs.data(), ld.data(), Cs.data(), ld.data(), nullptr, s);
+    if (it >= 2) {
+      cudaEventRecord(e1, s);
+      if (!st) st = cuda_status(cudaEventSynchronize(e1), "autotune timing");
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      ms = std::min(ms, t);
+    }
+  }
+  *ms_out = ms;
+  return st;
+}
+
+// Autotuner of a batch. Candidates with one split threshold for every matrix (and, for F32,
+// the other tile height) are built and timed as whole batches. With host-resident matrices
+// the performance model then proposes one more candidate with a threshold and tile height
+// per matrix: Eq. 2 is fitted to the timed candidates' throughput as a function of their
+// total CSR-part and BCSR-part work, and Eq. 3 is applied per matrix (coordinate ascent on
+// the predicted throughput of the whole batch, over each matrix's candidate splits). That
+// candidate reuses the sub-plans built for the timed ones and is timed the same way; the
+// fastest candidate is kept.
+loops_status autotune_batch(const loops_csr* As, const int64_t* Ns, int32_t count, loops_dtype dtype,
+                            const loops_plan_opts& o, int32_t br, const SubBuilder& sub, bool use_model,
+                            cudaStream_t s, BatchState** out) {
+  *out = nullptr;
+  struct Cand {
+    double tau;
+    int32_t br;
+    BatchState* b = nullptr;
+    float ms = INFINITY;
+  };
+  std::vector<Cand> cands;
+  for (double t : {(double)INFINITY, 4.0, 2.0, 1.25, 0.0}) cands.push_back({t, br});
+  if (dtype == LOOPS_F32 && o.block_rows == 0)
+    for (double t : {4.0, 2.0, 1.25}) cands.push_back({t, br == 16 ? 8 : 16});
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  std::vector<void*> bufs;
+  std::vector<const void*> Bs((size_t)count);
+  std::vector<void*> Cs((size_t)count);
+  std::vector<int64_t> ld((size_t)count);
+  const int64_t eb = dtype == LOOPS_F32 ? 4 : 2;
+  cudaError_t e = cudaSuccess;
+  for (int32_t m = 0; m < count && e == cudaSuccess; ++m) {
+    void *pb = nullptr, *pc = nullptr;
+    e = dev_malloc(&pb, (size_t)std::max<int64_t>(As[m].n_cols * Ns[m] * eb, 16));
+    if (e == cudaSuccess) e = dev_malloc(&pc, (size_t)std::max<int64_t>(As[m].n_rows * Ns[m] * 4, 16));
+    if (e == cudaSuccess) e = cudaMemsetAsync(pb, 0x3C, (size_t)(As[m].n_cols * Ns[m] * eb), s);
+    bufs.push_back(pb);
+    bufs.push_back(pc);
+    Bs[(size_t)m] = pb;
+    Cs[(size_t)m] = pc;
+    ld[(size_t)m] = Ns[m];
+  }
+  loops_status st = cuda_status(e, "autotune buffers");
+  L2Flush flush;
+  for (Cand& c : cands) {
+    if (st) break;
+    const std::vector<int32_t> brs((size_t)count, c.br);
+    const std::vector<double> taus((size_t)count, c.tau);
+    if ((st = build_batch(As, Ns, count, dtype, o, brs, taus, sub, nullptr, &c.b))) break;
+    st = time_batch(c.b, Bs, Cs, ld, flush, e0, e1, s, &c.ms);
+  }
+  double flops = 0.0;
+  for (int32_t m = 0; m < count; ++m) flops += 2.0 * (double)As[m].nnz * (double)Ns[m];
+  size_t best_c = 0;
+  for (size_t c = 1; c < cands.size(); ++c)
+    if (cands[c].ms < cands[best_c].ms) best_c = c;
+  BatchState* model = nullptr;
+  float model_ms = INFINITY;
+  double model_pred = NAN;
+  if (!st && use_model && count > 0) {
+    // per-matrix (x, y) of every candidate, from row-block profiles
+    const int32_t kpad = k_pad_for(dtype);
+    std::vector<std::vector<SplitWork>> w((size_t)count, std::vector<SplitWork>(cands.size()));
+    BlockProfile prof;
+    for (int32_t m = 0; m < count; ++m) {
+      for (int32_t h : {8, 16}) {
+        bool used = false;
+        for (const Cand& c : cands) used = used || c.br == h;
+        if (!used) continue;
+        block_profile(&As[m], h, prof);
+        for (size_t c = 0; c < cands.size(); ++c)
+          if (cands[c].br == h) w[(size_t)m][c] = split_work(prof, cands[c].tau, kpad, Ns[m]);
+      }
+    }
+    std::vector<double> X(cands.size(), 0.0), Y(cands.size(), 0.0), P(cands.size());
+    for (size_t c = 0; c < cands.size(); ++c) {
+      for (int32_t m = 0; m < count; ++m) {
+        X[c] += w[(size_t)m][c].x;
+        Y[c] += w[(size_t)m][c].y;
+      }
+      P[c] = flops / (std::max((double)cands[c].ms, 1e-6) * 1e-3) / 1e9;
+    }
+    double a[5];
+    if (fit_perf_model(X.data(), Y.data(), P.data(), (int)cands.size(), a)) {
+      // Eq. 3 per matrix: coordinate ascent from the best timed candidate
+      std::vector<size_t> pick((size_t)count, best_c);
+      double x = X[best_c], y = Y[best_c];
+      double cur = eval_perf_model(a, x, y);
+      for (int pass = 0; pass < 3; ++pass) {
+        bool moved = false;
+        for (int32_t m = 0; m < count; ++m) {
+          const SplitWork& now = w[(size_t)m][pick[(size_t)m]];
+          for (size_t c = 0; c < cands.size(); ++c) {
+            const SplitWork& alt = w[(size_t)m][c];
+            const double nx = x - now.x + alt.x, ny = y - now.y + alt.y;
+            const double pr = eval_perf_model(a, nx, ny);
+            if (pr > cur * (1.0 + 1e-9)) {
+              cur = pr;
+              x = nx;
+              y = ny;
+              pick[(size_t)m] = c;
+              moved = true;
+              break;
+            }
+          }
+        }
+        if (!moved) break;
+      }
+      bool uniform = true;
+      for (int32_t m = 1; m < count; ++m) uniform = uniform && pick[(size_t)m] == pick[0];
+      model_pred = cur;
+      if (!uniform) {
+        std::vector<int32_t> brs((size_t)count);
+        std::vector<double> taus((size_t)count);
+        std::vector<loops_plan_s*> subs((size_t)count);
+        for (int32_t m = 0; m < count; ++m) {
+          const Cand& c = cands[pick[(size_t)m]];
+          brs[(size_t)m] = c.br;
+          taus[(size_t)m] = c.tau;
+          subs[(size_t)m] = c.b->subs[(size_t)m];
+        }
+        if (!(st = build_batch(As, Ns, count, dtype, o, brs, taus, sub, &subs, &model)))
+          st = time_batch(model, Bs, Cs, ld, flush, e0, e1, s, &model_ms);
+      }
+    }
+  }
+  cudaStreamSynchronize(s);
+  for (void* q : bufs)
+    if (q) cudaFree(q);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st) {
+    if (model) destroy_batch(model);
+    for (Cand& c : cands)
+      if (c.b) destroy_batch(c.b);
+    return st;
+  }
+  BatchState* best = nullptr;
+  const double timed_gflops = flops / (std::max((double)cands[best_c].ms, 1e-6) * 1e-3) / 1e9;
+  if (model && model_ms < cands[best_c].ms) {
+    // the per-matrix candidate wins: it takes ownership of the sub-plans it borrowed
+    for (int32_t m = 0; m < count; ++m) {
+      for (Cand& c : cands)
+        if (c.b && c.b->subs[(size_t)m] == model->subs[(size_t)m]) c.b->subs[(size_t)m] = nullptr;
+      model->owned[(size_t)m] = 1;
+    }
+    best = model;
+    best->tau_source = 2;
+    for (Cand& c : cands) destroy_batch(c.b);
+  } else {
+    if (model) destroy_batch(model);  // borrowed sub-plans stay with their candidates
+    best = cands[best_c].b;
+    cands[best_c].b = nullptr;
+    best->tau_source = 1;
+    for (Cand& c : cands)
+      if (c.b) destroy_batch(c.b);
+  }
+  best->model_gflops = model_pred;
+  best->model_measured_gflops = model ? flops / (std::max((double)model_ms, 1e-6) * 1e-3) / 1e9 : NAN;
+  best->timed_best_gflops = timed_gflops;
+  // a plan built during tuning has captured the autotuner's operands: drop its graph state so
+  // the first real call uploads the caller's descriptors
+  best->copied_once = false;
+  *out = best;
+  return LOOPS_OK;
 }
 
 }  // namespace
@@ -347,75 +593,11 @@ static loops_status plan_batched(const loops_csr* As, const int64_t* Ns, int32_t
   };
   BatchState* best = nullptr;
   if (o.tau >= 0.0) {
-    if ((st = build_batch(As, Ns, count, dtype, o, br, o.tau, sub, &best))) return st;
+    const std::vector<int32_t> brs((size_t)count, br);
+    const std::vector<double> taus((size_t)count, o.tau);
+    if ((st = build_batch(As, Ns, count, dtype, o, brs, taus, sub, nullptr, &best))) return st;
   } else {
-    // autotune: split threshold (and, for F32, the tile height) by timing the whole batch
-    struct Cand { double tau; int32_t br; };
-    std::vector<Cand> cands;
-    for (double t : {(double)INFINITY, 4.0, 2.0, 1.25, 0.0}) cands.push_back({t, br});
-    if (dtype == LOOPS_F32 && o.block_rows == 0) cands.push_back({2.0, br == 16 ? 8 : 16});
-    float best_ms = INFINITY;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    std::vector<void*> bufs;
-    std::vector<const void*> Bs((size_t)count);
-    std::vector<void*> Cs((size_t)count);
-    std::vector<int64_t> ld((size_t)count);
-    const int64_t eb = dtype == LOOPS_F32 ? 4 : 2;
-    cudaError_t e = cudaSuccess;
-    for (int32_t m = 0; m < count && e == cudaSuccess; ++m) {
-      void *pb = nullptr, *pc = nullptr;
-      e = dev_malloc(&pb, (size_t)std::max<int64_t>(As[m].n_cols * Ns[m] * eb, 16));
-      if (e == cudaSuccess) e = dev_malloc(&pc, (size_t)std::max<int64_t>(As[m].n_rows * Ns[m] * 4, 16));
-      if (e == cudaSuccess) e = cudaMemsetAsync(pb, 0x3C, (size_t)(As[m].n_cols * Ns[m] * eb), s);
-      bufs.push_back(pb);
-      bufs.push_back(pc);
-      Bs[(size_t)m] = pb;
-      Cs[(size_t)m] = pc;
-      ld[(size_t)m] = Ns[m];
-    }
-    st = cuda_status(e, "autotune buffers");
-    L2Flush flush;
-    for (const Cand& c : cands) {
-      if (st) break;
-      loops_plan_opts oc = o;
-      oc.block_rows = c.br;
-      BatchState* b = nullptr;
-      if ((st = build_batch(As, Ns, count, dtype, oc, c.br, c.tau, sub, &b))) break;
-      float ms = INFINITY;
-      for (int it = 0; it < 5 && !st; ++it) {
-        if (it >= 2) {
-          if ((st = cuda_status(flush.run(s), "L2 flush"))) break;
-          cudaEventRecord(e0, s);
-        }
-        st = spmm_batch(b, Bs.data(), ld.data(), Cs.data(), ld.data(), nullptr, s);
-        if (it >= 2) {
-          cudaEventRecord(e1, s);
-          if (!st) st = cuda_status(cudaEventSynchronize(e1), "autotune timing");
-          float t = 0.f;
-          cudaEventElapsedTime(&t, e0, e1);
-          ms = std::min(ms, t);
-        }
-      }
-      if (!st && ms < best_ms) {
-        best_ms = ms;
-        if (best) destroy_batch(best);
-        best = b;
-        br = c.br;
-      } else {
-        destroy_batch(b);
-      }
-    }
-    cudaStreamSynchronize(s);
-    for (void* q : bufs)
-      if (q) cudaFree(q);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    if (st) { if (best) destroy_batch(best); return st; }
-    // a plan built during tuning has captured dummy pointers: drop its graph state so the
-    // first real call uploads the caller's descriptors
-    best->copied_once = false;
+    if ((st = autotune_batch(As, Ns, count, dtype, o, br, sub, !device, s, &best))) return st;
   }
   loops_plan_s* p = new (std::nothrow) loops_plan_s();
   if (!p) { destroy_batch(best); set_error("host allocation failed"); return LOOPS_ERR_OOM; }
@@ -597,6 +779,10 @@ loops_status loops_plan_batched_stats(loops_plan_t p, loops_batched_info* out) {
   out->nnz = b->total_nnz;
   out->nnz_bcsr = p->nnz_bcsr;
   out->device_bytes = b->device_bytes + b->stage_bytes;
+  out->tau_source = b->tau_source;
+  out->model_gflops = b->model_gflops;
+  out->model_measured_gflops = b->model_measured_gflops;
+  out->timed_best_gflops = b->timed_best_gflops;
   return LOOPS_OK;
 }
 

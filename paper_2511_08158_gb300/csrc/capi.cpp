@@ -497,6 +497,91 @@ loops_status autotune_tau(const PlanBuilder& build, int64_t n_rows, int64_t n_co
   return st;
 }
 
+// Split threshold from the performance model (Eq. 2 and Eq. 3, restated in perf_model.cpp):
+// the warm-up candidates (the timed autotuner's thresholds, each distinct split once) are
+// built and timed (L2 flushed before each timed call), Eq. 2 is fitted to their (CSR work,
+// BCSR work, GFLOP/s), and Eq. 3 picks the threshold of highest predicted throughput among
+// +inf, 0 and the matrix's distinct block densities -- including thresholds never timed.
+loops_status model_tau(const PlanBuilder& build, const BlockProfile& prof, int64_t n_rows, int64_t n_cols,
+                       int64_t nnz, int64_t N, loops_dtype dtype, int32_t split_len, cudaStream_t s,
+                       double* tau_out, double* pred_out, double coef[5]) {
+  *tau_out = 2.0;
+  *pred_out = NAN;
+  for (int i = 0; i < 5; ++i) coef[i] = 0.0;
+  if (nnz == 0 || N == 0 || n_rows == 0) return LOOPS_OK;
+  const int32_t kpad = k_pad_for(dtype);
+  const double flops = 2.0 * (double)nnz * (double)N;
+  const int64_t eb = dense_elem_bytes(dtype), ec = out_elem_bytes(dtype);
+  void *dB = nullptr, *dC = nullptr;
+  cudaError_t e = dev_malloc(&dB, (size_t)std::max<int64_t>(n_cols * N * eb, 16));
+  if (e == cudaSuccess) e = dev_malloc(&dC, (size_t)std::max<int64_t>(n_rows * N * ec, 16));
+  if (e == cudaSuccess) e = fill_finite(dB, n_cols * N * eb, s);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  loops_status st = cuda_status(e, "model setup");
+  L2Flush flush;
+  std::vector<double> xs, ys, ps;
+  loops_plan_opts o;
+  loops_plan_opts_default(&o);
+  o.split_len = split_len;
+  o.tile_min = 0;
+  const double warm[] = {(double)INFINITY, 8.0, 4.0, 3.0, 2.0, 1.5, 1.25, 0.0};
+  std::vector<double> taus;
+  for (double tau : warm) {
+    if (st) break;
+    const SplitWork w = split_work(prof, tau, kpad, N);
+    bool dup = false;
+    for (size_t i = 0; i < xs.size(); ++i) dup = dup || (xs[i] == w.x && ys[i] == w.y);
+    if (dup) continue;
+    loops_plan_s* p = nullptr;
+    if ((st = build(o, tau, &p))) break;
+    float best_ms = INFINITY;
+    for (int it = 0; it < 7 && !st; ++it) {
+      if ((st = run_spmm(p, dB, N, nullptr, dC, N, s))) break;  // it 0, 1: warm-up
+      if (it < 2) continue;
+      if ((st = cuda_status(flush.run(s), "L2 flush"))) break;
+      cudaEventRecord(e0, s);
+      st = run_spmm(p, dB, N, nullptr, dC, N, s);
+      cudaEventRecord(e1, s);
+      if (!st) st = cuda_status(cudaEventSynchronize(e1), "model timing");
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      best_ms = std::min(best_ms, ms);
+    }
+    destroy_plan(p);
+    if (st) break;
+    xs.push_back(w.x);
+    ys.push_back(w.y);
+    taus.push_back(tau);
+    ps.push_back(flops / (std::max((double)best_ms, 1e-6) * 1e-3) / 1e9);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (dB) cudaFree(dB);
+  if (dC) cudaFree(dC);
+  if (st) return st;
+  if (!fit_perf_model(xs.data(), ys.data(), ps.data(), (int)xs.size(), coef)) {
+    // degenerate samples: the best measured threshold
+    size_t b = 0;
+    for (size_t i = 1; i < ps.size(); ++i)
+      if (ps[i] > ps[b]) b = i;
+    if (!taus.empty()) *tau_out = taus[b];
+    return LOOPS_OK;
+  }
+  double best = -INFINITY;
+  for (double tau : tau_grid(prof, 64)) {
+    const SplitWork w = split_work(prof, tau, kpad, N);
+    const double pr = eval_perf_model(coef, w.x, w.y);
+    if (pr > best) {
+      best = pr;
+      *tau_out = tau;
+    }
+  }
+  *pred_out = best;
+  return LOOPS_OK;
+}
+
 // Paper mode with the boundary from Eq. 1: time the pure CSR plan (the paper's pure vector-unit
 // configuration) and the pure BCSR plan (rows from 0 on in BCSR) on synthetic B, take each
 // part's throughput TP = rows / time, and choose r_b so that the two parts, running side by
@@ -639,7 +724,21 @@ loops_status loops_plan(const loops_csr* A, int64_t N, loops_dtype dtype, const 
   std::vector<double> vals;
   read_vals_f64(A, vals);
   double tau = o.tau;
-  if (tau < 0.0 && !o.contiguous_split) {
+  int32_t tau_source = o.contiguous_split ? 3 : 0;
+  double model_pred = NAN, coef[5] = {0, 0, 0, 0, 0};
+  if (tau == LOOPS_TAU_MODEL && !o.contiguous_split) {
+    const PlanBuilder host_build = [&](const loops_plan_opts& oc, double t, loops_plan_s** q) {
+      return make_plan(A, vals.data(), N, dtype, oc, br, t, false, q);
+    };
+    BlockProfile prof;
+    block_profile(A, br, prof);
+    if ((st = model_tau(host_build, prof, A->n_rows, A->n_cols, A->nnz, N, dtype, o.split_len, (cudaStream_t)stream,
+                        &tau, &model_pred, coef)))
+      return st;
+    o.tile_min = 0;
+    tau_source = 2;
+  } else if (tau < 0.0 && !o.contiguous_split) {
+    tau_source = 1;
     int32_t tmin = o.tile_min;
     const PlanBuilder host_build = [&](const loops_plan_opts& oc, double t, loops_plan_s** q) {
       return make_plan(A, vals.data(), N, dtype, oc, br, t, false, q);
@@ -659,6 +758,9 @@ loops_status loops_plan(const loops_csr* A, int64_t N, loops_dtype dtype, const 
   }
   loops_plan_s* p = nullptr;
   if ((st = make_plan(A, vals.data(), N, dtype, o, br, tau, false, &p))) return st;
+  p->tau_source = tau_source;
+  p->model_gflops = model_pred;
+  for (int i = 0; i < 5; ++i) p->model_coef[i] = coef[i];
   if (o.want_backward) {
     std::vector<int64_t> trp;
     std::vector<int32_t> tci;
@@ -724,6 +826,10 @@ loops_status loops_plan_device(const loops_csr* A, int64_t N, loops_dtype dtype,
     return make_plan_device(d, nullptr, scale, N, dtype, oc, br, t, false, false, s, q);
   };
   double tau = o.tau;
+  if (tau == LOOPS_TAU_MODEL && !o.contiguous_split) {
+    set_error("the performance model (LOOPS_TAU_MODEL) needs host CSR arrays: use loops_plan");
+    return LOOPS_ERR_UNSUPPORTED;
+  }
   if (tau < 0.0 && !o.contiguous_split) {
     int32_t tmin = o.tile_min;
     if ((st = autotune_tau(dev_build, A->n_rows, A->n_cols, A->nnz, N, dtype, o.split_len,
@@ -737,6 +843,7 @@ loops_status loops_plan_device(const loops_csr* A, int64_t N, loops_dtype dtype,
   }
   loops_plan_s* p = nullptr;
   if ((st = make_plan_device(d, nullptr, scale, N, dtype, o, br, tau, true, false, s, &p))) return st;
+  p->tau_source = o.contiguous_split ? 3 : (o.tau < 0.0 ? 1 : 0);
   if (o.want_backward) {
     int64_t* trp = nullptr;
     int32_t* tci = nullptr;
@@ -822,6 +929,9 @@ loops_status plan_info_of(const loops_plan_s* p, loops_plan_info* out) {
   out->device_bytes = p->dev.device_bytes + p->other_bytes + p->vmap.bytes;
   out->r_boundary = p->opts.contiguous_split ? p->opts.r_boundary : -1;
   out->tile_min = p->tile_min;
+  out->tau_source = p->tau_source;
+  out->model_gflops = p->model_gflops;
+  for (int i = 0; i < 5; ++i) out->model_coef[i] = p->model_coef[i];
   if (p->transposed)
     out->device_bytes += p->transposed->dev.device_bytes + p->transposed->other_bytes + p->transposed->vmap.bytes;
   return LOOPS_OK;

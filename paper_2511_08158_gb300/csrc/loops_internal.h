@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
+
 #include <string>
 #include <vector>
 
@@ -236,10 +238,9 @@ struct BatchDesc {
   const float* col_scale;
   int64_t ldb, ldc, N, n_rows;
   float inv_scale;
-  int32_t G;                           // lanes per CSR item / F32 block: N / elements per 16 B
 };
 
-// One task of the persistent batched kernel: kind 0 CSR items [first, first + count) of
+// One task of a persistent batched kernel: kind 0 CSR items [first, first + count) of
 // matrix m, kind 1 F32 BCSR units [first, first + count), kind 2 one F16/BF16 BCSR unit.
 struct BatchTask {
   int32_t m;
@@ -249,19 +250,31 @@ struct BatchTask {
   int32_t pad;
 };
 
+// A class of tasks: one kind and one lane-group width (G lanes per CSR item or F32 unit, VPL
+// 16-byte vectors per lane), run by one persistent kernel specialised for it over the tasks
+// [first, first + n_tasks) of the list, with `grid` blocks of 256 threads.
+struct BatchClass {
+  int32_t kind;
+  int32_t G;
+  int32_t vpl;
+  int32_t br;                          // tile height of an F32 BCSR class (8 or 16)
+  int32_t grid;
+  int64_t first;
+  int64_t n_tasks;
+};
+
 struct BatchLaunch {
   const BatchDesc* descs;
   const BatchTask* tasks;
-  int64_t n_tasks;
+  const BatchClass* classes;           // host array
+  int n_classes;
+  unsigned long long* counters;        // one task counter per class (device), zeroed per call
   const int2* splits;                  // (matrix, split row) pairs
   int64_t n_splits;
   const int2* bsplits;                 // (matrix, split block) pairs
   int64_t n_bsplits;
-  int grid;
-  int smem_per_warp;
-  unsigned long long* counter;         // task counter of the dynamic schedule (null: static)
-  const cudaEvent_t* tev;              // optional timing events: [0]/[1] around the persistent
-                                       // kernel, [2]/[3] around the partial-sum launches
+  const cudaEvent_t* tev;              // optional timing events: [0]/[1] around the class
+                                       // kernels, [2]/[3] around the partial-sum launches
 };
 
 struct BatchState;
@@ -315,6 +328,9 @@ struct loops_plan_s {
   // partition counts (canonical): CSR-part rows and entries, BCSR blocks and tiles
   int64_t n_csr_rows, nnz_csr, n_rb, n_tiles;
   bool device_built;                   // built by loops_plan_device (no host canonical copy)
+  int32_t tau_source = 0;              // 0 given, 1 timed autotuner, 2 Eq. 2/3 model, 3 Eq. 1 / contiguous
+  double model_gflops = NAN;           // Eq. 2 prediction for the chosen split (model mode)
+  double model_coef[5] = {0, 0, 0, 0, 0};
   bool has_vmap;                       // value maps present (loops_plan_set_values works)
 };
 
@@ -353,8 +369,10 @@ cudaError_t launch_csr(const loops_plan_s* p, const CsrDev& d, const DenseArgs& 
 cudaError_t launch_bcsr(const loops_plan_s* p, const BcsrDev& d, const DenseArgs& a, cudaStream_t s);
 cudaError_t launch_sddmm(const loops_plan_s* p, const void* dC, int64_t lddc, const void* B,
                          int64_t ldb, void* dvals, const float* dc_scale, const float* b_scale, cudaStream_t s);
-cudaError_t launch_batched(loops_dtype dtype, int32_t br, const BatchLaunch& L, cudaStream_t s);
-int batched_grid_blocks(loops_dtype dtype, int32_t br, int smem_per_warp);
+cudaError_t launch_batched(loops_dtype dtype, const BatchLaunch& L, cudaStream_t s);
+// Blocks of a class kernel: resident blocks per SM x SMs, at most one per 8 tasks; 0 if the
+// class has no kernel.
+int batched_class_grid(loops_dtype dtype, const BatchClass& c);
 
 // Plan construction shared by the single and batched entry points (capi.cpp). `light` plans
 // (sub-plans of a batch) get no side stream, events or error word.
@@ -413,6 +431,24 @@ struct L2Flush {
   L2Flush& operator=(const L2Flush&) = delete;
   cudaError_t run(cudaStream_t s);
 };
+
+// ------------------------------------------------------------------ performance model
+// Per row block of B_r rows: stored entries and distinct columns (perf_model.cpp).
+struct BlockProfile {
+  int32_t br = 16;
+  std::vector<int64_t> nnz, ucols;
+};
+struct SplitWork {
+  double x, y;  // CSR-part work (entries x N), BCSR-part work (tiles x B_r x N)
+};
+void block_profile(const loops_csr* A, int32_t br, BlockProfile& out);
+SplitWork split_work(const BlockProfile& p, double tau, int32_t kpad, int64_t N);
+// Thresholds worth predicting: +inf, the distinct block densities (quantiles if more than
+// max_cands), 0.
+std::vector<double> tau_grid(const BlockProfile& p, size_t max_cands);
+// Eq. 2: perf(x, y) = a0 + a1 x + a2 y + a3 x^2 + a4 y^2, least squares over n samples.
+bool fit_perf_model(const double* x, const double* y, const double* perf, int n, double a[5]);
+double eval_perf_model(const double a[5], double x, double y);
 
 cudaError_t launch_set_values(const loops_plan_s* p, const void* vals, loops_dtype vd, cudaStream_t s);
 cudaError_t launch_cast_scaled(const float* X, int64_t rows, int64_t cols, int64_t ldx,

@@ -122,3 +122,13 @@ def test_batched_blocks_cut_into_units(lp):
     for fmt in ("f32", "bf16"):
         _, _, _, _, errs = _run(lp, mats, fmt, 0.0)
         assert max(errs) <= TOL[fmt], errs
+
+
+@pytest.mark.parametrize("fmt", ["f32", "bf16"])
+@pytest.mark.parametrize("tau", [math.inf, 2.0])
+def test_batched_n_not_a_power_of_two(lp, fmt, tau):
+    # N values whose 16-byte vectors per row are not a power of two: lane groups are rounded
+    # up and the lanes past N idle
+    mats = W.batched_mix(count=16, seed=11, min_rows=200, max_rows=2500, Ns=(8, 24, 40, 48, 56, 96, 104, 120))
+    plan, _, _, _, errs = _run(lp, mats, fmt, tau, seed=3)
+    assert max(errs) <= TOL[fmt], errs
