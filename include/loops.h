@@ -222,14 +222,15 @@ int64_t loops_test_fail_alloc(int64_t n);
 int64_t loops_test_wait_limit(int64_t polls);
 
 /* The performance model of Sec. 3.5 restated for the GPU (host only, no device access).
- * Eq. 2: perf(x, y) = a0 + a1 x + a2 y + a3 x^2 + a4 y^2, where x is the CSR-part work
- * (stored entries of the CSR part x N) and y the BCSR-part work (tiles x B_r x N, padding
- * included) of a split, and perf its throughput. loops_perf_model_fit computes the five
- * coefficients coef[0..4] by least squares over n samples (x[i], y[i], perf[i]); samples on a
- * line (one matrix, whose x and y move together) still give a solution (a tiny ridge).
- * LOOPS_ERR_STATE if the system has no finite solution. loops_perf_model_argmax is Eq. 3:
- * the index of the candidate (x[i], y[i]) of highest predicted perf, and that prediction.
- * Plans use them with tau = LOOPS_TAU_MODEL (loops_plan) and in the batched autotuner. */
+ * Eq. 2: f(x, y) = a0 + a1 x + a2 y + a3 x^2 + a4 y^2, where x is the CSR-part work (stored
+ * entries of the CSR part x N) and y the BCSR-part work (tiles x B_r x N, padding included)
+ * of a split. loops_perf_model_fit computes the five coefficients coef[0..4] by least squares
+ * over n samples (x[i], y[i], f[i]); samples on a line (one matrix, whose x and y move
+ * together) still give a solution (a tiny ridge). LOOPS_ERR_STATE if the system has no finite
+ * solution. loops_perf_model_argmax is Eq. 3: the index of the candidate (x[i], y[i]) of
+ * highest predicted f, and that prediction. The library's plans fit f to the measured time
+ * and take the highest predicted throughput (flops / predicted time): with tau =
+ * LOOPS_TAU_MODEL (loops_plan) and in the batched autotuner. */
 loops_status loops_perf_model_fit(const double* x, const double* y, const double* perf, int32_t n, double* coef);
 loops_status loops_perf_model_argmax(const double* coef, const double* x, const double* y, int32_t n,
                                      int32_t* best, double* best_perf);

@@ -42,7 +42,7 @@
 #define LOOPS_BATCHED_HMMA_STAGES 3
 #endif
 #ifndef LOOPS_BATCHED_FFMA_MIN_BLOCKS
-#define LOOPS_BATCHED_FFMA_MIN_BLOCKS 2
+#define LOOPS_BATCHED_FFMA_MIN_BLOCKS 3
 #endif
 
 namespace loops {

@@ -85,10 +85,13 @@ int next_pow2(int64_t x) {
 }
 
 // Class of a matrix's CSR items: G lanes per item with VPL 16-byte column vectors each (two
-// vectors per lane once a row has at least 16 of them, as in the single-plan kernel).
+// vectors per lane once a row has at least LOOPS_BATCHED_CSR_VPL2 of them).
+#ifndef LOOPS_BATCHED_CSR_VPL2
+#define LOOPS_BATCHED_CSR_VPL2 16
+#endif
 void csr_shape(loops_dtype dtype, int64_t N, int32_t* G, int32_t* vpl) {
   const int64_t nvec = N / elems_per_16b(dtype);
-  *vpl = nvec >= 16 ? 2 : 1;
+  *vpl = nvec >= LOOPS_BATCHED_CSR_VPL2 ? 2 : 1;
   *G = next_pow2(*vpl == 2 ? (nvec + 1) / 2 : nvec);
 }
 
@@ -359,9 +362,9 @@ loops_status time_batch(BatchState* b, const std::vector<const void*>& Bs, const
 // Autotuner of a batch. Candidates with one split threshold for every matrix (and, for F32,
 // the other tile height) are built and timed as whole batches. With host-resident matrices
 // the performance model then proposes one more candidate with a threshold and tile height
-// per matrix: Eq. 2 is fitted to the timed candidates' throughput as a function of their
-// total CSR-part and BCSR-part work, and Eq. 3 is applied per matrix (coordinate ascent on
-// the predicted throughput of the whole batch, over each matrix's candidate splits). That
+// per matrix: Eq. 2 is fitted to the timed candidates' times as a function of their total
+// CSR-part and BCSR-part work, and Eq. 3 is applied per matrix (coordinate descent of the
+// predicted batch time, over each matrix's candidate splits). That
 // candidate reuses the sub-plans built for the timed ones and is timed the same way; the
 // fastest candidate is kept.
 loops_status autotune_batch(const loops_csr* As, const int64_t* Ns, int32_t count, loops_dtype dtype,
@@ -430,17 +433,22 @@ loops_status autotune_batch(const loops_csr* As, const int64_t* Ns, int32_t coun
           if (cands[c].br == h) w[(size_t)m][c] = split_work(prof, cands[c].tau, kpad, Ns[m]);
       }
     }
-    std::vector<double> X(cands.size(), 0.0), Y(cands.size(), 0.0), P(cands.size());
+    std::vector<double> X(cands.size(), 0.0), Y(cands.size(), 0.0), T(cands.size());
+    double tmin = INFINITY;
     for (size_t c = 0; c < cands.size(); ++c) {
       for (int32_t m = 0; m < count; ++m) {
         X[c] += w[(size_t)m][c].x;
         Y[c] += w[(size_t)m][c].y;
       }
-      P[c] = flops / (std::max((double)cands[c].ms, 1e-6) * 1e-3) / 1e9;
+      T[c] = (double)cands[c].ms;
+      tmin = std::min(tmin, T[c]);
     }
     double a[5];
-    if (fit_perf_model(X.data(), Y.data(), P.data(), (int)cands.size(), a)) {
-      // Eq. 3 per matrix: coordinate ascent from the best timed candidate
+    if (fit_perf_model(X.data(), Y.data(), T.data(), (int)cands.size(), a)) {
+      // Eq. 3 per matrix: coordinate descent of the predicted batch time (the highest
+      // predicted throughput) from the best timed candidate, over each matrix's candidate
+      // splits; predictions below half the fastest measured time are extrapolations and
+      // are not followed
       std::vector<size_t> pick((size_t)count, best_c);
       double x = X[best_c], y = Y[best_c];
       double cur = eval_perf_model(a, x, y);
@@ -451,9 +459,9 @@ loops_status autotune_batch(const loops_csr* As, const int64_t* Ns, int32_t coun
           for (size_t c = 0; c < cands.size(); ++c) {
             const SplitWork& alt = w[(size_t)m][c];
             const double nx = x - now.x + alt.x, ny = y - now.y + alt.y;
-            const double pr = eval_perf_model(a, nx, ny);
-            if (pr > cur * (1.0 + 1e-9)) {
-              cur = pr;
+            const double t = eval_perf_model(a, nx, ny);
+            if (t < cur * (1.0 - 1e-9) && t > 0.5 * tmin) {
+              cur = t;
               x = nx;
               y = ny;
               pick[(size_t)m] = c;
@@ -466,7 +474,7 @@ loops_status autotune_batch(const loops_csr* As, const int64_t* Ns, int32_t coun
       }
       bool uniform = true;
       for (int32_t m = 1; m < count; ++m) uniform = uniform && pick[(size_t)m] == pick[0];
-      model_pred = cur;
+      model_pred = flops / (std::max(cur, 1e-6) * 1e-3) / 1e9;
       if (!uniform) {
         std::vector<int32_t> brs((size_t)count);
         std::vector<double> taus((size_t)count);

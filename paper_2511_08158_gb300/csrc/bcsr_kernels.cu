@@ -105,25 +105,28 @@ __global__ void __launch_bounds__(WARPS * 32) bcsr_hmma(BcsrKArgs a) {
   }
   __syncthreads();
 
-  // stage g: B rows of tiles g*16 .. g*16+15 into sB[g % kStages]
+  // stage g: B rows of tiles g*16 .. g*16+15 into sB[g % kStages]. With bulk copies, lane k
+  // of warp 0 (k < 16) fetches row k: a padding tile's row (column -1) is zero-filled by its
+  // lane first, then lane 0 announces the stage's total bytes on its barrier (its arrival
+  // releases the zero rows to the waiting threads), then the lanes issue their copies at once.
   auto issue = [&](int g) {
     const int s = g % kStages;
     if (BULK) {
-      if (tid == 0) {
-        fence_proxy_async_smem();
-        uint32_t bytes = 0;
+      if (warp == 0) {
         const uint32_t row_bytes = (uint32_t)width * sizeof(T);
-        for (int k = 0; k < 16; ++k) {
-          const int32_t c = cols[g * 16 + k];
-          if (c >= 0) {
-            bulk_g2s(&sB[s][k][0], Bp + (int64_t)c * a.ldb + n0, row_bytes, &bar[s]);
-            bytes += row_bytes;
-          } else {
-            uint4* z = reinterpret_cast<uint4*>(&sB[s][k][0]);
-            for (int q = 0; q < CT * (int)sizeof(T) / 16; ++q) z[q] = make_uint4(0, 0, 0, 0);
-          }
+        const int32_t c = lane < 16 ? cols[g * 16 + lane] : -1;
+        if (lane < 16 && c < 0) {
+          uint4* z = reinterpret_cast<uint4*>(&sB[s][lane][0]);
+          for (int q = 0; q < CT * (int)sizeof(T) / 16; ++q) z[q] = make_uint4(0, 0, 0, 0);
         }
-        mbar_arrive_expect_tx(&bar[s], bytes);
+        const uint32_t bytes = __reduce_add_sync(0xffffffffu, (lane < 16 && c >= 0) ? row_bytes : 0u);
+        __syncwarp();
+        if (lane == 0) mbar_arrive_expect_tx(&bar[s], bytes);
+        __syncwarp();
+        if (lane < 16 && c >= 0) {
+          fence_proxy_async_smem();
+          bulk_g2s(&sB[s][lane][0], Bp + (int64_t)c * a.ldb + n0, row_bytes, &bar[s]);
+        }
       }
     } else {
       for (int i = tid; i < 16 * CT; i += WARPS * 32) {

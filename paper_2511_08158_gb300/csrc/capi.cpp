@@ -500,8 +500,9 @@ loops_status autotune_tau(const PlanBuilder& build, int64_t n_rows, int64_t n_co
 // Split threshold from the performance model (Eq. 2 and Eq. 3, restated in perf_model.cpp):
 // the warm-up candidates (the timed autotuner's thresholds, each distinct split once) are
 // built and timed (L2 flushed before each timed call), Eq. 2 is fitted to their (CSR work,
-// BCSR work, GFLOP/s), and Eq. 3 picks the threshold of highest predicted throughput among
-// +inf, 0 and the matrix's distinct block densities -- including thresholds never timed.
+// BCSR work, time), and Eq. 3 picks the threshold of highest predicted throughput (flops over
+// predicted time) among +inf, 0 and the matrix's distinct block densities -- including
+// thresholds never timed.
 loops_status model_tau(const PlanBuilder& build, const BlockProfile& prof, int64_t n_rows, int64_t n_cols,
                        int64_t nnz, int64_t N, loops_dtype dtype, int32_t split_len, cudaStream_t s,
                        double* tau_out, double* pred_out, double coef[5]) {
@@ -554,7 +555,7 @@ loops_status model_tau(const PlanBuilder& build, const BlockProfile& prof, int64
     xs.push_back(w.x);
     ys.push_back(w.y);
     taus.push_back(tau);
-    ps.push_back(flops / (std::max((double)best_ms, 1e-6) * 1e-3) / 1e9);
+    ps.push_back((double)best_ms);
   }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
@@ -562,23 +563,27 @@ loops_status model_tau(const PlanBuilder& build, const BlockProfile& prof, int64
   if (dC) cudaFree(dC);
   if (st) return st;
   if (!fit_perf_model(xs.data(), ys.data(), ps.data(), (int)xs.size(), coef)) {
-    // degenerate samples: the best measured threshold
+    // degenerate samples: the fastest measured threshold
     size_t b = 0;
     for (size_t i = 1; i < ps.size(); ++i)
-      if (ps[i] > ps[b]) b = i;
+      if (ps[i] < ps[b]) b = i;
     if (!taus.empty()) *tau_out = taus[b];
     return LOOPS_OK;
   }
-  double best = -INFINITY;
+  // Eq. 3: the highest predicted throughput, flops / predicted time (predictions of no more
+  // than a tenth of the fastest measured time are not trusted: the fit extrapolates there)
+  double tmin = INFINITY;
+  for (double t : ps) tmin = std::min(tmin, t);
+  double best = INFINITY;
   for (double tau : tau_grid(prof, 64)) {
     const SplitWork w = split_work(prof, tau, kpad, N);
-    const double pr = eval_perf_model(coef, w.x, w.y);
-    if (pr > best) {
-      best = pr;
+    const double t = eval_perf_model(coef, w.x, w.y);
+    if (t > 0.1 * tmin && t < best) {
+      best = t;
       *tau_out = tau;
     }
   }
-  *pred_out = best;
+  if (best < INFINITY) *pred_out = flops / (best * 1e-3) / 1e9;
   return LOOPS_OK;
 }
 

@@ -13,8 +13,11 @@
 //   y = BCSR-part work  = tiles of the BCSR part x B_r x N (padding tiles included).
 // A configuration is a split threshold (per matrix, in a batch). Its (x, y) follows from a
 // profile of the row blocks (stored entries and distinct columns of each block), so every
-// threshold can be predicted without building its plan. perf is the measured throughput
-// (GFLOP/s) of the warm-up runs.
+// threshold can be predicted without building its plan. The quadratic is fitted to the
+// measured time of the warm-up runs, and the performance score of Eq. 3 is the throughput
+// flops / predicted time: on the GPU both parts' work adds to one time, which grows about
+// linearly with the work, so a fit of the time extrapolates between and beyond the warm-up
+// splits far better than a fit of the throughput.
 #include <algorithm>
 #include <cmath>
 #include <thread>
