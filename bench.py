@@ -67,6 +67,10 @@ def parse(argv=None):
     ap.add_argument("--N", type=int, default=64, help="laplacian: columns of B")
     ap.add_argument("--batch-count", type=int, default=BATCH_COUNT,
                     help="batched: number of matrices (smaller counts give small profiling cases)")
+    ap.add_argument("--batch-kinds", default="all", choices=["all", "uniform", "banded", "blocks"],
+                    help="batched: keep only the matrices of one structure (index mod 3), for profiling cases")
+    ap.add_argument("--tau", type=float, default=-1.0,
+                    help="batched: split threshold of the timed plan (default -1: autotuned)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-sub", action="store_true", help="batched: skip the sub-line workloads")
     return ap.parse_args(argv)
@@ -265,11 +269,16 @@ def oracle_batch(mats, Bs, threads):
 
 
 # ------------------------------------------------------------------ the 512-matrix batch
-def batch_inputs(count: int, fmt: str):
+def batch_inputs(count: int, fmt: str, kinds: str = "all"):
     """The batch (A_m, N_m) and its dense operands B_m (host, float32 N(0, 1), seeded per
-    matrix); for BF16 the values the GPU multiplies are the BF16 roundings."""
+    matrix); for BF16 the values the GPU multiplies are the BF16 roundings. kinds: all, or only
+    the uniform / banded / blocks matrices (index mod 3 = 0 / 1 / 2)."""
     mats = W.batched_mix(count=count, seed=BATCH_SEED)
     Bs = [W.dense_normal(A.n_cols, N, 10_000 + m).astype(np.float32) for m, (A, N) in enumerate(mats)]
+    if kinds != "all":
+        k = {"uniform": 0, "banded": 1, "blocks": 2}[kinds]
+        keep = [m for m in range(len(mats)) if m % 3 == k]
+        mats, Bs = [mats[m] for m in keep], [Bs[m] for m in keep]
     return mats, Bs
 
 
@@ -288,7 +297,7 @@ def run_batched(args, torch, lp, flush, rank, world, hbm_peak, hbm_src):
     e = 4 if fmt == "f32" else 2
     dt = torch.float32 if fmt == "f32" else torch.bfloat16
     t0 = time.perf_counter()
-    mats, Bh = batch_inputs(args.batch_count, fmt)
+    mats, Bh = batch_inputs(args.batch_count, fmt, args.batch_kinds)
     gen_s = time.perf_counter() - t0
     As = [A for A, _ in mats]
     Ns = [N for _, N in mats]
@@ -299,7 +308,7 @@ def run_batched(args, torch, lp, flush, rank, world, hbm_peak, hbm_src):
     Cd = [torch.empty((A.n_rows, N), device="cuda") for A, N in mats]
 
     t0 = time.perf_counter()
-    plan = lp.BatchedPlan(As, Ns, fmt, tau=-1.0)
+    plan = lp.BatchedPlan(As, Ns, fmt, tau=args.tau)
     plan_s = time.perf_counter() - t0
     st = plan.stats()
 
@@ -383,6 +392,7 @@ def run_batched(args, torch, lp, flush, rank, world, hbm_peak, hbm_src):
             "vs_baseline": None, "dtype": fmt,
             "data": "synthetic (seeded: matrices of the batch recipe, B ~ N(0,1) per matrix)",
             "config": dict(batch_config(args.batch_count, fmt, nnz), parallelism=f"replicas{world}",
+                           kinds=args.batch_kinds,
                            tau_autotuned=st["tau"], block_rows=st["block_rows"], plan_build_s=plan_s,
                            input_generation_s=gen_s),
             "roofline": {"bound": "hbm", "kernel": "batched persistent kernel(s) (one graph replay)",
@@ -502,7 +512,10 @@ def run_single(name, args, torch, lp, flush, hbm_peak, hbm_src, steps, warmup, f
     out = {"workload": desc, "dtype": fmt, "nnz": int(A.nnz), "N": N, "value": flops / (ms * 1e-3) / 1e9,
            "unit": "GFLOP/s", "ms_per_step": ms, "steps": steps, "roofline": roof,
            "hbm": {"alg_bytes_per_step": alg, "frac_of_measured": alg / (ms * 1e-3) / 1e9 / hbm_peak},
-           "tau_autotuned": inf["tau"], "tile_min": inf["tile_min"], "part_ms": {"csr": csr_ms, "bcsr": bcsr_ms},
+           "tau_autotuned": inf["tau"], "tile_min": inf["tile_min"],
+           "shapes_autotuned": {"block_rows": inf["block_rows"], "csr_lane_vectors": inf["csr_lane_vectors"],
+                                "bcsr_col_tile": inf["bcsr_col_tile"]},
+           "part_ms": {"csr": csr_ms, "bcsr": bcsr_ms},
            "rel_l2_vs_oracle": rel_l2(C, ref), "rel_l2_tol": TOL[fmt],
            "gpu_launches_per_step": launches_per_step(inf)}
     if fmt in ("f16", "bf16"):
@@ -515,6 +528,14 @@ def run_single(name, args, torch, lp, flush, hbm_peak, hbm_src, steps, warmup, f
             var[vname] = {"gflops": flops / (statistics.mean(s_v) * 1e-3) / 1e9, "ms_per_step": statistics.mean(s_v),
                           "bcsr_row_blocks": vp.info()["n_row_blocks"]}
             vp.destroy()
+        # the performance model (Eq. 2 fitted to warm-up times, Eq. 3) beside the timed autotuner
+        mp = lp.Plan(A, N, fmt, tau=lp.TAU_MODEL)
+        mi = mp.info()
+        s_m, _, _ = time_steps(torch, lambda: mp.spmm(Bd, Cd, col_scale=sc), max(5, steps // 2), 2, flush)
+        var["model"] = {"tau": mi["tau"], "predicted_gflops": mi["model_gflops"],
+                        "gflops": flops / (statistics.mean(s_m) * 1e-3) / 1e9, "ms_per_step": statistics.mean(s_m),
+                        "bcsr_row_blocks": mi["n_row_blocks"], "coef": mi["model_coef"]}
+        mp.destroy()
         out["variants"] = var
     if name == "gcn":
         dYd = torch.as_tensor(dY, dtype=torch.float32).cuda()
@@ -547,7 +568,7 @@ def run_reference(args):
     oracle.build()
     threads = host_cores()
     if args.workload == "batched":
-        mats, Bh = batch_inputs(args.batch_count, args.dtype or "f32")
+        mats, Bh = batch_inputs(args.batch_count, args.dtype or "f32", args.batch_kinds)
         idx = list(range(0, len(mats), 8))
         sub = [mats[i][0] for i in idx]
         Bs = [Bh[i].astype(np.float64) for i in idx]
@@ -611,10 +632,10 @@ def run_loops(args):
             subs = {}
             k = max(5, min(args.steps, 10))
             for name, fmt in (("laplacian", None), ("rmat", "f16"), ("rmat", "bf16"), ("gcn", None),
-                              ("uniform", None)):
+                              ("uniform", None), ("mixed", "bf16")):
                 key = name if fmt is None else f"{name}_{fmt}"
                 subs[key] = run_single(name, args, torch, lp, flush, hbm_peak, hbm_src, k, 3, fmt=fmt,
-                                       full=(name == "laplacian"))
+                                       full=(name in ("laplacian", "mixed")))
                 torch.cuda.empty_cache()
             line["workloads"] = subs
     else:

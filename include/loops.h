@@ -74,10 +74,13 @@ typedef struct {
  *      (nnz per B_r x 1 tile, the paper's block density, Sec. 4.2/4.5). A block with
  *      nnz_rb >= tau * distinct_cols goes to the BCSR part. LOOPS_TAU_MODEL (-2): the
  *      performance model picks tau (see LOOPS_TAU_MODEL). Other tau < 0: autotune (time
- *      candidate thresholds on the plan's stream); +inf: CSR only (the pure vector-unit
- *      configuration of Sec. 4.3); 0: every non-empty block BCSR (pure matrix unit).
- * block_rows: B_r (tile height); 0 = default (8 for F64, 16 otherwise); F64 needs 8,
- *      F16/BF16 need 16, F32 accepts 8 or 16.
+ *      candidate thresholds on the plan's stream, the L2 flushed before each timed call;
+ *      for F32 with block_rows 0 also B_r 8 and 16; then, on the chosen split, the CSR
+ *      kernel's vectors per lane and the F16/BF16 BCSR kernel's columns per CTA -- reported
+ *      by loops_plan_info); +inf: CSR only (the pure vector-unit configuration of Sec. 4.3);
+ *      0: every non-empty block BCSR (pure matrix unit).
+ * block_rows: B_r (tile height); 0 = default (8 for F64, 16 otherwise; F32 autotuning tries
+ *      both); F64 needs 8, F16/BF16 need 16, F32 accepts 8 or 16.
  * contiguous_split: paper mode (Eq. 1, Algorithm 1): rows [0, r_boundary) rounded up to a
  *      multiple of B_r form the CSR part and every later row block is BCSR; tau ignored.
  *      r_boundary < 0 derives it from Eq. 1: the all-CSR and all-BCSR plans are timed on the
@@ -127,6 +130,10 @@ typedef struct {
   int64_t tile_min;        /* tile-level split threshold in effect (0: off) */
   int32_t tau_source;      /* 0 given, 1 timed autotuner, 2 performance model (Eq. 2/3),
                               3 contiguous split (paper mode) */
+  int32_t csr_lane_vectors;/* CSR kernel: 16-byte column vectors per lane the autotuner chose
+                              (1 or 2); 0: the built-in rule */
+  int32_t bcsr_col_tile;   /* F16/BF16 BCSR kernel: columns per CTA the autotuner chose (32, 64,
+                              128); 0: the smallest tile covering N */
   int32_t reserved0;
   double model_gflops;     /* tau_source 2: the Eq. 2 prediction for the chosen split; else NaN */
   double model_coef[5];    /* tau_source 2: the fitted a0..a4 of Eq. 2 */

@@ -67,6 +67,7 @@ class _Info(ctypes.Structure):
                 ("n_split_rows", ctypes.c_int64), ("n_segments", ctypes.c_int64),
                 ("n_subnormal_vals", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
                 ("r_boundary", ctypes.c_int64), ("tile_min", ctypes.c_int64), ("tau_source", ctypes.c_int32),
+                ("csr_lane_vectors", ctypes.c_int32), ("bcsr_col_tile", ctypes.c_int32),
                 ("reserved0", ctypes.c_int32), ("model_gflops", ctypes.c_double),
                 ("model_coef", ctypes.c_double * 5)]
 

@@ -241,13 +241,16 @@ cudaError_t launch_hmma_cfg(const BcsrKArgs& a, bool bulk, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Column tile of a CTA: the plan's bcsr_ntile when the autotuner set it (32, 64 or 128), else
+// the smallest of 8 .. 128 that covers N.
 template <class T>
-cudaError_t launch_hmma(const BcsrKArgs& a, cudaStream_t s) {
+cudaError_t launch_hmma(const BcsrKArgs& a, int ntile, cudaStream_t s) {
   const bool bulk = (a.N % 8 == 0) && ((uintptr_t)a.B % 16 == 0) && ((a.ldb * 2) % 16 == 0);
-  if (a.N <= 8) return launch_hmma_cfg<T, 1, 1>(a, bulk, s);
-  if (a.N <= 16) return launch_hmma_cfg<T, 1, 2>(a, bulk, s);
-  if (a.N <= 32) return launch_hmma_cfg<T, 2, 2>(a, bulk, s);
-  if (a.N <= 64) return launch_hmma_cfg<T, 4, 2>(a, bulk, s);
+  const int64_t ct = ntile > 0 ? ntile : (a.N <= 8 ? 8 : a.N <= 16 ? 16 : a.N <= 32 ? 32 : a.N <= 64 ? 64 : 128);
+  if (ct <= 8) return launch_hmma_cfg<T, 1, 1>(a, bulk, s);
+  if (ct <= 16) return launch_hmma_cfg<T, 1, 2>(a, bulk, s);
+  if (ct <= 32) return launch_hmma_cfg<T, 2, 2>(a, bulk, s);
+  if (ct <= 64) return launch_hmma_cfg<T, 4, 2>(a, bulk, s);
   return launch_hmma_cfg<T, 4, 4>(a, bulk, s);
 }
 
@@ -526,8 +529,8 @@ cudaError_t launch_bcsr(const loops_plan_s* p, const BcsrDev& d, const DenseArgs
   switch (p->dtype) {
     case LOOPS_F64: e = launch_dmma(a, s); break;
     case LOOPS_F32: e = p->br == 8 ? launch_ffma_br<8>(a, s) : launch_ffma_br<16>(a, s); break;
-    case LOOPS_F16: e = launch_hmma<__half>(a, s); break;
-    case LOOPS_BF16: e = launch_hmma<__nv_bfloat16>(a, s); break;
+    case LOOPS_F16: e = launch_hmma<__half>(a, p->bcsr_ntile, s); break;
+    case LOOPS_BF16: e = launch_hmma<__nv_bfloat16>(a, p->bcsr_ntile, s); break;
   }
   if (e != cudaSuccess || d.n_split == 0) return e;
   dim3 grid((unsigned)d.n_split, (unsigned)std::min<int64_t>((p->br * a.N + 255) / 256, 64));

@@ -23,9 +23,13 @@ void clear_error() { g_last_error.clear(); }
 loops_status export_part(const loops_plan_s* p, loops_partition* out);
 // Builds a candidate plan for the given options and threshold (host or device builder).
 using PlanBuilder = std::function<loops_status(const loops_plan_opts& o, double tau, loops_plan_s** out)>;
+struct TunedShape {
+  double tau;
+  int32_t tile_min, br, csr_vpl, bcsr_ntile;
+};
 loops_status autotune_tau(const PlanBuilder& build, int64_t n_rows, int64_t n_cols, int64_t nnz, int64_t N,
-                          loops_dtype dtype, int32_t split_len, bool try_tile_split, cudaStream_t s,
-                          double* tau_out, int32_t* tile_min_out);
+                          loops_dtype dtype, int32_t split_len, bool try_tile_split, int32_t br, bool try_br,
+                          cudaStream_t s, TunedShape* out);
 
 loops_status cuda_status(cudaError_t e, const char* what) {
   if (e == cudaSuccess) return LOOPS_OK;
@@ -436,19 +440,22 @@ cudaError_t L2Flush::run(cudaStream_t s) {
   return buf ? cudaMemsetAsync(buf, ++n & 0xff, kL2FlushBytes, s) : cudaSuccess;
 }
 
-// Autotuner (replaces the paper's Eq. 2/Eq. 3 CPU model): times C = A.B for candidate split
-// thresholds on synthetic B and keeps the fastest. Candidates that give the same row-block
-// split as an earlier one are skipped.
+// Autotuner: times C = A.B for candidate split thresholds (and, for F32, either tile height)
+// on synthetic B with the L2 flushed before each timed call, keeps the fastest, then times the
+// shapes of its kernels on that plan: the CSR kernel's 16-byte column vectors per lane (1 or
+// 2) and, for F16/BF16, the BCSR kernel's columns per CTA (32, 64 or 128). Candidates that give
+// the same row-block split as an earlier one are skipped.
 loops_status autotune_tau(const PlanBuilder& build, int64_t n_rows, int64_t n_cols, int64_t nnz, int64_t N,
-                          loops_dtype dtype, int32_t split_len, bool try_tile_split, cudaStream_t s,
-                          double* tau_out, int32_t* tile_min_out) {
-  struct Cand { double tau; int32_t tile_min; };
+                          loops_dtype dtype, int32_t split_len, bool try_tile_split, int32_t br, bool try_br,
+                          cudaStream_t s, TunedShape* out) {
+  struct Cand { double tau; int32_t tile_min; int32_t br; };
   std::vector<Cand> cands;
-  for (double t : {(double)INFINITY, 8.0, 4.0, 3.0, 2.0, 1.5, 1.25, 0.0}) cands.push_back({t, 0});
+  for (double t : {(double)INFINITY, 8.0, 4.0, 3.0, 2.0, 1.5, 1.25, 0.0}) cands.push_back({t, 0, br});
   if (try_tile_split)  // tile-level split: dense tiles (>= 2 entries) on the BCSR kernel only
-    for (double t : {4.0, 2.0, 1.25}) cands.push_back({t, 2});
-  *tau_out = 2.0;
-  *tile_min_out = 0;
+    for (double t : {4.0, 2.0, 1.25}) cands.push_back({t, 2, br});
+  if (try_br && dtype == LOOPS_F32)
+    for (double t : {4.0, 2.0, 1.25}) cands.push_back({t, 0, br == 16 ? 8 : 16});
+  *out = TunedShape{2.0, 0, br, 0, 0};
   if (nnz == 0 || N == 0 || n_rows == 0) return LOOPS_OK;
   const int64_t eb = dense_elem_bytes(dtype), ec = out_elem_bytes(dtype);
   void *dB = nullptr, *dC = nullptr;
@@ -460,23 +467,11 @@ loops_status autotune_tau(const PlanBuilder& build, int64_t n_rows, int64_t n_co
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   loops_status st = cuda_status(e, "autotune setup");
   L2Flush flush;
-  double best = INFINITY;
-  std::vector<std::pair<int64_t, int64_t>> seen;
-  loops_plan_opts o;
-  loops_plan_opts_default(&o);
-  o.split_len = split_len;
-  for (const Cand& cand : cands) {
-    if (st) break;
-    const double tau = cand.tau;
-    o.tile_min = cand.tile_min;
-    loops_plan_s* p = nullptr;
-    if ((st = build(o, tau, &p))) break;
-    const std::pair<int64_t, int64_t> key(p->n_rb, p->n_tiles);
-    if (std::find(seen.begin(), seen.end(), key) != seen.end()) { destroy_plan(p); continue; }
-    seen.push_back(key);
+  // best of 5 timed calls (after 2 warm-up calls), the L2 flushed before each
+  auto time_plan = [&](loops_plan_s* p, float* ms_out) {
     float best_ms = INFINITY;
     for (int it = 0; it < 7 && !st; ++it) {
-      if ((st = run_spmm(p, dB, N, nullptr, dC, N, s))) break;  // it 0, 1: warm-up
+      if ((st = run_spmm(p, dB, N, nullptr, dC, N, s))) break;
       if (it < 2) continue;
       if ((st = cuda_status(flush.run(s), "L2 flush"))) break;
       cudaEventRecord(e0, s);
@@ -487,9 +482,59 @@ loops_status autotune_tau(const PlanBuilder& build, int64_t n_rows, int64_t n_co
       cudaEventElapsedTime(&ms, e0, e1);
       best_ms = std::min(best_ms, ms);
     }
-    destroy_plan(p);
-    if (!st && best_ms < best) { best = best_ms; *tau_out = tau; *tile_min_out = cand.tile_min; }
+    *ms_out = best_ms;
+  };
+  float best = INFINITY;
+  loops_plan_s* best_p = nullptr;
+  std::vector<std::tuple<int64_t, int64_t, int32_t>> seen;
+  loops_plan_opts o;
+  loops_plan_opts_default(&o);
+  o.split_len = split_len;
+  for (const Cand& cand : cands) {
+    if (st) break;
+    o.tile_min = cand.tile_min;
+    o.block_rows = cand.br;
+    loops_plan_s* p = nullptr;
+    if ((st = build(o, cand.tau, &p))) break;
+    const auto key = std::make_tuple(p->n_rb, p->n_tiles, cand.br);
+    if (std::find(seen.begin(), seen.end(), key) != seen.end()) { destroy_plan(p); continue; }
+    seen.push_back(key);
+    float ms = INFINITY;
+    time_plan(p, &ms);
+    if (!st && ms < best) {
+      best = ms;
+      out->tau = cand.tau;
+      out->tile_min = cand.tile_min;
+      out->br = cand.br;
+      if (best_p) destroy_plan(best_p);
+      best_p = p;
+    } else {
+      destroy_plan(p);
+    }
   }
+  // kernel shapes on the chosen split
+  if (!st && best_p) {
+    const int64_t nvec = dtype == LOOPS_F64 ? 0 : N / (16 / dense_elem_bytes(dtype));
+    if (best_p->dev.csr.n_items > 0 && nvec >= 2 && N % (16 / dense_elem_bytes(dtype)) == 0) {
+      for (int v : {1, 2}) {
+        best_p->csr_vpl = v;
+        float ms = INFINITY;
+        time_plan(best_p, &ms);
+        if (!st && ms < best) { best = ms; out->csr_vpl = v; }
+      }
+      best_p->csr_vpl = out->csr_vpl;
+    }
+    if ((dtype == LOOPS_F16 || dtype == LOOPS_BF16) && best_p->dev.bcsr.n_rb > 0 && N > 32) {
+      for (int t : {32, 64, 128}) {
+        if (t > 2 * N) break;
+        best_p->bcsr_ntile = t;
+        float ms = INFINITY;
+        time_plan(best_p, &ms);
+        if (!st && ms < best) { best = ms; out->bcsr_ntile = t; }
+      }
+    }
+  }
+  if (best_p) destroy_plan(best_p);
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   if (dB) cudaFree(dB);
@@ -729,6 +774,7 @@ loops_status loops_plan(const loops_csr* A, int64_t N, loops_dtype dtype, const 
   std::vector<double> vals;
   read_vals_f64(A, vals);
   double tau = o.tau;
+  TunedShape shape{tau, o.tile_min, br, 0, 0};
   int32_t tau_source = o.contiguous_split ? 3 : 0;
   double model_pred = NAN, coef[5] = {0, 0, 0, 0, 0};
   if (tau == LOOPS_TAU_MODEL && !o.contiguous_split) {
@@ -744,14 +790,15 @@ loops_status loops_plan(const loops_csr* A, int64_t N, loops_dtype dtype, const 
     tau_source = 2;
   } else if (tau < 0.0 && !o.contiguous_split) {
     tau_source = 1;
-    int32_t tmin = o.tile_min;
     const PlanBuilder host_build = [&](const loops_plan_opts& oc, double t, loops_plan_s** q) {
-      return make_plan(A, vals.data(), N, dtype, oc, br, t, false, q);
+      return make_plan(A, vals.data(), N, dtype, oc, oc.block_rows > 0 ? oc.block_rows : br, t, false, q);
     };
     if ((st = autotune_tau(host_build, A->n_rows, A->n_cols, A->nnz, N, dtype, o.split_len,
-                           tmin < 0 && !o.want_backward, (cudaStream_t)stream, &tau, &tmin)))
+                           o.tile_min < 0 && !o.want_backward, br, o.block_rows == 0, (cudaStream_t)stream, &shape)))
       return st;
-    o.tile_min = tmin;
+    tau = shape.tau;
+    o.tile_min = shape.tile_min;
+    br = o.block_rows = shape.br;
   }
   if (o.contiguous_split && o.r_boundary < 0) {
     const PlanBuilder host_build = [&](const loops_plan_opts& oc, double t, loops_plan_s** q) {
@@ -764,6 +811,8 @@ loops_status loops_plan(const loops_csr* A, int64_t N, loops_dtype dtype, const 
   loops_plan_s* p = nullptr;
   if ((st = make_plan(A, vals.data(), N, dtype, o, br, tau, false, &p))) return st;
   p->tau_source = tau_source;
+  p->csr_vpl = shape.csr_vpl;
+  p->bcsr_ntile = shape.bcsr_ntile;
   p->model_gflops = model_pred;
   for (int i = 0; i < 5; ++i) p->model_coef[i] = coef[i];
   if (o.want_backward) {
@@ -828,19 +877,22 @@ loops_status loops_plan_device(const loops_csr* A, int64_t N, loops_dtype dtype,
   if ((st = validate_csr_device(d, dtype, s, &max_abs))) return st;
   const double scale = plan_scale_from_max(max_abs, dtype);
   const PlanBuilder dev_build = [&](const loops_plan_opts& oc, double t, loops_plan_s** q) {
-    return make_plan_device(d, nullptr, scale, N, dtype, oc, br, t, false, false, s, q);
+    return make_plan_device(d, nullptr, scale, N, dtype, oc, oc.block_rows > 0 ? oc.block_rows : br, t, false,
+                            false, s, q);
   };
   double tau = o.tau;
   if (tau == LOOPS_TAU_MODEL && !o.contiguous_split) {
     set_error("the performance model (LOOPS_TAU_MODEL) needs host CSR arrays: use loops_plan");
     return LOOPS_ERR_UNSUPPORTED;
   }
+  TunedShape shape{tau, o.tile_min, br, 0, 0};
   if (tau < 0.0 && !o.contiguous_split) {
-    int32_t tmin = o.tile_min;
     if ((st = autotune_tau(dev_build, A->n_rows, A->n_cols, A->nnz, N, dtype, o.split_len,
-                           tmin < 0 && !o.want_backward, s, &tau, &tmin)))
+                           o.tile_min < 0 && !o.want_backward, br, o.block_rows == 0, s, &shape)))
       return st;
-    o.tile_min = tmin;
+    tau = shape.tau;
+    o.tile_min = shape.tile_min;
+    br = o.block_rows = shape.br;
   }
   if (o.contiguous_split && o.r_boundary < 0) {
     if ((st = model_boundary(dev_build, A->n_rows, A->n_cols, A->nnz, N, dtype, o.split_len, s, &o.r_boundary)))
@@ -849,6 +901,8 @@ loops_status loops_plan_device(const loops_csr* A, int64_t N, loops_dtype dtype,
   loops_plan_s* p = nullptr;
   if ((st = make_plan_device(d, nullptr, scale, N, dtype, o, br, tau, true, false, s, &p))) return st;
   p->tau_source = o.contiguous_split ? 3 : (o.tau < 0.0 ? 1 : 0);
+  p->csr_vpl = shape.csr_vpl;
+  p->bcsr_ntile = shape.bcsr_ntile;
   if (o.want_backward) {
     int64_t* trp = nullptr;
     int32_t* tci = nullptr;
@@ -935,6 +989,8 @@ loops_status plan_info_of(const loops_plan_s* p, loops_plan_info* out) {
   out->r_boundary = p->opts.contiguous_split ? p->opts.r_boundary : -1;
   out->tile_min = p->tile_min;
   out->tau_source = p->tau_source;
+  out->csr_lane_vectors = p->csr_vpl;
+  out->bcsr_col_tile = p->bcsr_ntile;
   out->model_gflops = p->model_gflops;
   for (int i = 0; i < 5; ++i) out->model_coef[i] = p->model_coef[i];
   if (p->transposed)

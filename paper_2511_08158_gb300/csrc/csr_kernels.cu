@@ -342,9 +342,12 @@ cudaError_t launch_csr_t(const loops_plan_s* p, const CsrDev& d, const DenseArgs
       // lanes per item: the 16-byte vectors of a row, LOOPS_CSR_LANE_VECTORS per lane while
       // the group keeps at least 8 lanes (more vectors per lane: fewer shuffles per byte and
       // more loads in flight per lane; narrower groups lose more to the per-row overhead)
+      // (the plan's csr_vpl, when the autotuner set it, overrides this heuristic)
       constexpr int LV = LOOPS_CSR_LANE_VECTORS;
-      const bool lv = !std::is_same<Tr, TrF64>::value && LV > 1 && nvec >= 8 * LV;
-      const int64_t nv = lv ? (nvec + LV - 1) / LV : nvec;
+      const bool lv = p->csr_vpl == 2 ? nvec >= 2
+                    : p->csr_vpl == 1 ? false
+                    : (!std::is_same<Tr, TrF64>::value && LV > 1 && nvec >= 8 * LV);
+      const int64_t nv = lv ? (nvec + 1) / 2 : nvec;
       const int G = next_pow2(nv);
       const bool two = lv || nvec > 32;
       switch (G) {

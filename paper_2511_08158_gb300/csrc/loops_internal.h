@@ -328,6 +328,8 @@ struct loops_plan_s {
   // partition counts (canonical): CSR-part rows and entries, BCSR blocks and tiles
   int64_t n_csr_rows, nnz_csr, n_rb, n_tiles;
   bool device_built;                   // built by loops_plan_device (no host canonical copy)
+  int32_t csr_vpl = 0;                 // CSR kernel: 16-byte vectors per lane (0: heuristic, 1, 2)
+  int32_t bcsr_ntile = 0;              // F16/BF16 BCSR kernel: columns per CTA (0: smallest covering N)
   int32_t tau_source = 0;              // 0 given, 1 timed autotuner, 2 Eq. 2/3 model, 3 Eq. 1 / contiguous
   double model_gflops = NAN;           // Eq. 2 prediction for the chosen split (model mode)
   double model_coef[5] = {0, 0, 0, 0, 0};

@@ -16,20 +16,27 @@ import bench  # noqa: E402
 
 
 def test_traffic_reported_only_for_the_captured_source(tmp_path, monkeypatch):
-    # the committed figure matches the committed kernel source
-    assert isinstance(bench.traffic_for("csr_spmm_f64_n64"), int)
+    # the committed figures match the committed kernel sources
+    d_all = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    for key in d_all:
+        assert isinstance(bench.traffic_for(key), int), key
     assert bench.traffic_for("no_such_kernel") is None
-    # a copy of the tree whose kernel source differs by one byte: no traffic figure
-    d = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))["csr_spmm_f64_n64"]
+    # a copy of the tree in which one of the captured sources differs by one byte: no figure
+    d = d_all["batched_f32_batch512"]
     (tmp_path / "profiles").mkdir()
     shutil.copy(os.path.join(ROOT, "profiles", "traffic.json"), tmp_path / "profiles" / "traffic.json")
-    src = tmp_path / d["source"]
-    src.parent.mkdir(parents=True)
-    src.write_bytes(open(os.path.join(ROOT, d["source"]), "rb").read() + b"\n")
+    srcs = list(d["sources"])
+    for src in srcs:
+        dst = tmp_path / src
+        dst.parent.mkdir(parents=True, exist_ok=True)
+        dst.write_bytes(open(os.path.join(ROOT, src), "rb").read())
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    assert bench.traffic_for("csr_spmm_f64_n64") is None
-    src.write_bytes(open(os.path.join(ROOT, d["source"]), "rb").read())
-    assert bench.traffic_for("csr_spmm_f64_n64") == d["dram_bytes_per_launch"]
+    assert bench.traffic_for("batched_f32_batch512") == d["dram_bytes_per_launch"]
+    last = tmp_path / srcs[-1]
+    last.write_bytes(open(os.path.join(ROOT, srcs[-1]), "rb").read() + b"\n")
+    assert bench.traffic_for("batched_f32_batch512") is None
+    last.write_bytes(open(os.path.join(ROOT, srcs[-1]), "rb").read())
+    assert bench.traffic_for("batched_f32_batch512") == d["dram_bytes_per_launch"]
 
 
 def test_whole_job_throughput_and_slowest_rank():

@@ -89,6 +89,21 @@ def test_autotuner_gives_different_structures_different_shapes(lp):
     for fmt in ("f32", "bf16"):
         mix = lp.Plan(A_mix, 64, fmt, tau=-1.0).info()
         uni = lp.Plan(A_uni, 64, fmt, tau=-1.0).info()
-        print(f"{fmt}: block mix tau {mix['tau']} ({mix['n_row_blocks']} BCSR blocks), uniform tau {uni['tau']}")
+        print(f"{fmt}: block mix tau {mix['tau']} ({mix['n_row_blocks']} BCSR blocks, B_r {mix['block_rows']}, "
+              f"CSR vectors per lane {mix['csr_lane_vectors']}, BCSR tile {mix['bcsr_col_tile']}), uniform tau "
+              f"{uni['tau']} (CSR vectors per lane {uni['csr_lane_vectors']})")
         assert math.isfinite(mix["tau"]) and mix["n_row_blocks"] > 0
         assert uni["tau"] == math.inf and uni["n_row_blocks"] == 0
+        assert mix["block_rows"] in ((8, 16) if fmt == "f32" else (16,))
+        # 0: the built-in rule was kept (no timed alternative was faster)
+        assert uni["csr_lane_vectors"] in (0, 1, 2)
+        assert mix["bcsr_col_tile"] in ((0,) if fmt == "f32" else (0, 32, 64, 128))
+        # the tuned plan is correct
+        p = lp.Plan(A_mix, 64, fmt, tau=-1.0)
+        B = W.dense_normal(A_mix.n_cols, 64, 3)
+        A_r, Bq, s, B_eff = rounded_inputs(A_mix, B, fmt)
+        sc = None if s is None else torch.as_tensor(s, dtype=torch.float32).cuda()
+        C = p.spmm(to_device(torch, Bq, fmt), col_scale=sc)
+        rows = np.arange(0, A_mix.n_rows, 97)
+        ref = oracle.spmm_rows(A_r, B_eff, rows)
+        assert rel_l2(C[torch.as_tensor(rows).cuda()].double().cpu().numpy(), ref) <= TOL[fmt]
