@@ -491,22 +491,28 @@ ClassKernel csr_kernel(int G, int VPL) {
   }
 }
 
+template <int BR, int G>
+ClassKernel ffma_g(int*, int*) {
+  return batched_ffma<BR, G>;
+}
+
 template <int BR>
-ClassKernel ffma_kernel(int G) {
+ClassKernel ffma_kernel(int G, int* smem, int* threads) {
   switch (G) {
-    case 1: return batched_ffma<BR, 1>;
-    case 2: return batched_ffma<BR, 2>;
-    case 4: return batched_ffma<BR, 4>;
-    case 8: return batched_ffma<BR, 8>;
-    case 16: return batched_ffma<BR, 16>;
-    case 32: return batched_ffma<BR, 32>;
+    case 1: return ffma_g<BR, 1>(smem, threads);
+    case 2: return ffma_g<BR, 2>(smem, threads);
+    case 4: return ffma_g<BR, 4>(smem, threads);
+    case 8: return ffma_g<BR, 8>(smem, threads);
+    case 16: return ffma_g<BR, 16>(smem, threads);
+    case 32: return ffma_g<BR, 32>(smem, threads);
     default: return nullptr;
   }
 }
 
-// The kernel of a class, with its dynamic shared memory per block.
-ClassKernel class_kernel(loops_dtype dtype, const BatchClass& c, int* smem) {
+// The kernel of a class, with its dynamic shared memory and threads per block.
+ClassKernel class_kernel(loops_dtype dtype, const BatchClass& c, int* smem, int* threads) {
   *smem = 0;
+  *threads = 256;
   if (c.kind == 0) {
     switch (dtype) {
       case LOOPS_F32: return csr_kernel<TrF32>(c.G, c.vpl);
@@ -517,7 +523,7 @@ ClassKernel class_kernel(loops_dtype dtype, const BatchClass& c, int* smem) {
   }
   if (c.kind == 1) {
     if (dtype != LOOPS_F32) return nullptr;
-    return c.br == 8 ? ffma_kernel<8>(c.G) : ffma_kernel<16>(c.G);
+    return c.br == 8 ? ffma_kernel<8>(c.G, smem, threads) : ffma_kernel<16>(c.G, smem, threads);
   }
   *smem = kHmmaSmemPerWarp * 8;
   if (dtype == LOOPS_F16) return batched_hmma<__half>;
@@ -542,8 +548,8 @@ cudaError_t launch_reduces(const BatchLaunch& L, cudaStream_t s) {
 }  // namespace
 
 int batched_class_grid(loops_dtype dtype, const BatchClass& c) {
-  int smem = 0;
-  ClassKernel k = class_kernel(dtype, c, &smem);
+  int smem = 0, threads = 256;
+  ClassKernel k = class_kernel(dtype, c, &smem, &threads);
   if (!k) return 0;
   int dev = 0, sms = 152, per_sm = 1;
   cudaGetDevice(&dev);
@@ -552,12 +558,12 @@ int batched_class_grid(loops_dtype dtype, const BatchClass& c) {
     cudaGetLastError();
     return 0;
   }
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, smem) != cudaSuccess || per_sm < 1) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem) != cudaSuccess || per_sm < 1) {
     cudaGetLastError();
     per_sm = 1;
   }
   // no more blocks than the class has tasks for their warps
-  const int64_t need = (c.n_tasks + 7) / 8;
+  const int64_t need = (c.n_tasks + threads / 32 - 1) / (threads / 32);
   return (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * per_sm, need));
 }
 
@@ -571,14 +577,14 @@ cudaError_t launch_batched(loops_dtype dtype, const BatchLaunch& L, cudaStream_t
     e = cudaMemsetAsync(L.counters, 0, sizeof(unsigned long long) * (size_t)L.n_classes, s);
   for (int i = 0; i < L.n_classes && e == cudaSuccess; ++i) {
     const BatchClass& c = L.classes[i];
-    int smem = 0;
-    ClassKernel k = class_kernel(dtype, c, &smem);
+    int smem = 0, threads = 256;
+    ClassKernel k = class_kernel(dtype, c, &smem, &threads);
     if (!k) return cudaErrorInvalidValue;
     if (smem > 48 * 1024) {
       e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
       if (e != cudaSuccess) break;
     }
-    k<<<c.grid, 256, smem, s>>>(L.descs, L.tasks + c.first, c.n_tasks, L.counters + i);
+    k<<<c.grid, threads, smem, s>>>(L.descs, L.tasks + c.first, c.n_tasks, L.counters + i);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = rec(1);
