@@ -575,6 +575,16 @@ cudaError_t launch_batched(loops_dtype dtype, const BatchLaunch& L, cudaStream_t
   cudaError_t e = rec(0);
   if (e == cudaSuccess && L.n_classes > 0)
     e = cudaMemsetAsync(L.counters, 0, sizeof(unsigned long long) * (size_t)L.n_classes, s);
+  // with extra branches, the classes are dealt to n_side + 1 parallel branches of the graph:
+  // in two halves of the class list (CSR classes, then BCSR classes, each in N order) for two
+  // branches, round-robin for more; the branches join before the partial sums
+  const int nb = L.n_side > 0 ? std::min(L.n_side + 1, L.n_classes) : 1;
+  if (e == cudaSuccess && nb > 1) {
+    e = cudaEventRecord(L.fork, s);
+    for (int j = 0; j < nb - 1 && e == cudaSuccess; ++j) e = cudaStreamWaitEvent(L.side[j], L.fork, 0);
+  }
+  int n_csr = 0;
+  for (int i = 0; i < L.n_classes; ++i) n_csr += L.classes[i].kind == 0;
   for (int i = 0; i < L.n_classes && e == cudaSuccess; ++i) {
     const BatchClass& c = L.classes[i];
     int smem = 0, threads = 256;
@@ -584,8 +594,16 @@ cudaError_t launch_batched(loops_dtype dtype, const BatchLaunch& L, cudaStream_t
       e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
       if (e != cudaSuccess) break;
     }
-    k<<<c.grid, threads, smem, s>>>(L.descs, L.tasks + c.first, c.n_tasks, L.counters + i);
+    int branch = 0;
+    if (nb == 2) branch = (n_csr > 0 && n_csr < L.n_classes) ? (c.kind > 0) : (i >= L.n_classes / 2);
+    else if (nb > 2) branch = i % nb;
+    cudaStream_t st = branch == 0 ? s : L.side[branch - 1];
+    k<<<c.grid, threads, smem, st>>>(L.descs, L.tasks + c.first, c.n_tasks, L.counters + i);
     e = cudaGetLastError();
+  }
+  for (int j = 0; j < nb - 1 && e == cudaSuccess; ++j) {
+    e = cudaEventRecord(L.join[j], L.side[j]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, L.join[j], 0);
   }
   if (e == cudaSuccess) e = rec(1);
   if (e == cudaSuccess) e = rec(2);

@@ -25,6 +25,9 @@ struct BatchState {
   std::vector<BatchClass> classes;    // task classes, one persistent kernel each
   unsigned long long* d_counters = nullptr;  // one task counter per class
   cudaStream_t cap = nullptr;         // capture stream
+  std::vector<cudaStream_t> side;     // extra branches of the captured graph
+  std::vector<cudaEvent_t> ev_join;   // one per extra branch
+  cudaEvent_t ev_fork = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaEvent_t ev_copied = nullptr;    // the last descriptor upload has read h_desc
@@ -64,6 +67,11 @@ void destroy_batch(BatchState* b) {
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (b->cap) cudaStreamDestroy(b->cap);
+  for (cudaStream_t x : b->side)
+    if (x) cudaStreamDestroy(x);
+  for (cudaEvent_t x : b->ev_join)
+    if (x) cudaEventDestroy(x);
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
   if (b->ev_copied) cudaEventDestroy(b->ev_copied);
   delete b;
 }
@@ -77,6 +85,12 @@ int batch_kernels_per_call(const BatchState* b) {
 namespace {
 
 int elems_per_16b(loops_dtype d) { return d == LOOPS_F32 ? 4 : 8; }
+
+// Branches of the captured graph: the class kernels are dealt to this many parallel branches
+// (their tails overlap); 1 runs every class in turn on one stream.
+#ifndef LOOPS_BATCHED_BRANCHES
+#define LOOPS_BATCHED_BRANCHES 4
+#endif
 
 int next_pow2(int64_t x) {
   int p = 1;
@@ -237,6 +251,16 @@ loops_status build_batch(const loops_csr* As, const int64_t* Ns, int32_t count, 
   if (e == cudaSuccess && !b->classes.empty())
     e = dev_malloc((void**)&b->d_counters, sizeof(unsigned long long) * b->classes.size());
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  const int n_side = std::min<int>(LOOPS_BATCHED_BRANCHES, (int)b->classes.size()) - 1;
+  if (e == cudaSuccess && n_side > 0) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+  for (int i = 0; i < n_side && e == cudaSuccess; ++i) {
+    cudaStream_t x = nullptr;
+    cudaEvent_t j = nullptr;
+    e = cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking);
+    if (e == cudaSuccess) b->side.push_back(x);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&j, cudaEventDisableTiming);
+    if (e == cudaSuccess) b->ev_join.push_back(j);
+  }
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_copied, cudaEventDisableTiming);
   if (e != cudaSuccess) { st = cuda_status(e, "batched plan setup"); destroy_batch(b); return st; }
   b->device_bytes = (int64_t)(sizeof(BatchDesc) * count + sizeof(BatchTask) * b->n_tasks +
@@ -285,6 +309,10 @@ cudaError_t run_batch(BatchState* b, cudaStream_t s) {
   L.bsplits = b->d_bsplits;
   L.n_bsplits = b->n_bsplits;
   L.tev = b->timing ? b->tev : nullptr;
+  L.n_side = (int)b->side.size();
+  L.side = b->side.data();
+  L.fork = b->ev_fork;
+  L.join = b->ev_join.data();
   return launch_batched(b->dtype, L, s);
 }
 

@@ -496,7 +496,8 @@ loops_status autotune_tau(const PlanBuilder& build, int64_t n_rows, int64_t n_co
     o.block_rows = cand.br;
     loops_plan_s* p = nullptr;
     if ((st = build(o, cand.tau, &p))) break;
-    const auto key = std::make_tuple(p->n_rb, p->n_tiles, cand.br);
+    // a split without BCSR blocks is the same plan for either tile height
+    const auto key = std::make_tuple(p->n_rb, p->n_tiles, p->n_rb > 0 ? cand.br : 0);
     if (std::find(seen.begin(), seen.end(), key) != seen.end()) { destroy_plan(p); continue; }
     seen.push_back(key);
     float ms = INFINITY;

@@ -275,6 +275,10 @@ struct BatchLaunch {
   int64_t n_bsplits;
   const cudaEvent_t* tev;              // optional timing events: [0]/[1] around the class
                                        // kernels, [2]/[3] around the partial-sum launches
+  int n_side;                          // extra branches of the graph (0: one stream)
+  const cudaStream_t* side;            // their streams
+  cudaEvent_t fork;                    // the branches start after the counters are zeroed
+  const cudaEvent_t* join;             // one per extra branch: the call waits for all of them
 };
 
 struct BatchState;
