@@ -372,9 +372,10 @@ loops_status loops_plan_batched_device(const loops_csr* As, const int64_t* Ns, i
 /* C_m = A_m . B_m for every matrix of a batched plan. Bs, Cs, ldbs, ldcs: HOST arrays of
  * `count` entries holding device pointers / leading dimensions (rows 16-byte aligned);
  * col_scales: NULL, or a host array of `count` device f32[N_m] pointers (16-bit dtypes; NULL
- * entries mean no scaling). When the pointers differ from the previous call the descriptor
- * table is re-uploaded first (waiting, on the host, for the previous upload to have been
- * read). Stream-ordered otherwise. */
+ * entries mean no scaling). The kernels index each B_m with 32-bit element offsets, so
+ * n_cols x ldbs[m] must stay below 2^31 (LOOPS_ERR_UNSUPPORTED otherwise). When the pointers
+ * differ from the previous call the descriptor table is re-uploaded first (waiting, on the
+ * host, for the previous upload to have been read). Stream-ordered otherwise. */
 loops_status loops_spmm_batched(loops_plan_t plan, const void* const* Bs, const int64_t* ldbs,
                                 void* const* Cs, const int64_t* ldcs, const float* const* col_scales,
                                 loops_stream_t stream);

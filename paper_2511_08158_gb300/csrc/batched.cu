@@ -26,15 +26,21 @@
 #include "device_common.cuh"
 #include "loops_internal.h"
 
-// Tuning knobs (compile time): resident blocks per SM the CSR and FFMA class kernels must
-// allow (their register caps), B-row loads in flight per lane in FP32 CSR items, tiles in
+// Tuning knobs (compile time): resident blocks per SM the CSR class kernels must allow (their
+// register caps: FP32, 16-bit), B-row loads in flight
+// per lane in FP32 CSR items (a power of two), the same for the FFMA class kernels, tiles in
 // flight in B_r = 8 FFMA units, and cp.async stages of the HMMA units.
 #ifndef LOOPS_BATCHED_CSR_MIN_BLOCKS
 #define LOOPS_BATCHED_CSR_MIN_BLOCKS 3
 #endif
+#ifndef LOOPS_BATCHED_CSR16_MIN_BLOCKS
+#define LOOPS_BATCHED_CSR16_MIN_BLOCKS 4
+#endif
 #ifndef LOOPS_BATCHED_CSR_LOADS
 #define LOOPS_BATCHED_CSR_LOADS 8
 #endif
+static_assert(LOOPS_BATCHED_CSR_LOADS >= 2 && (LOOPS_BATCHED_CSR_LOADS & (LOOPS_BATCHED_CSR_LOADS - 1)) == 0,
+              "CSR loads in flight must be a power of two: the load batches tile a chunk exactly");
 #ifndef LOOPS_BATCHED_FFMA_TILES
 #define LOOPS_BATCHED_FFMA_TILES 4
 #endif
@@ -104,16 +110,23 @@ __device__ __forceinline__ void csr_item(const BatchDesc& d, int64_t item, int s
   // twice the registers), half that with two vectors per lane
   constexpr int UMAX = (VE == 8 ? LOOPS_BATCHED_CSR_LOADS / 2 : LOOPS_BATCHED_CSR_LOADS) / VPL;
   constexpr int U = UMAX < CH ? UMAX : CH;
-  const int64_t beg = d.item_ptr[item], end = d.item_ptr[item + 1];
+  static_assert(U >= 1 && CH % U == 0, "load batches must tile the chunk");
+  // 32-bit indices inside the item and inside B (the batched call keeps every B below 2^31
+  // elements), 64-bit pointers only for the bases: fewer registers per lane
+  const int64_t beg = d.item_ptr[item];
+  const int32_t len = (int32_t)(d.item_ptr[item + 1] - beg);
   const int32_t row = d.item_row[item];
-  const TB* __restrict__ Bp = reinterpret_cast<const TB*>(d.B);
-  const TB* __restrict__ vals = reinterpret_cast<const TB*>(d.val);
-  int64_t coff[VPL];
+  const int32_t* __restrict__ colp = d.col + beg;
+  const TB* __restrict__ valp = reinterpret_cast<const TB*>(d.val) + beg;
+  const uint32_t ldb = (uint32_t)d.ldb;
+  const int32_t N = (int32_t)d.N;
+  const TB* bl[VPL];
   bool colok[VPL];
 #pragma unroll
   for (int p = 0; p < VPL; ++p) {
-    coff[p] = (int64_t)(p * G + sub) * VE;
-    colok[p] = coff[p] < d.N;
+    const int32_t off = (p * G + sub) * VE;
+    colok[p] = off < N;
+    bl[p] = reinterpret_cast<const TB*>(d.B) + off;
   }
   TAcc acc[VPL][VE];
 #pragma unroll
@@ -121,15 +134,15 @@ __device__ __forceinline__ void csr_item(const BatchDesc& d, int64_t item, int s
 #pragma unroll
     for (int e = 0; e < VE; ++e) acc[p][e] = TAcc(0);
 
-  auto fetch = [&](int64_t k0, int32_t (&c)[R], TAcc (&v)[R]) {
+  auto fetch = [&](int32_t k0, int32_t (&c)[R], TAcc (&v)[R]) {
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      const int64_t k = k0 + r * G + sub;
+      const int32_t k = k0 + r * G + sub;
       c[r] = 0;
       v[r] = TAcc(0);
-      if (k < end) {
-        c[r] = __ldg(d.col + k);
-        v[r] = Tr::to_acc(vals[k]);
+      if (k < len) {
+        c[r] = __ldg(colp + k);
+        v[r] = Tr::to_acc(valp[k]);
       }
     }
   };
@@ -141,12 +154,12 @@ __device__ __forceinline__ void csr_item(const BatchDesc& d, int64_t item, int s
   };
   int32_t c[R];
   TAcc v[R];
-  fetch(beg, c, v);
-  for (int64_t k0 = beg; k0 < end; k0 += CH) {
+  fetch(0, c, v);
+  for (int32_t k0 = 0; k0 < len; k0 += CH) {
     int32_t cn[R];
     TAcc vn[R];
     fetch(k0 + CH, cn, vn);                             // next chunk's entries, in flight now
-    if (k0 + CH <= end) {                               // full chunk: batches of U loads, then FMAs
+    if (k0 + CH <= len) {                               // full chunk: batches of U loads, then FMAs
 #pragma unroll
       for (int e0 = 0; e0 < CH; e0 += U) {
         uint4 bv[U][VPL];
@@ -154,11 +167,10 @@ __device__ __forceinline__ void csr_item(const BatchDesc& d, int64_t item, int s
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           const int e = e0 + u;
-          const int cj = __shfl_sync(gmask, c[e / G], e % G, G);
+          const uint32_t cj = (uint32_t)__shfl_sync(gmask, c[e / G], e % G, G);
           av[u] = __shfl_sync(gmask, v[e / G], e % G, G);
-          const TB* brow = Bp + (int64_t)cj * d.ldb;
 #pragma unroll
-          for (int p = 0; p < VPL; ++p) bv[u][p] = colok[p] ? ldg16(brow + coff[p]) : make_uint4(0, 0, 0, 0);
+          for (int p = 0; p < VPL; ++p) bv[u][p] = colok[p] ? ldg16(bl[p] + cj * ldb) : make_uint4(0, 0, 0, 0);
         }
 #pragma unroll
         for (int u = 0; u < U; ++u)
@@ -166,16 +178,27 @@ __device__ __forceinline__ void csr_item(const BatchDesc& d, int64_t item, int s
           for (int p = 0; p < VPL; ++p) fma_vec(p, bv[u][p], av[u]);
       }
     } else {                                            // the last, partial chunk
-      const int cnt = (int)(end - k0);
+      // the same batches under predicates: entries past the row's end load nothing and carry
+      // zero values, so they add exact zeros, and the live loads of a batch stay in flight
+      // together instead of one entry at a time
+      const int cnt = len - k0;
 #pragma unroll
-      for (int e = 0; e < CH; ++e) {
-        if (e < cnt) {
-          const int cj = __shfl_sync(gmask, c[e / G], e % G, G);
-          const TAcc a = __shfl_sync(gmask, v[e / G], e % G, G);
-          const TB* brow = Bp + (int64_t)cj * d.ldb;
+      for (int e0 = 0; e0 < CH; e0 += U) {
+        if (e0 < cnt) {
+          uint4 bv[U][VPL];
+          TAcc av[U];
 #pragma unroll
-          for (int p = 0; p < VPL; ++p)
-            if (colok[p]) fma_vec(p, ldg16(brow + coff[p]), a);
+          for (int u = 0; u < U; ++u) {
+            const int e = e0 + u;
+            const uint32_t cj = (uint32_t)__shfl_sync(gmask, c[e / G], e % G, G);
+            av[u] = __shfl_sync(gmask, v[e / G], e % G, G);
+#pragma unroll
+            for (int p = 0; p < VPL; ++p) bv[u][p] = ldg16_if(colok[p] && e < cnt, bl[p] + cj * ldb);
+          }
+#pragma unroll
+          for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int p = 0; p < VPL; ++p) fma_vec(p, bv[u][p], av[u]);
         }
       }
     }
@@ -190,12 +213,13 @@ __device__ __forceinline__ void csr_item(const BatchDesc& d, int64_t item, int s
 #pragma unroll
     for (int p = 0; p < VPL; ++p) {
       if (!colok[p]) continue;
+      const int32_t off = (p * G + sub) * VE;
       TC o[VE];
 #pragma unroll
-      for (int e = 0; e < VE; ++e) o[e] = Tr::kScaled ? (TC)(acc[p][e] * col_mult<Tr>(d, coff[p] + e)) : (TC)acc[p][e];
+      for (int e = 0; e < VE; ++e) o[e] = Tr::kScaled ? (TC)(acc[p][e] * col_mult<Tr>(d, off + e)) : (TC)acc[p][e];
 #pragma unroll
       for (int q = 0; q < (int)(VE * sizeof(TC) / 16); ++q)
-        *reinterpret_cast<uint4*>(crow + coff[p] + q * (16 / sizeof(TC))) =
+        *reinterpret_cast<uint4*>(crow + off + q * (16 / sizeof(TC))) =
             *reinterpret_cast<const uint4*>(&o[q * (16 / sizeof(TC))]);
     }
   } else {
@@ -203,14 +227,20 @@ __device__ __forceinline__ void csr_item(const BatchDesc& d, int64_t item, int s
 #pragma unroll
     for (int p = 0; p < VPL; ++p) {
       if (!colok[p]) continue;
+      const int32_t off = (p * G + sub) * VE;
 #pragma unroll
-      for (int e = 0; e < VE; ++e) srow[coff[p] + e] = acc[p][e];
+      for (int e = 0; e < VE; ++e) srow[off + e] = acc[p][e];
     }
   }
 }
 
+template <class Tr>
+constexpr int csr_min_blocks() {
+  return Tr::kVE == 8 ? LOOPS_BATCHED_CSR16_MIN_BLOCKS : LOOPS_BATCHED_CSR_MIN_BLOCKS;
+}
+
 template <class Tr, int G, int VPL>
-__global__ void __launch_bounds__(256, LOOPS_BATCHED_CSR_MIN_BLOCKS) batched_csr(const BatchDesc* __restrict__ descs,
+__global__ void __launch_bounds__(256, csr_min_blocks<Tr>()) batched_csr(const BatchDesc* __restrict__ descs,
                                                       const BatchTask* __restrict__ tasks, int64_t n_tasks,
                                                       unsigned long long* counter) {
   const int lane = threadIdx.x & 31;
@@ -254,26 +284,39 @@ __device__ __forceinline__ void ffma_unit(const BatchDesc& d, int64_t u, int sub
         for (int e = 0; e < 4; ++e) acc[r4 * 4 + i][e] = fmaf(a4[i], bv[e], acc[r4 * 4 + i][e]);
     }
   };
-  auto load_tile = [&](int64_t tt, uint4& v, uint4 (&w)[BR / 4]) {
-    const int32_t c = __ldg(d.tile_col + tt);
-    v = (c >= 0 && colok) ? ldg16(Bp + (int64_t)c * d.ldb + n) : make_uint4(0, 0, 0, 0);
+  // tile columns of the next batch are read one batch ahead, so each batch's B and A loads
+  // issue together without waiting on their column indices (-1 past the unit's end)
+  auto load_cols = [&](int64_t base, int32_t (&cc)[T]) {
 #pragma unroll
-    for (int r4 = 0; r4 < BR / 4; ++r4) w[r4] = ldg16(Av + tt * BR + r4 * 4);
+    for (int q = 0; q < T; ++q) cc[q] = base + q < t1 ? __ldg(d.tile_col + base + q) : -1;
   };
+  auto load_tile = [&](bool live, int64_t tt, int32_t c, uint4& v, uint4 (&w)[BR / 4]) {
+    v = ldg16_if(live && c >= 0 && colok, Bp + (int64_t)c * d.ldb + n);
+#pragma unroll
+    for (int r4 = 0; r4 < BR / 4; ++r4) w[r4] = ldg16_if(live, Av + tt * BR + r4 * 4);
+  };
+  int32_t c[T];
+  load_cols(t0, c);
   int64_t tt = t0;
   for (; tt + T <= t1; tt += T) {
+    int32_t cn[T];
+    load_cols(tt + T, cn);
     uint4 v[T];
     uint4 w[T][BR / 4];
 #pragma unroll
-    for (int q = 0; q < T; ++q) load_tile(tt + q, v[q], w[q]);
+    for (int q = 0; q < T; ++q) load_tile(true, tt + q, c[q], v[q], w[q]);
 #pragma unroll
     for (int q = 0; q < T; ++q) tile_fma(v[q], w[q]);
+#pragma unroll
+    for (int q = 0; q < T; ++q) c[q] = cn[q];
   }
-  for (; tt < t1; ++tt) {
-    uint4 v;
-    uint4 w[BR / 4];
-    load_tile(tt, v, w);
-    tile_fma(v, w);
+  if (tt < t1) {  // the last 1 .. T-1 tiles as one batch under predicates (the rest add zeros)
+    uint4 v[T];
+    uint4 w[T][BR / 4];
+#pragma unroll
+    for (int q = 0; q < T; ++q) load_tile(tt + q < t1, tt + q, c[q], v[q], w[q]);
+#pragma unroll
+    for (int q = 0; q < T; ++q) tile_fma(v[q], w[q]);
   }
   if (!colok) return;
   if (slot >= 0) {  // unit of a split block: partial sums
@@ -473,21 +516,33 @@ using ClassKernel = void (*)(const BatchDesc*, const BatchTask*, int64_t, unsign
 
 template <class Tr>
 ClassKernel csr_kernel(int G, int VPL) {
-  if (VPL == 2) {
-    switch (G) {
-      case 8: return batched_csr<Tr, 8, 2>;
-      case 16: return batched_csr<Tr, 16, 2>;
+  // 16-bit rows (N <= 128) take one vector per lane: at most 16 lanes, never two vectors
+  if constexpr (Tr::kVE == 8) {
+    switch (VPL == 1 ? G : 0) {
+      case 1: return batched_csr<Tr, 1, 1>;
+      case 2: return batched_csr<Tr, 2, 1>;
+      case 4: return batched_csr<Tr, 4, 1>;
+      case 8: return batched_csr<Tr, 8, 1>;
+      case 16: return batched_csr<Tr, 16, 1>;
       default: return nullptr;
     }
-  }
-  switch (G) {
-    case 1: return batched_csr<Tr, 1, 1>;
-    case 2: return batched_csr<Tr, 2, 1>;
-    case 4: return batched_csr<Tr, 4, 1>;
-    case 8: return batched_csr<Tr, 8, 1>;
-    case 16: return batched_csr<Tr, 16, 1>;
-    case 32: return batched_csr<Tr, 32, 1>;
-    default: return nullptr;
+  } else {
+    if (VPL == 2) {
+      switch (G) {
+        case 8: return batched_csr<Tr, 8, 2>;
+        case 16: return batched_csr<Tr, 16, 2>;
+        default: return nullptr;
+      }
+    }
+    switch (G) {
+      case 1: return batched_csr<Tr, 1, 1>;
+      case 2: return batched_csr<Tr, 2, 1>;
+      case 4: return batched_csr<Tr, 4, 1>;
+      case 8: return batched_csr<Tr, 8, 1>;
+      case 16: return batched_csr<Tr, 16, 1>;
+      case 32: return batched_csr<Tr, 32, 1>;
+      default: return nullptr;
+    }
   }
 }
 

@@ -40,6 +40,7 @@ struct BatchState {
   double model_measured_gflops = NAN; // the per-matrix choice, measured
   double timed_best_gflops = NAN;     // the best single-threshold candidate, measured
   cudaEvent_t tev[4] = {nullptr, nullptr, nullptr, nullptr};  // caller's timing events
+  cudaGraphNode_t tev_node[4] = {nullptr, nullptr, nullptr, nullptr};  // their nodes in `graph`
   bool timing = false;
   // loops_spmm_batched_host: one device staging area (every B, then every C, dense rows)
   void* stage = nullptr;
@@ -47,14 +48,51 @@ struct BatchState {
 };
 
 void batch_set_timing(BatchState* b, const cudaEvent_t* ev) {
+  // new events for a graph that already records events: point its event nodes at them (the
+  // launches already queued keep the old ones), with no capture or instantiation
+  if (ev && b->timing && b->exec && b->tev_node[0] && b->tev_node[1] && b->tev_node[2] && b->tev_node[3]) {
+    bool ok = true;
+    for (int i = 0; i < 4 && ok; ++i) ok = cudaGraphExecEventRecordNodeSetEvent(b->exec, b->tev_node[i], ev[i]) == cudaSuccess;
+    if (ok) {
+      for (int i = 0; i < 4; ++i) b->tev[i] = ev[i];
+      return;
+    }
+    cudaGetLastError();
+  }
   b->timing = ev != nullptr;
-  for (int i = 0; i < 4; ++i) b->tev[i] = ev ? ev[i] : nullptr;
+  for (int i = 0; i < 4; ++i) {
+    b->tev[i] = ev ? ev[i] : nullptr;
+    b->tev_node[i] = nullptr;
+  }
   // the next call captures the graph again, with or without the event nodes
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   b->exec = nullptr;
   b->graph = nullptr;
 }
+
+namespace {
+
+// The event-record nodes of a captured graph that record the caller's timing events.
+void find_timing_nodes(BatchState* b) {
+  for (auto& n : b->tev_node) n = nullptr;
+  if (!b->timing || !b->graph) return;
+  size_t n = 0;
+  if (cudaGraphGetNodes(b->graph, nullptr, &n) != cudaSuccess) { cudaGetLastError(); return; }
+  std::vector<cudaGraphNode_t> nodes(n);
+  if (n && cudaGraphGetNodes(b->graph, nodes.data(), &n) != cudaSuccess) { cudaGetLastError(); return; }
+  for (cudaGraphNode_t node : nodes) {
+    cudaGraphNodeType t;
+    cudaEvent_t e = nullptr;
+    if (cudaGraphNodeGetType(node, &t) != cudaSuccess || t != cudaGraphNodeTypeEventRecord) continue;
+    if (cudaGraphEventRecordNodeGetEvent(node, &e) != cudaSuccess) continue;
+    for (int i = 0; i < 4; ++i)
+      if (e == b->tev[i] && !b->tev_node[i]) { b->tev_node[i] = node; break; }
+  }
+  cudaGetLastError();
+}
+
+}  // namespace
 
 void destroy_batch(BatchState* b) {
   if (!b) return;
@@ -98,14 +136,16 @@ int next_pow2(int64_t x) {
   return p;
 }
 
-// Class of a matrix's CSR items: G lanes per item with VPL 16-byte column vectors each (two
-// vectors per lane once a row has at least LOOPS_BATCHED_CSR_VPL2 of them).
+// Class of a matrix's CSR items: G lanes per item with VPL 16-byte column vectors each. FP32
+// rows take two vectors per lane once they have at least LOOPS_BATCHED_CSR_VPL2 of them (fewer
+// lanes per item, more items per warp); 16-bit rows (at most 16 vectors) always take one,
+// which measured faster (their unpacked vectors double the registers of a second one).
 #ifndef LOOPS_BATCHED_CSR_VPL2
 #define LOOPS_BATCHED_CSR_VPL2 16
 #endif
 void csr_shape(loops_dtype dtype, int64_t N, int32_t* G, int32_t* vpl) {
   const int64_t nvec = N / elems_per_16b(dtype);
-  *vpl = nvec >= LOOPS_BATCHED_CSR_VPL2 ? 2 : 1;
+  *vpl = dtype == LOOPS_F32 && nvec >= LOOPS_BATCHED_CSR_VPL2 ? 2 : 1;
   *G = next_pow2(*vpl == 2 ? (nvec + 1) / 2 : nvec);
 }
 
@@ -358,6 +398,7 @@ loops_status spmm_batch(BatchState* b, const void* const* Bs, const int64_t* ldb
       cudaGetLastError();
       return cuda_status(e, "graph capture of the batched launch");
     }
+    find_timing_nodes(b);
   }
   return cuda_status(cudaGraphLaunch(b->exec, s), "graph launch");
 }
@@ -702,6 +743,11 @@ loops_status loops_spmm_batched(loops_plan_t p, const void* const* Bs, const int
       set_error("bad dense operand of matrix " + std::to_string(m));
       return LOOPS_ERR_INVALID_ARG;
     }
+    if (sp->n_cols > 0 && ldbs[m] > (INT32_MAX / sp->n_cols)) {
+      set_error("batched SpMM indexes B with 32-bit offsets: n_cols x ldb must stay below 2^31 (matrix " +
+                std::to_string(m) + ")");
+      return LOOPS_ERR_UNSUPPORTED;
+    }
     if (((uintptr_t)Bs[m] % 16) || ((uintptr_t)Cs[m] % 16) || ((ldbs[m] * eb) % 16) || ((ldcs[m] * 4) % 16)) {
       set_error("batched SpMM needs 16-byte aligned rows of B and C (matrix " + std::to_string(m) + ")");
       return LOOPS_ERR_UNSUPPORTED;
@@ -733,6 +779,11 @@ loops_status loops_spmm_batched_host(loops_plan_t p, const void* const* Bs_host,
     if (ldbs[m] < sp->N || ldcs[m] < sp->N || (!Bs_host[m] && sp->n_cols > 0) || (!Cs_host[m] && sp->n_rows > 0)) {
       set_error("bad host operand of matrix " + std::to_string(m));
       return LOOPS_ERR_INVALID_ARG;
+    }
+    if (sp->n_cols > 0 && sp->N > (INT32_MAX / sp->n_cols)) {
+      set_error("batched SpMM indexes B with 32-bit offsets: n_cols x N must stay below 2^31 (matrix " +
+                std::to_string(m) + ")");
+      return LOOPS_ERR_UNSUPPORTED;
     }
     boff[(size_t)m] = off;
     off += (sp->n_cols * sp->N * eb + 255) / 256 * 256;

@@ -158,31 +158,30 @@ __global__ void __launch_bounds__(256, (csr_min_blocks<Tr, VPL>())) csr_spmm_vec
         }
     }
     if constexpr (U > 1) {
-    if (j0 < cnt) {  // tail of 1 .. U-1 entries: no multiply by padded zeros
+    if (j0 < cnt) {  // tail of 1 .. U-1 entries: one batch under predicates
+      // entries past the tail load nothing and take a zero value, so they add exact zeros;
+      // the live loads issue together instead of one per round trip
       uint4 bv[U - 1][VPL];
       TAcc av[U - 1];
 #pragma unroll
       for (int u = 0; u < U - 1; ++u) {
-        if (j0 + u < cnt) {
-          const int cj = __shfl_sync(gmask, c, (j0 + u) & (G - 1), G);
-          av[u] = __shfl_sync(gmask, v, (j0 + u) & (G - 1), G);
-          const TB* brow = Bp + (int64_t)cj * a.ldb;
+        const bool live = j0 + u < cnt;
+        const int cj = __shfl_sync(gmask, c, (j0 + u) & (G - 1), G);
+        const TAcc vj = __shfl_sync(gmask, v, (j0 + u) & (G - 1), G);
+        av[u] = live ? vj : TAcc(0);
+        const TB* brow = Bp + (int64_t)cj * a.ldb;
 #pragma unroll
-          for (int p = 0; p < VPL; ++p) bv[u][p] = colok[p] ? ldg16(brow + coff[p]) : make_uint4(0, 0, 0, 0);
-        }
+        for (int p = 0; p < VPL; ++p) bv[u][p] = ldg16_if(live && colok[p], brow + coff[p]);
       }
 #pragma unroll
-      for (int u = 0; u < U - 1; ++u) {
-        if (j0 + u < cnt) {
+      for (int u = 0; u < U - 1; ++u)
 #pragma unroll
-          for (int p = 0; p < VPL; ++p) {
-            TAcc b[VE];
-            unpack16<Tr>(bv[u][p], b);
+        for (int p = 0; p < VPL; ++p) {
+          TAcc b[VE];
+          unpack16<Tr>(bv[u][p], b);
 #pragma unroll
-            for (int e = 0; e < VE; ++e) acc[p][e] = fma(av[u], b[e], acc[p][e]);
-          }
+          for (int e = 0; e < VE; ++e) acc[p][e] = fma(av[u], b[e], acc[p][e]);
         }
-      }
     }
     }
   }

@@ -89,6 +89,18 @@ __device__ __forceinline__ uint4 ldg16(const void* p) {
   return r;
 }
 
+// 16-byte load under a predicate, zeros when it is off: no branch, so a batch of them issues
+// back to back like unpredicated loads
+__device__ __forceinline__ uint4 ldg16_if(bool on, const void* p) {
+  uint4 r = make_uint4(0, 0, 0, 0);
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %4, 0;\n\t"
+      "@q ld.global.nc.v4.u32 {%0,%1,%2,%3}, [%5];\n\t}"
+      : "+r"(r.x), "+r"(r.y), "+r"(r.z), "+r"(r.w)
+      : "r"((int)on), "l"(p));
+  return r;
+}
+
 // ------------------------------------------------------------------ mbarrier / bulk copy
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);

@@ -86,6 +86,37 @@ def test_batched_graph_replay_and_pointer_change(lp, small_batch):
     assert max(rel_l2(C.double().cpu().numpy(), r) for C, r in zip(Cs2, refs)) <= TOL[fmt]
 
 
+def test_batched_timing_events_swapped_between_calls(lp, small_batch):
+    """New timing events before every call (as a timed loop does) repoint the captured graph's
+    event nodes; every call still computes the product, every event pair measures it, and
+    switching the events off and on again works."""
+    fmt = "f32"
+    plan, Bs, Cs, refs, errs = _run(lp, small_batch, fmt, 2.0)
+    assert max(errs) <= TOL[fmt]
+    s = torch.cuda.current_stream()
+    for rnd in range(2):
+        pairs = []
+        for k in range(4):
+            evs = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            for e in evs:
+                e.record(s)
+            torch.cuda.synchronize()
+            plan.set_timing_events([e.cuda_event for e in evs])
+            for C in Cs:
+                C.fill_(float("nan"))
+            plan.spmm(Bs, Cs)
+            torch.cuda.synchronize()
+            assert max(rel_l2(C.double().cpu().numpy(), r) for C, r in zip(Cs, refs)) <= TOL[fmt]
+            pairs.append(evs)
+        for evs in pairs:
+            assert evs[0].elapsed_time(evs[1]) > 0.0
+            assert evs[2].elapsed_time(evs[3]) >= 0.0
+        plan.set_timing_events(None)
+        plan.spmm(Bs, Cs)
+        torch.cuda.synchronize()
+        assert max(rel_l2(C.double().cpu().numpy(), r) for C, r in zip(Cs, refs)) <= TOL[fmt]
+
+
 def test_batched_split_rows_and_column_scales(lp):
     mats = W.batched_mix(count=6, seed=9, min_rows=200, max_rows=1500)
     # a long row in every matrix
@@ -109,6 +140,28 @@ def test_batched_rejects_unsupported_n(lp):
         lp.BatchedPlan([A], [6], "f32", tau=2.0)
     with pytest.raises(lp.LoopsError):
         lp.BatchedPlan([A], [32], "f64", tau=2.0)
+
+
+def test_batched_rejects_b_beyond_32bit_offsets(lp):
+    """The kernels index B with 32-bit element offsets: a leading dimension that puts the last
+    row of B at or past 2^31 elements is refused before anything runs."""
+    import ctypes
+    A = W.random_csr(64, 1 << 16, 0.001, 3)
+    plan = lp.BatchedPlan([A], [32], "f32", tau=2.0)
+    B = torch.zeros((A.n_cols, 32), device="cuda")
+    C = torch.zeros((A.n_rows, 32), device="cuda")
+    L = plan._L
+    ldb_bad = ((1 << 31) // A.n_cols + 4) // 4 * 4        # 16-byte rows, n_cols x ldb > 2^31
+    bp = (ctypes.c_void_p * 1)(B.data_ptr())
+    cp = (ctypes.c_void_p * 1)(C.data_ptr())
+    lc = (ctypes.c_int64 * 1)(32)
+    st = L.loops_spmm_batched(plan._h, bp, (ctypes.c_int64 * 1)(ldb_bad), cp, lc, None, None)
+    assert st == 3                                          # LOOPS_ERR_UNSUPPORTED
+    assert b"32-bit" in L.loops_last_error()
+    st = L.loops_spmm_batched(plan._h, bp, (ctypes.c_int64 * 1)(32), cp, lc, None, None)
+    assert st == 0
+    torch.cuda.synchronize()
+    plan.destroy()
 
 
 def test_batched_blocks_cut_into_units(lp):
