@@ -382,11 +382,17 @@ loops_status loops_spmm_batched(loops_plan_t plan, const void* const* Bs, const 
 
 /* End-to-end batched SpMM with HOST buffers: copies every B_m (host, n_cols x N_m, ldbs[m],
  * in the plan dtype; pinned memory makes the copies asynchronous and fast) into one
- * plan-owned device staging area, runs the batch (loops_spmm_batched, no column scales),
- * copies every C_m (f32, n_rows x N_m, ldcs[m]) back to the host and synchronises `stream`.
- * The staging area (all B and C of the batch, dense) is allocated on the first call and kept
- * until the plan is destroyed. No counterpart in the paper (its operands never leave the
- * CPU's memory). */
+ * plan-owned device staging area, runs the batch (no column scales), copies every C_m (f32,
+ * n_rows x N_m, ldcs[m]) back to the host and synchronises `stream`. The matrices go in up to
+ * 16 groups of consecutive matrices (about equal bytes): group g's kernels run on `stream`
+ * once its B operands are in, while later groups' B operands are copied in and earlier
+ * groups' C results copied out on two plan-owned streams. Matrices whose dense host operands
+ * lie back to back in memory (one host arena for all B, one for all C, in matrix order) move
+ * in one copy per group and direction, which the CPU-GPU link carries at a higher rate than
+ * many small ones; other layouts are copied matrix by matrix, and no byte outside the C_m
+ * operands is written. The staging area is allocated on the first call and kept until the
+ * plan is destroyed. On an error no copy is left in flight. No counterpart in the paper (its operands never leave
+ * the CPU's memory). */
 loops_status loops_spmm_batched_host(loops_plan_t plan, const void* const* Bs_host, const int64_t* ldbs,
                                      void* const* Cs_host, const int64_t* ldcs, loops_stream_t stream);
 

@@ -45,6 +45,23 @@ struct BatchState {
   // loops_spmm_batched_host: one device staging area (every B, then every C, dense rows)
   void* stage = nullptr;
   int64_t stage_bytes = 0;
+  // host copies of the task list (sorted) and of the partial-sum lists, for the host call's
+  // groups of matrices
+  std::vector<BatchTask> h_tasks;
+  std::vector<int2> h_splits, h_bsplits;
+  // loops_spmm_batched_host pipeline: consecutive matrices in groups; group g's copies in,
+  // kernels and copies out overlap the neighbouring groups' on three streams
+  struct HostGroup {
+    int32_t m0 = 0, m1 = 0;           // matrices [m0, m1)
+    std::vector<BatchClass> classes;  // the classes' sub-runs of the task list for these matrices
+    int64_t split0 = 0, n_splits = 0, bsplit0 = 0, n_bsplits = 0;
+    int64_t counter0 = 0;             // first of its task counters in d_gcounters
+  };
+  std::vector<HostGroup> groups;
+  unsigned long long* d_gcounters = nullptr;
+  cudaStream_t copy_in = nullptr, copy_out = nullptr;
+  cudaEvent_t ev_start = nullptr, ev_fin = nullptr;
+  std::vector<cudaEvent_t> ev_in, ev_out;
 };
 
 void batch_set_timing(BatchState* b, const cudaEvent_t* ev) {
@@ -101,7 +118,7 @@ void destroy_batch(BatchState* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   if (b->h_desc) cudaFreeHost(b->h_desc);
-  void* ptrs[] = {b->d_desc, b->d_tasks, b->d_splits, b->d_bsplits, b->d_counters, b->stage};
+  void* ptrs[] = {b->d_desc, b->d_tasks, b->d_splits, b->d_bsplits, b->d_counters, b->stage, b->d_gcounters};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (b->cap) cudaStreamDestroy(b->cap);
@@ -111,6 +128,14 @@ void destroy_batch(BatchState* b) {
     if (x) cudaEventDestroy(x);
   if (b->ev_fork) cudaEventDestroy(b->ev_fork);
   if (b->ev_copied) cudaEventDestroy(b->ev_copied);
+  for (cudaStream_t x : {b->copy_in, b->copy_out})
+    if (x) cudaStreamDestroy(x);
+  for (cudaEvent_t x : {b->ev_start, b->ev_fin})
+    if (x) cudaEventDestroy(x);
+  for (cudaEvent_t x : b->ev_in)
+    if (x) cudaEventDestroy(x);
+  for (cudaEvent_t x : b->ev_out)
+    if (x) cudaEventDestroy(x);
   delete b;
 }
 
@@ -333,6 +358,9 @@ loops_status build_batch(const loops_csr* As, const int64_t* Ns, int32_t count, 
     d.inv_scale = (float)(1.0 / p->scale);
     b->device_bytes += p->dev.device_bytes;
   }
+  b->h_tasks = std::move(sorted);
+  b->h_splits = std::move(splits);
+  b->h_bsplits = std::move(bsplits);
   *out = b;
   return LOOPS_OK;
 }
@@ -356,11 +384,10 @@ cudaError_t run_batch(BatchState* b, cudaStream_t s) {
   return launch_batched(b->dtype, L, s);
 }
 
-// Per call: refresh the descriptors' dense pointers if they changed (one upload from the
-// pinned copy, which is not rewritten before the previous upload has read it), then replay
-// the captured graph -- one persistent launch, plus the split-row sums if any.
-loops_status spmm_batch(BatchState* b, const void* const* Bs, const int64_t* ldbs, void* const* Cs,
-                        const int64_t* ldcs, const float* const* col_scales, cudaStream_t s) {
+// Refresh the descriptors' dense pointers if they changed: one upload from the pinned copy,
+// which is not rewritten before the previous upload has read it.
+cudaError_t refresh_descs(BatchState* b, const void* const* Bs, const int64_t* ldbs, void* const* Cs,
+                          const int64_t* ldcs, const float* const* col_scales, cudaStream_t s) {
   bool changed = !b->copied_once;
   for (int32_t m = 0; m < b->count && !changed; ++m) {
     const BatchDesc& d = b->h_desc[m];
@@ -371,7 +398,7 @@ loops_status spmm_batch(BatchState* b, const void* const* Bs, const int64_t* ldb
   if (changed) {
     if (b->copied_once) {
       e = cudaEventSynchronize(b->ev_copied);
-      if (e != cudaSuccess) return cuda_status(e, "wait for descriptor upload");
+      if (e != cudaSuccess) return e;
     }
     for (int32_t m = 0; m < b->count; ++m) {
       BatchDesc& d = b->h_desc[m];
@@ -383,9 +410,18 @@ loops_status spmm_batch(BatchState* b, const void* const* Bs, const int64_t* ldb
     }
     e = cudaMemcpyAsync(b->d_desc, b->h_desc, sizeof(BatchDesc) * (size_t)b->count, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaEventRecord(b->ev_copied, s);
-    if (e != cudaSuccess) return cuda_status(e, "descriptor upload");
+    if (e != cudaSuccess) return e;
     b->copied_once = true;
   }
+  return cudaSuccess;
+}
+
+// Per call: refresh the descriptors, then replay the captured graph (the class kernels, plus
+// the partial sums if any).
+loops_status spmm_batch(BatchState* b, const void* const* Bs, const int64_t* ldbs, void* const* Cs,
+                        const int64_t* ldcs, const float* const* col_scales, cudaStream_t s) {
+  cudaError_t e = refresh_descs(b, Bs, ldbs, Cs, ldcs, col_scales, s);
+  if (e != cudaSuccess) return cuda_status(e, "descriptor upload");
   if (!b->exec) {
     e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
@@ -760,6 +796,92 @@ loops_status loops_spmm_batched(loops_plan_t p, const void* const* Bs, const int
   return spmm_batch(b, Bs, ldbs, Cs, ldcs, col_scales, (cudaStream_t)stream);
 }
 
+namespace {
+
+// Groups of consecutive matrices for the host call's pipeline, about equal in bytes moved (B
+// in, C out). Each group runs its matrices' sub-runs of every class's tasks (the task list is
+// in matrix order within a class) with its own task counters, and its own runs of the
+// partial-sum lists (in matrix order too).
+#ifndef LOOPS_BATCHED_HOST_GROUPS
+#define LOOPS_BATCHED_HOST_GROUPS 16
+#endif
+cudaError_t build_host_groups(BatchState* b) {
+  const int64_t eb = b->dtype == LOOPS_F32 ? 4 : 2;
+  std::vector<int64_t> bytes((size_t)b->count);
+  int64_t total = 0;
+  for (int32_t m = 0; m < b->count; ++m) {
+    const loops_plan_s* sp = b->subs[(size_t)m];
+    bytes[(size_t)m] = sp->n_cols * sp->N * eb + sp->n_rows * sp->N * 4;
+    total += bytes[(size_t)m];
+  }
+  const int ng = std::max(1, std::min<int>(LOOPS_BATCHED_HOST_GROUPS, b->count));
+  auto by_m = [](const BatchTask& t, int32_t m) { return t.m < m; };
+  auto split_m = [](const int2& x, int32_t m) { return x.x < m; };
+  int64_t n_counters = 0, acc = 0;
+  int32_t m0 = 0;
+  for (int g = 0; g < ng && m0 < b->count; ++g) {
+    const int64_t target = total / ng * (g + 1);
+    int32_t m1 = m0;
+    while (m1 < b->count) {
+      if (m1 > m0 && g < ng - 1 && acc + bytes[(size_t)m1] > target) break;
+      acc += bytes[(size_t)m1++];
+    }
+    BatchState::HostGroup hg;
+    hg.m0 = m0;
+    hg.m1 = m1;
+    hg.counter0 = n_counters;
+    for (const BatchClass& c : b->classes) {
+      auto beg = b->h_tasks.begin() + c.first, end = beg + c.n_tasks;
+      auto lo = std::lower_bound(beg, end, m0, by_m);
+      auto hi = std::lower_bound(lo, end, m1, by_m);
+      if (hi == lo) continue;
+      BatchClass gc = c;
+      gc.first = (int64_t)(lo - b->h_tasks.begin());
+      gc.n_tasks = (int64_t)(hi - lo);
+      // one block slot per SM left to the copy kernels, which run beside the class kernels
+      gc.grid = batched_class_grid(b->dtype, gc);
+      if (gc.grid <= 0) return cudaErrorInvalidValue;
+      hg.classes.push_back(gc);
+    }
+    n_counters += (int64_t)hg.classes.size();
+    auto s_lo = std::lower_bound(b->h_splits.begin(), b->h_splits.end(), m0, split_m);
+    auto s_hi = std::lower_bound(s_lo, b->h_splits.end(), m1, split_m);
+    hg.split0 = (int64_t)(s_lo - b->h_splits.begin());
+    hg.n_splits = (int64_t)(s_hi - s_lo);
+    auto q_lo = std::lower_bound(b->h_bsplits.begin(), b->h_bsplits.end(), m0, split_m);
+    auto q_hi = std::lower_bound(q_lo, b->h_bsplits.end(), m1, split_m);
+    hg.bsplit0 = (int64_t)(q_lo - b->h_bsplits.begin());
+    hg.n_bsplits = (int64_t)(q_hi - q_lo);
+    b->groups.push_back(std::move(hg));
+    m0 = m1;
+  }
+  cudaError_t e = dev_malloc((void**)&b->d_gcounters, sizeof(unsigned long long) * (size_t)std::max<int64_t>(n_counters, 1));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->copy_in, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->copy_out, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_start, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fin, cudaEventDisableTiming);
+  for (size_t g = 0; g < b->groups.size() && e == cudaSuccess; ++g) {
+    cudaEvent_t x = nullptr, y = nullptr;
+    e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
+    if (e == cudaSuccess) b->ev_in.push_back(x);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&y, cudaEventDisableTiming);
+    if (e == cudaSuccess) b->ev_out.push_back(y);
+  }
+  if (e != cudaSuccess) b->groups.clear();  // built again (and the rest freed with the plan)
+  return e;
+}
+
+// Host <-> device copy of a matrix of `rows` rows of `width` bytes (pitches in bytes): one
+// plain copy when both sides are dense.
+cudaError_t copy_rows(void* dst, size_t dpitch, const void* src, size_t spitch, size_t width, size_t rows,
+                      cudaMemcpyKind kind, cudaStream_t s) {
+  if (rows == 0 || width == 0) return cudaSuccess;
+  if (dpitch == width && spitch == width) return cudaMemcpyAsync(dst, src, width * rows, kind, s);
+  return cudaMemcpy2DAsync(dst, dpitch, src, spitch, width, rows, kind, s);
+}
+
+}  // namespace
+
 loops_status loops_spmm_batched_host(loops_plan_t p, const void* const* Bs_host, const int64_t* ldbs,
                                      void* const* Cs_host, const int64_t* ldcs, loops_stream_t stream) {
   clear_error();
@@ -770,29 +892,71 @@ loops_status loops_spmm_batched_host(loops_plan_t p, const void* const* Bs_host,
   BatchState* b = p->batch;
   if (b->count && (!Bs_host || !Cs_host || !ldbs || !ldcs)) { set_error("NULL batch array"); return LOOPS_ERR_INVALID_ARG; }
   const int64_t eb = b->dtype == LOOPS_F32 ? 4 : 2;
-  // staging layout: B of every matrix (n_cols x N, dense), then C of every matrix, each
-  // starting on a 256-byte boundary
-  std::vector<int64_t> boff((size_t)b->count), coff((size_t)b->count);
-  int64_t off = 0;
   for (int32_t m = 0; m < b->count; ++m) {
     const loops_plan_s* sp = b->subs[(size_t)m];
     if (ldbs[m] < sp->N || ldcs[m] < sp->N || (!Bs_host[m] && sp->n_cols > 0) || (!Cs_host[m] && sp->n_rows > 0)) {
       set_error("bad host operand of matrix " + std::to_string(m));
       return LOOPS_ERR_INVALID_ARG;
     }
-    if (sp->n_cols > 0 && sp->N > (INT32_MAX / sp->n_cols)) {
-      set_error("batched SpMM indexes B with 32-bit offsets: n_cols x N must stay below 2^31 (matrix " +
+    if (sp->n_cols > 0 && ldbs[m] > (INT32_MAX / sp->n_cols)) {
+      set_error("batched SpMM indexes B with 32-bit offsets: n_cols x ldb must stay below 2^31 (matrix " +
                 std::to_string(m) + ")");
       return LOOPS_ERR_UNSUPPORTED;
     }
-    boff[(size_t)m] = off;
-    off += (sp->n_cols * sp->N * eb + 255) / 256 * 256;
   }
-  for (int32_t m = 0; m < b->count; ++m) {
+  if (b->count == 0) return cuda_status(cudaStreamSynchronize((cudaStream_t)stream), "batched host call");
+  if (b->groups.empty()) {
+    cudaError_t e = build_host_groups(b);
+    if (e != cudaSuccess) return cuda_status(e, "batched host pipeline setup");
+  }
+  // Staging layout: every B, then every C. A matrix with dense host rows whose host operand
+  // directly follows the previous matrix's in the same group (one host arena) keeps that
+  // offset in the staging area too, so the run moves in one copy that touches no byte outside
+  // the operands. Other matrices start on a 256-byte boundary and copy on their own: B with
+  // its host pitch when that is a 16-byte multiple (one plain copy of its own storage), else
+  // into dense rows; C always into dense rows.
+  const int32_t cnt = b->count;
+  std::vector<int64_t> boff((size_t)cnt), coff((size_t)cnt), ldB((size_t)cnt), ldC((size_t)cnt);
+  std::vector<uint8_t> brun((size_t)cnt), crun((size_t)cnt);  // 1: continues the previous matrix's run
+  std::vector<int32_t> grp((size_t)cnt);
+  for (size_t g = 0; g < b->groups.size(); ++g)
+    for (int32_t m = b->groups[g].m0; m < b->groups[g].m1; ++m) grp[(size_t)m] = (int32_t)g;
+  auto host_span = [](const void* p0, int64_t bytes) { return static_cast<const char*>(p0) + bytes; };
+  int64_t off = 0;
+  for (int32_t m = 0; m < cnt; ++m) {
     const loops_plan_s* sp = b->subs[(size_t)m];
-    coff[(size_t)m] = off;
-    off += (sp->n_rows * sp->N * 4 + 255) / 256 * 256;
+    const loops_plan_s* pp = m > 0 ? b->subs[(size_t)m - 1] : nullptr;
+    const bool pitched_ok = (ldbs[m] * eb) % 16 == 0;
+    brun[(size_t)m] = m > 0 && grp[(size_t)m] == grp[(size_t)m - 1] && ldbs[m] == sp->N && ldbs[m - 1] == pp->N &&
+                      pitched_ok && sp->n_cols > 0 && pp->n_cols > 0 &&
+                      Bs_host[m] == host_span(Bs_host[m - 1], pp->n_cols * pp->N * eb);
+    if (brun[(size_t)m]) {
+      boff[(size_t)m] = boff[(size_t)m - 1] + pp->n_cols * ldbs[m - 1] * eb;
+      ldB[(size_t)m] = ldbs[m];
+    } else {
+      off = (off + 255) / 256 * 256;
+      boff[(size_t)m] = off;
+      // a run may start here: keep the host pitch when it is a 16-byte multiple
+      ldB[(size_t)m] = pitched_ok ? ldbs[m] : sp->N;
+    }
+    off = boff[(size_t)m] + sp->n_cols * ldB[(size_t)m] * eb;
   }
+  for (int32_t m = 0; m < cnt; ++m) {
+    const loops_plan_s* sp = b->subs[(size_t)m];
+    const loops_plan_s* pp = m > 0 ? b->subs[(size_t)m - 1] : nullptr;
+    crun[(size_t)m] = m > 0 && grp[(size_t)m] == grp[(size_t)m - 1] && ldcs[m] == sp->N && ldcs[m - 1] == pp->N &&
+                      sp->n_rows > 0 && pp->n_rows > 0 && (sp->N * 4) % 16 == 0 &&
+                      Cs_host[m] == host_span(Cs_host[m - 1], pp->n_rows * pp->N * 4);
+    if (crun[(size_t)m]) {
+      coff[(size_t)m] = coff[(size_t)m - 1] + pp->n_rows * pp->N * 4;
+    } else {
+      off = (off + 255) / 256 * 256;
+      coff[(size_t)m] = off;
+    }
+    ldC[(size_t)m] = sp->N;
+    off = coff[(size_t)m] + sp->n_rows * sp->N * 4;
+  }
+  off = (off + 255) / 256 * 256;
   if (off > b->stage_bytes) {
     if (b->stage) {
       cudaDeviceSynchronize();
@@ -805,30 +969,92 @@ loops_status loops_spmm_batched_host(loops_plan_t p, const void* const* Bs_host,
     b->stage_bytes = off;
   }
   cudaStream_t s = (cudaStream_t)stream;
-  std::vector<const void*> dB((size_t)b->count);
-  std::vector<void*> dC((size_t)b->count);
-  std::vector<int64_t> ldB((size_t)b->count), ldC((size_t)b->count);
+  std::vector<const void*> dB((size_t)cnt);
+  std::vector<void*> dC((size_t)cnt);
   char* base = static_cast<char*>(b->stage);
-  cudaError_t e = cudaSuccess;
-  for (int32_t m = 0; m < b->count && e == cudaSuccess; ++m) {
-    const loops_plan_s* sp = b->subs[(size_t)m];
+  for (int32_t m = 0; m < cnt; ++m) {
     dB[(size_t)m] = base + boff[(size_t)m];
     dC[(size_t)m] = base + coff[(size_t)m];
-    ldB[(size_t)m] = ldC[(size_t)m] = sp->N;
-    if (sp->n_cols > 0)
-      e = cudaMemcpy2DAsync(base + boff[(size_t)m], (size_t)(sp->N * eb), Bs_host[m], (size_t)(ldbs[m] * eb),
-                            (size_t)(sp->N * eb), (size_t)sp->n_cols, cudaMemcpyHostToDevice, s);
   }
-  if (e != cudaSuccess) return cuda_status(e, "copy of B to the device");
-  if ((st = spmm_batch(b, dB.data(), ldB.data(), dC.data(), ldC.data(), nullptr, s))) return st;
-  for (int32_t m = 0; m < b->count && e == cudaSuccess; ++m) {
+  cudaError_t e = refresh_descs(b, dB.data(), ldB.data(), dC.data(), ldC.data(), nullptr, s);
+  if (e != cudaSuccess) return cuda_status(e, "descriptor upload");
+  // three streams: copies in (every group's B, in order), the kernels on `stream` (group g
+  // once its B is in), copies out (group g's C once its kernels are done)
+  e = cudaEventRecord(b->ev_start, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(b->copy_in, b->ev_start, 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(b->copy_out, b->ev_start, 0);
+  // copy of B for matrices [m, end of its run): one plain copy of the run's host span, or
+  // the matrix alone (pitched into dense staging rows when its host pitch is not kept)
+  auto copy_in_from = [&](int32_t m, int32_t m1, int32_t* next) -> cudaError_t {
     const loops_plan_s* sp = b->subs[(size_t)m];
-    if (sp->n_rows > 0)
-      e = cudaMemcpy2DAsync(Cs_host[m], (size_t)(ldcs[m] * 4), base + coff[(size_t)m], (size_t)(sp->N * 4),
-                            (size_t)(sp->N * 4), (size_t)sp->n_rows, cudaMemcpyDeviceToHost, s);
+    int32_t k = m + 1;
+    int64_t bytes = sp->n_cols * ldB[(size_t)m] * eb;
+    if (ldB[(size_t)m] == ldbs[m]) {
+      while (k < m1 && brun[(size_t)k]) bytes += b->subs[(size_t)k]->n_cols * ldbs[k] * eb, ++k;
+      // a lone pitched matrix: its last row is read only up to its N columns (runs are dense)
+      if (sp->n_cols > 0) bytes -= (ldbs[m] - sp->N) * eb;
+    }
+    *next = k;
+    if (sp->n_cols == 0) return cudaSuccess;
+    if (ldB[(size_t)m] == ldbs[m])
+      return cudaMemcpyAsync(base + boff[(size_t)m], Bs_host[m], (size_t)bytes, cudaMemcpyHostToDevice, b->copy_in);
+    return copy_rows(base + boff[(size_t)m], (size_t)(sp->N * eb), Bs_host[m], (size_t)(ldbs[m] * eb),
+                     (size_t)(sp->N * eb), (size_t)sp->n_cols, cudaMemcpyHostToDevice, b->copy_in);
+  };
+  auto copy_out_from = [&](int32_t m, int32_t m1, int32_t* next) -> cudaError_t {
+    const loops_plan_s* sp = b->subs[(size_t)m];
+    int32_t k = m + 1;
+    int64_t bytes = sp->n_rows * sp->N * 4;
+    while (k < m1 && crun[(size_t)k]) bytes += b->subs[(size_t)k]->n_rows * b->subs[(size_t)k]->N * 4, ++k;
+    *next = k;
+    if (k > m + 1)  // a dense run: one plain copy
+      return cudaMemcpyAsync(Cs_host[m], base + coff[(size_t)m], (size_t)bytes, cudaMemcpyDeviceToHost, b->copy_out);
+    return copy_rows(Cs_host[m], (size_t)(ldcs[m] * 4), base + coff[(size_t)m], (size_t)(sp->N * 4),
+                     (size_t)(sp->N * 4), (size_t)sp->n_rows, cudaMemcpyDeviceToHost, b->copy_out);
+  };
+  for (size_t g = 0; g < b->groups.size() && e == cudaSuccess; ++g) {
+    const BatchState::HostGroup& hg = b->groups[g];
+    for (int32_t m = hg.m0, nx = 0; m < hg.m1 && e == cudaSuccess; m = nx) e = copy_in_from(m, hg.m1, &nx);
+    if (e == cudaSuccess) e = cudaEventRecord(b->ev_in[g], b->copy_in);
   }
+  // on a failure, no copy may still be reading or writing the caller's buffers on return
+  auto drain = [&](cudaError_t err, const char* what) {
+    cudaStreamSynchronize(b->copy_in);
+    cudaStreamSynchronize(b->copy_out);
+    cudaStreamSynchronize(s);
+    return cuda_status(err, what);
+  };
+  if (e != cudaSuccess) return drain(e, "copy of B to the device");
+  for (size_t g = 0; g < b->groups.size() && e == cudaSuccess; ++g) {
+    const BatchState::HostGroup& hg = b->groups[g];
+    e = cudaStreamWaitEvent(s, b->ev_in[g], 0);
+    if (e == cudaSuccess) {
+      BatchLaunch L;
+      L.descs = b->d_desc;
+      L.tasks = b->d_tasks;
+      L.classes = hg.classes.data();
+      L.n_classes = (int)hg.classes.size();
+      L.counters = b->d_gcounters + hg.counter0;
+      L.splits = b->d_splits + hg.split0;
+      L.n_splits = hg.n_splits;
+      L.bsplits = b->d_bsplits + hg.bsplit0;
+      L.n_bsplits = hg.n_bsplits;
+      L.tev = nullptr;
+      L.n_side = (int)b->side.size();
+      L.side = b->side.data();
+      L.fork = b->ev_fork;
+      L.join = b->ev_join.data();
+      e = launch_batched(b->dtype, L, s);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(b->ev_out[g], s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->copy_out, b->ev_out[g], 0);
+    for (int32_t m = hg.m0, nx = 0; m < hg.m1 && e == cudaSuccess; m = nx) e = copy_out_from(m, hg.m1, &nx);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(b->ev_fin, b->copy_out);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->ev_fin, 0);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  return cuda_status(e, "copy of C to the host");
+  if (e != cudaSuccess) return drain(e, "batched host call");
+  return LOOPS_OK;
 }
 
 loops_status loops_plan_batched_info(loops_plan_t p, int32_t* count, int64_t* n_tasks, double* tau,

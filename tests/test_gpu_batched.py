@@ -134,6 +134,79 @@ def test_batched_split_rows_and_column_scales(lp):
     assert max(errs) <= TOL["bf16"], errs
 
 
+@pytest.mark.parametrize("fmt", ["f32", "bf16"])
+def test_batched_host_call_pipeline(lp, fmt):
+    """The end-to-end call with host buffers (groups of matrices whose copies in, kernels and
+    copies out overlap) gives the device call's product for every matrix: pinned and pageable
+    host memory, padded host rows, split rows and split blocks in several groups, repeated
+    calls and fresh buffers."""
+    mats = W.batched_mix(count=21, seed=13, min_rows=100, max_rows=2500)
+
+    def with_long_row(A):
+        n = A.n_rows
+        r = np.concatenate([A.row_ids(), np.full(n, n // 3)])
+        c = np.concatenate([A.col_idx.astype(np.int64), np.arange(n)])
+        v = np.concatenate([A.vals, np.ones(n) * 0.25])
+        return W.csr_from_coo(n, n, r, c, v)
+
+    out = []
+    for k, (A, N) in enumerate(mats):
+        if k % 4 == 1:      # sparse rows around a long one: a CSR row split into segments
+            A = with_long_row(W.random_csr(3000, 3000, 8 / 3000, 100 + k))
+        elif k % 4 == 3:    # dense rows around a long one: a BCSR block cut into units
+            A = with_long_row(W.random_csr(300, 300, 0.1, 100 + k))
+        out.append((A, N))
+    plan, Bs, Cs, refs, errs = _run(lp, out, fmt, 1.5, split_len=64)
+    assert max(errs) <= TOL[fmt], errs
+    st = plan.stats()
+    assert st["n_split_rows"] > 0 and st["n_split_blocks"] > 0, st
+    def separate(pinned, pad):
+        Bh, Ch, keep = [], [], []
+        for B, C in zip(Bs, Cs):
+            hb = torch.zeros((B.shape[0], B.shape[1] + pad), dtype=B.dtype, pin_memory=pinned)
+            hb[:, : B.shape[1]] = B.cpu()
+            Bh.append(hb[:, : B.shape[1]])
+            hc = torch.full((C.shape[0], C.shape[1] + pad), 7.0, pin_memory=pinned)
+            Ch.append(hc[:, : C.shape[1]])
+            keep.append(hc)
+        return Bh, Ch, keep
+
+    def arena(pinned):
+        # one host buffer for all B and one for all C, operands back to back (runs copied in
+        # one piece), except matrix 5, whose C rows are padded and whose B sits after a gap
+        eb = Bs[0].element_size()
+        nb = sum(B.numel() for B in Bs) + 64
+        nc = sum(C.shape[0] * (C.shape[1] + 4) for C in Cs)
+        hb = torch.zeros(nb, dtype=Bs[0].dtype, pin_memory=pinned)
+        hc = torch.full((nc,), 7.0, pin_memory=pinned)
+        Bh, Ch, ob, oc = [], [], 0, 0
+        for m, (B, C) in enumerate(zip(Bs, Cs)):
+            if m == 5:
+                ob += 64 // eb
+            v = hb[ob: ob + B.numel()].view(B.shape)
+            v.copy_(B.cpu())
+            Bh.append(v)
+            ob += B.numel()
+            w = C.shape[1] + (4 if m == 5 else 0)
+            Ch.append(hc[oc: oc + C.shape[0] * w].view(C.shape[0], w)[:, : C.shape[1]])
+            oc += C.shape[0] * w
+        return Bh, Ch, [hc]
+
+    layouts = [("pinned", separate(True, 0)), ("pageable", separate(False, 0)), ("pinned padded", separate(True, 8)),
+               ("pinned arena", arena(True)), ("pageable arena", arena(False))]
+    for name, (Bh, Ch, keep) in layouts:
+        plan.spmm_host(Bh, Ch)
+        for m, (C, hc, r) in enumerate(zip(Cs, Ch, refs)):
+            assert torch.equal(hc, C.cpu()), (name, m)     # same kernels, same order: bit for bit
+            assert rel_l2(hc.double().numpy(), r) <= TOL[fmt]
+        # no byte of the host buffers outside the C operands was written
+        written = sum(C.numel() for C in Ch)
+        assert sum(int((k == 7.0).sum()) for k in keep) >= sum(k.numel() for k in keep) - written, name
+        if name.startswith("pinned padded"):
+            assert all(bool((k[:, -8:] == 7.0).all()) for k in keep)
+    plan.destroy()
+
+
 def test_batched_rejects_unsupported_n(lp):
     A = W.random_csr(50, 50, 0.1, 1)
     with pytest.raises(lp.LoopsError):
