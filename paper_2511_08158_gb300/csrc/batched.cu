@@ -27,9 +27,9 @@
 #include "loops_internal.h"
 
 // Tuning knobs (compile time): resident blocks per SM the CSR class kernels must allow (their
-// register caps: FP32, 16-bit), B-row loads in flight
-// per lane in FP32 CSR items (a power of two), the same for the FFMA class kernels, tiles in
-// flight in B_r = 8 FFMA units, and cp.async stages of the HMMA units.
+// register caps: FP32, 16-bit), B-row loads in flight per lane in FP32 and in 16-bit CSR items
+// (powers of two), the same for the FFMA class kernels, tiles in flight in B_r = 8 FFMA units,
+// and cp.async stages of the HMMA units.
 #ifndef LOOPS_BATCHED_CSR_MIN_BLOCKS
 #define LOOPS_BATCHED_CSR_MIN_BLOCKS 3
 #endif
@@ -39,6 +39,11 @@
 #ifndef LOOPS_BATCHED_CSR_LOADS
 #define LOOPS_BATCHED_CSR_LOADS 8
 #endif
+#ifndef LOOPS_BATCHED_CSR16_LOADS
+#define LOOPS_BATCHED_CSR16_LOADS 4
+#endif
+static_assert(LOOPS_BATCHED_CSR16_LOADS >= 1 && (LOOPS_BATCHED_CSR16_LOADS & (LOOPS_BATCHED_CSR16_LOADS - 1)) == 0,
+              "16-bit CSR loads in flight must be a power of two");
 static_assert(LOOPS_BATCHED_CSR_LOADS >= 2 && (LOOPS_BATCHED_CSR_LOADS & (LOOPS_BATCHED_CSR_LOADS - 1)) == 0,
               "CSR loads in flight must be a power of two: the load batches tile a chunk exactly");
 #ifndef LOOPS_BATCHED_FFMA_TILES
@@ -103,12 +108,13 @@ __device__ __forceinline__ void csr_item(const BatchDesc& d, int64_t item, int s
   using TB = typename Tr::TB;
   using TAcc = typename Tr::TAcc;
   using TC = typename Tr::TC;
+  using TV = typename Tr::TV;
   constexpr int VE = Tr::kVE;
   constexpr int R = G >= 8 ? 1 : (G >= 2 ? 8 / G : 4);  // chunks of at least 4-8 entries
   constexpr int CH = G * R;                             // entries per chunk
-  // B loads in flight per lane: 8 for FP32 rows, 4 for 16-bit (whose unpacked vectors take
-  // twice the registers), half that with two vectors per lane
-  constexpr int UMAX = (VE == 8 ? LOOPS_BATCHED_CSR_LOADS / 2 : LOOPS_BATCHED_CSR_LOADS) / VPL;
+  // B loads in flight per lane (FP32 and 16-bit rows, each a power of two), half that with two
+  // vectors per lane
+  constexpr int UMAX = (VE == 8 ? LOOPS_BATCHED_CSR16_LOADS : LOOPS_BATCHED_CSR_LOADS) / VPL;
   constexpr int U = UMAX < CH ? UMAX : CH;
   static_assert(U >= 1 && CH % U == 0, "load batches must tile the chunk");
   // 32-bit indices inside the item and inside B (the batched call keeps every B below 2^31
@@ -134,36 +140,30 @@ __device__ __forceinline__ void csr_item(const BatchDesc& d, int64_t item, int s
 #pragma unroll
     for (int e = 0; e < VE; ++e) acc[p][e] = TAcc(0);
 
-  auto fetch = [&](int32_t k0, int32_t (&c)[R], TAcc (&v)[R]) {
+  auto fetch = [&](int32_t k0, int32_t (&c)[R], TV (&v)[R]) {
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int32_t k = k0 + r * G + sub;
       c[r] = 0;
-      v[r] = TAcc(0);
+      v[r] = TV(0);
       if (k < len) {
         c[r] = __ldg(colp + k);
-        v[r] = Tr::to_acc(valp[k]);
+        v[r] = Tr::load_v(valp + k);
       }
     }
   };
-  auto fma_vec = [&](int p, const uint4& bv, TAcc a) {
-    TAcc b[VE];
-    unpack16<Tr>(bv, b);
-#pragma unroll
-    for (int e = 0; e < VE; ++e) acc[p][e] = fma(a, b[e], acc[p][e]);
-  };
   int32_t c[R];
-  TAcc v[R];
+  TV v[R];
   fetch(0, c, v);
   for (int32_t k0 = 0; k0 < len; k0 += CH) {
     int32_t cn[R];
-    TAcc vn[R];
+    TV vn[R];
     fetch(k0 + CH, cn, vn);                             // next chunk's entries, in flight now
     if (k0 + CH <= len) {                               // full chunk: batches of U loads, then FMAs
 #pragma unroll
       for (int e0 = 0; e0 < CH; e0 += U) {
         uint4 bv[U][VPL];
-        TAcc av[U];
+        TV av[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           const int e = e0 + u;
@@ -175,7 +175,7 @@ __device__ __forceinline__ void csr_item(const BatchDesc& d, int64_t item, int s
 #pragma unroll
         for (int u = 0; u < U; ++u)
 #pragma unroll
-          for (int p = 0; p < VPL; ++p) fma_vec(p, bv[u][p], av[u]);
+          for (int p = 0; p < VPL; ++p) fma_vec<Tr>(acc[p], bv[u][p], av[u]);
       }
     } else {                                            // the last, partial chunk
       // the same batches under predicates: entries past the row's end load nothing and carry
@@ -186,7 +186,7 @@ __device__ __forceinline__ void csr_item(const BatchDesc& d, int64_t item, int s
       for (int e0 = 0; e0 < CH; e0 += U) {
         if (e0 < cnt) {
           uint4 bv[U][VPL];
-          TAcc av[U];
+          TV av[U];
 #pragma unroll
           for (int u = 0; u < U; ++u) {
             const int e = e0 + u;
@@ -198,7 +198,7 @@ __device__ __forceinline__ void csr_item(const BatchDesc& d, int64_t item, int s
 #pragma unroll
           for (int u = 0; u < U; ++u)
 #pragma unroll
-            for (int p = 0; p < VPL; ++p) fma_vec(p, bv[u][p], av[u]);
+            for (int p = 0; p < VPL; ++p) fma_vec<Tr>(acc[p], bv[u][p], av[u]);
         }
       }
     }

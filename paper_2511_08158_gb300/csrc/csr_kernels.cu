@@ -87,6 +87,7 @@ __global__ void __launch_bounds__(256, (csr_min_blocks<Tr, VPL>())) csr_spmm_vec
   using TB = typename Tr::TB;
   using TAcc = typename Tr::TAcc;
   using TC = typename Tr::TC;
+  using TV = typename Tr::TV;
   constexpr int VE = Tr::kVE;
   const int lane = threadIdx.x & 31;
   const int sub = lane & (G - 1);
@@ -117,28 +118,28 @@ __global__ void __launch_bounds__(256, (csr_min_blocks<Tr, VPL>())) csr_spmm_vec
   // unpacking needs the registers, and FP64, bound by its FMA pipe, load them in turn
   constexpr bool kPrefetch = std::is_same<Tr, TrF32>::value;
   int32_t c_next = 0;
-  TAcc v_next = TAcc(0);
+  TV v_next = TV(0);
   if (kPrefetch && beg + sub < end) {
     c_next = __ldg(a.col + beg + sub);
-    v_next = Tr::to_acc(vals[beg + sub]);
+    v_next = Tr::load_v(vals + beg + sub);
   }
   for (int64_t k0 = beg; k0 < end; k0 += G) {
     int32_t c = c_next;
-    TAcc v = v_next;
+    TV v = v_next;
     const int64_t kn = kPrefetch ? k0 + G + sub : k0 + sub;
     if (kn < end) {
       c_next = __ldg(a.col + kn);
-      v_next = Tr::to_acc(vals[kn]);
+      v_next = Tr::load_v(vals + kn);
     }
     if constexpr (!kPrefetch) {
       c = kn < end ? c_next : 0;
-      v = kn < end ? v_next : TAcc(0);
+      v = kn < end ? v_next : TV(0);
     }
     const int cnt = (int)(end - k0 < (int64_t)G ? end - k0 : (int64_t)G);  // uniform in the group
     int j0 = 0;
     for (; j0 + U <= cnt; j0 += U) {  // full batches: U loads in flight, then U FMAs each
       uint4 bv[U][VPL];
-      TAcc av[U];
+      TV av[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int cj = __shfl_sync(gmask, c, (j0 + u) & (G - 1), G);
@@ -150,25 +151,20 @@ __global__ void __launch_bounds__(256, (csr_min_blocks<Tr, VPL>())) csr_spmm_vec
 #pragma unroll
       for (int u = 0; u < U; ++u)
 #pragma unroll
-        for (int p = 0; p < VPL; ++p) {
-          TAcc b[VE];
-          unpack16<Tr>(bv[u][p], b);
-#pragma unroll
-          for (int e = 0; e < VE; ++e) acc[p][e] = fma(av[u], b[e], acc[p][e]);
-        }
+        for (int p = 0; p < VPL; ++p) fma_vec<Tr>(acc[p], bv[u][p], av[u]);
     }
     if constexpr (U > 1) {
     if (j0 < cnt) {  // tail of 1 .. U-1 entries: one batch under predicates
       // entries past the tail load nothing and take a zero value, so they add exact zeros;
       // the live loads issue together instead of one per round trip
       uint4 bv[U - 1][VPL];
-      TAcc av[U - 1];
+      TV av[U - 1];
 #pragma unroll
       for (int u = 0; u < U - 1; ++u) {
         const bool live = j0 + u < cnt;
         const int cj = __shfl_sync(gmask, c, (j0 + u) & (G - 1), G);
-        const TAcc vj = __shfl_sync(gmask, v, (j0 + u) & (G - 1), G);
-        av[u] = live ? vj : TAcc(0);
+        const TV vj = __shfl_sync(gmask, v, (j0 + u) & (G - 1), G);
+        av[u] = live ? vj : TV(0);
         const TB* brow = Bp + (int64_t)cj * a.ldb;
 #pragma unroll
         for (int p = 0; p < VPL; ++p) bv[u][p] = ldg16_if(live && colok[p], brow + coff[p]);
@@ -176,12 +172,7 @@ __global__ void __launch_bounds__(256, (csr_min_blocks<Tr, VPL>())) csr_spmm_vec
 #pragma unroll
       for (int u = 0; u < U - 1; ++u)
 #pragma unroll
-        for (int p = 0; p < VPL; ++p) {
-          TAcc b[VE];
-          unpack16<Tr>(bv[u][p], b);
-#pragma unroll
-          for (int e = 0; e < VE; ++e) acc[p][e] = fma(av[u], b[e], acc[p][e]);
-        }
+        for (int p = 0; p < VPL; ++p) fma_vec<Tr>(acc[p], bv[u][p], av[u]);
     }
     }
   }

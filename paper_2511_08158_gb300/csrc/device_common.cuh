@@ -10,29 +10,40 @@ namespace loops {
 
 // Element traits per plan dtype: storage type of A values and B (TB), accumulator (TAcc),
 // output (TC), and conversion of a stored element to the accumulator type.
+// TV is the register form of an A value in the SpMM inner loops (load_v reads one): the
+// accumulator type, or for the 16-bit formats the raw 16 bits, which the mixed-precision FMA
+// (fma_vec below) takes as they are.
 struct TrF64 {
-  using TB = double; using TAcc = double; using TC = double;
+  using TB = double; using TAcc = double; using TC = double; using TV = double;
   static constexpr bool kScaled = false;  // outputs carry 1/s_A and column scales
   static constexpr int kVE = 2;  // elements per 16-byte vector
   __device__ static __forceinline__ TAcc to_acc(TB x) { return x; }
+  __device__ static __forceinline__ TV load_v(const TB* p) { return *p; }
 };
 struct TrF32 {
-  using TB = float; using TAcc = float; using TC = float;
+  using TB = float; using TAcc = float; using TC = float; using TV = float;
   static constexpr bool kScaled = false;  // outputs carry 1/s_A and column scales
   static constexpr int kVE = 4;
   __device__ static __forceinline__ TAcc to_acc(TB x) { return x; }
+  __device__ static __forceinline__ TV load_v(const TB* p) { return *p; }
 };
 struct TrF16 {
-  using TB = __half; using TAcc = float; using TC = float;
+  using TB = __half; using TAcc = float; using TC = float; using TV = uint32_t;
   static constexpr bool kScaled = true;  // outputs carry 1/s_A and column scales
   static constexpr int kVE = 8;
   __device__ static __forceinline__ TAcc to_acc(TB x) { return __half2float(x); }
+  __device__ static __forceinline__ TV load_v(const TB* p) {
+    return *reinterpret_cast<const unsigned short*>(p);
+  }
 };
 struct TrBF16 {
-  using TB = __nv_bfloat16; using TAcc = float; using TC = float;
+  using TB = __nv_bfloat16; using TAcc = float; using TC = float; using TV = uint32_t;
   static constexpr bool kScaled = true;  // outputs carry 1/s_A and column scales
   static constexpr int kVE = 8;
   __device__ static __forceinline__ TAcc to_acc(TB x) { return __bfloat162float(x); }
+  __device__ static __forceinline__ TV load_v(const TB* p) {
+    return *reinterpret_cast<const unsigned short*>(p);
+  }
 };
 
 // binary64 -> storage type, round to nearest even (the stored-value rounding of a plan).
@@ -80,6 +91,40 @@ __device__ __forceinline__ void unpack16<TrBF16>(const uint4& v, float (&out)[8]
     out[2 * i] = __uint_as_float(w[i] << 16);
     out[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
   }
+}
+
+// acc[e] += a * (element e of the 16-byte vector v), one rounding per element. The 16-bit
+// formats use the mixed-precision FMA (16-bit operands, binary32 addend and result): the
+// product of two 16-bit values is exact in binary32, so this equals converting both operands
+// and one binary32 FMA, without the conversions.
+template <class Tr>
+__device__ __forceinline__ void fma_vec(typename Tr::TAcc (&acc)[Tr::kVE], const uint4& v, typename Tr::TV a) {
+  typename Tr::TAcc b[Tr::kVE];
+  unpack16<Tr>(v, b);
+#pragma unroll
+  for (int e = 0; e < Tr::kVE; ++e) acc[e] = fma(a, b[e], acc[e]);
+}
+template <>
+__device__ __forceinline__ void fma_vec<TrF16>(float (&acc)[8], const uint4& v, uint32_t a) {
+  const unsigned short a16 = (unsigned short)a;
+  const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    asm("{\n\t.reg .f16 lo, hi;\n\tmov.b32 {lo, hi}, %2;\n\t"
+        "fma.rn.f32.f16 %0, lo, %3, %0;\n\tfma.rn.f32.f16 %1, hi, %3, %1;\n\t}"
+        : "+f"(acc[2 * i]), "+f"(acc[2 * i + 1])
+        : "r"(w[i]), "h"(a16));
+}
+template <>
+__device__ __forceinline__ void fma_vec<TrBF16>(float (&acc)[8], const uint4& v, uint32_t a) {
+  const unsigned short a16 = (unsigned short)a;
+  const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    asm("{\n\t.reg .b16 lo, hi;\n\tmov.b32 {lo, hi}, %2;\n\t"
+        "fma.rn.f32.bf16 %0, lo, %3, %0;\n\tfma.rn.f32.bf16 %1, hi, %3, %1;\n\t}"
+        : "+f"(acc[2 * i]), "+f"(acc[2 * i + 1])
+        : "r"(w[i]), "h"(a16));
 }
 
 __device__ __forceinline__ uint4 ldg16(const void* p) {
