@@ -220,11 +220,15 @@ def new_events(torch, n):
 def time_steps(torch, fn, steps, warmup, flush, plan=None):
     """Per-step device times (ms) of fn() with the L2 flushed before each step, and (with a
     plan) the times between its timing events [0]-[1] and [2]-[3] in each step."""
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    pev = [new_events(torch, 4) for _ in range(steps)] if plan is not None else None
+    # the plan records timing events from the warm-up on, so a batched plan's graph already
+    # holds its event nodes (later steps only repoint them) before the timed steps
+    if plan is not None:
+        plan.set_timing_events([e.cuda_event for e in pev[0]])
     for _ in range(warmup):
         fn()
     torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-    pev = [new_events(torch, 4) for _ in range(steps)] if plan is not None else None
     stream = torch.cuda.current_stream()
     for k in range(steps):
         flush()
