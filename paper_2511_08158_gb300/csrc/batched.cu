@@ -26,10 +26,12 @@
 #include "device_common.cuh"
 #include "loops_internal.h"
 
-// Tuning knobs (compile time): resident blocks per SM the CSR class kernels must allow (their
-// register caps: FP32, 16-bit), B-row loads in flight per lane in FP32 and in 16-bit CSR items
-// (powers of two), the same for the FFMA class kernels, tiles in flight in B_r = 8 FFMA units,
-// and cp.async stages of the HMMA units.
+// Tuning knobs (compile time):
+// * resident blocks per SM the class kernels must allow (their register caps): CSR FP32, CSR
+//   16-bit, FFMA B_r 8, FFMA B_r 16 (its 64 accumulators per lane spill at 3 blocks);
+// * B-row loads in flight per lane in CSR items, FP32 and 16-bit (powers of two);
+// * tiles in flight in FFMA units, B_r 8 and B_r 16;
+// * cp.async stages of the HMMA units.
 #ifndef LOOPS_BATCHED_CSR_MIN_BLOCKS
 #define LOOPS_BATCHED_CSR_MIN_BLOCKS 3
 #endif
@@ -54,6 +56,12 @@ static_assert(LOOPS_BATCHED_CSR_LOADS >= 2 && (LOOPS_BATCHED_CSR_LOADS & (LOOPS_
 #endif
 #ifndef LOOPS_BATCHED_FFMA_MIN_BLOCKS
 #define LOOPS_BATCHED_FFMA_MIN_BLOCKS 3
+#endif
+#ifndef LOOPS_BATCHED_FFMA16_MIN_BLOCKS
+#define LOOPS_BATCHED_FFMA16_MIN_BLOCKS 2
+#endif
+#ifndef LOOPS_BATCHED_FFMA16_TILES
+#define LOOPS_BATCHED_FFMA16_TILES 2
 #endif
 
 namespace loops {
@@ -258,7 +266,7 @@ __global__ void __launch_bounds__(256, csr_min_blocks<Tr>()) batched_csr(const B
 // T tiles' B vectors and A values are loaded before their FMAs.
 template <int BR, int G>
 __device__ __forceinline__ void ffma_unit(const BatchDesc& d, int64_t u, int sub) {
-  constexpr int T = BR == 8 ? LOOPS_BATCHED_FFMA_TILES : 2;
+  constexpr int T = BR == 8 ? LOOPS_BATCHED_FFMA_TILES : LOOPS_BATCHED_FFMA16_TILES;
   const int32_t b = d.unit_block[u];
   const int64_t rb = d.rb_id[b];
   const int64_t t0 = d.unit_t0[u], t1 = d.unit_t1[u];
@@ -336,7 +344,8 @@ __device__ __forceinline__ void ffma_unit(const BatchDesc& d, int64_t u, int sub
 }
 
 template <int BR, int G>
-__global__ void __launch_bounds__(256, LOOPS_BATCHED_FFMA_MIN_BLOCKS) batched_ffma(const BatchDesc* __restrict__ descs,
+__global__ void __launch_bounds__(256, BR == 8 ? LOOPS_BATCHED_FFMA_MIN_BLOCKS : LOOPS_BATCHED_FFMA16_MIN_BLOCKS)
+    batched_ffma(const BatchDesc* __restrict__ descs,
                                                        const BatchTask* __restrict__ tasks, int64_t n_tasks,
                                                        unsigned long long* counter) {
   const int lane = threadIdx.x & 31;
