@@ -69,6 +69,8 @@ def parse(argv=None):
                     help="batched: number of matrices (smaller counts give small profiling cases)")
     ap.add_argument("--batch-kinds", default="all", choices=["all", "uniform", "banded", "blocks"],
                     help="batched: keep only the matrices of one structure (index mod 3), for profiling cases")
+    ap.add_argument("--block-rows", type=int, default=0,
+                    help="batched: B_r of the plan (0: autotuned, or the default with a fixed --tau)")
     ap.add_argument("--tau", type=float, default=-1.0,
                     help="batched: split threshold of the timed plan (default -1: autotuned)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -312,7 +314,7 @@ def run_batched(args, torch, lp, flush, rank, world, hbm_peak, hbm_src):
     Cd = [torch.empty((A.n_rows, N), device="cuda") for A, N in mats]
 
     t0 = time.perf_counter()
-    plan = lp.BatchedPlan(As, Ns, fmt, tau=args.tau)
+    plan = lp.BatchedPlan(As, Ns, fmt, tau=args.tau, block_rows=args.block_rows)
     plan_s = time.perf_counter() - t0
     st = plan.stats()
 
