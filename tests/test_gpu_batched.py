@@ -207,6 +207,35 @@ def test_batched_host_call_pipeline(lp, fmt):
     plan.destroy()
 
 
+@pytest.mark.parametrize("fmt", ["f32", "bf16"])
+def test_batched_degenerate_matrices(lp, fmt):
+    """Degenerate members of a batch, beside ordinary ones: an all-zero matrix, one without
+    rows, a 1 x 1 matrix, rows empty everywhere but a few with one long (split) row, and a
+    ragged rectangular one; the device call and the host call give the oracle's product."""
+    n = 261
+    rows = np.concatenate([np.zeros(n, np.int64), [5, 5, 100, 260]])
+    cols = np.concatenate([np.arange(n), [3, 3, 7, 260]])
+    vals = np.random.default_rng(2).standard_normal(rows.size)
+    mats = [
+        (W.csr_from_coo(40, 30, np.zeros(0), np.zeros(0), np.zeros(0)), 16),
+        (W.batched_mix(count=1, seed=3, min_rows=500, max_rows=600)[0][0], 32),
+        (W.csr_from_coo(0, 30, np.zeros(0), np.zeros(0), np.zeros(0)), 16),
+        (W.csr_from_coo(1, 1, np.zeros(1, np.int64), np.zeros(1, np.int64), np.array([1.5])), 16),
+        (W.csr_from_coo(n, n, rows, cols, vals), 48),
+        (W.random_csr(97, 89, 0.1, 8), 64),
+    ]
+    for tau in (0.0, 2.0, math.inf):
+        plan, Bs, Cs, refs, errs = _run(lp, mats, fmt, tau, split_len=32)
+        assert max(errs) <= TOL[fmt], errs
+        assert bool((Cs[0] == 0).all()) and tuple(Cs[2].shape) == (0, 16)
+        Bh = [B.cpu().pin_memory() for B in Bs]
+        Ch = [torch.full(tuple(C.shape), float("nan")).pin_memory() for C in Cs]
+        plan.spmm_host(Bh, Ch)
+        for m, (C, hc) in enumerate(zip(Cs, Ch)):
+            assert torch.equal(hc, C.cpu()), (tau, m)
+        plan.destroy()
+
+
 def test_batched_rejects_unsupported_n(lp):
     A = W.random_csr(50, 50, 0.1, 1)
     with pytest.raises(lp.LoopsError):
