@@ -55,7 +55,7 @@ BATCH_COUNT, BATCH_SEED = 512, 5
 def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["loops", "reference"], default="loops")
     ap.add_argument("--workload", choices=["batched", "laplacian", "rmat", "gcn", "uniform", "mixed"],
