@@ -45,7 +45,7 @@ typedef enum {
   LOOPS_OK = 0,
   LOOPS_ERR_INVALID_ARG = 1,  /* null pointer, negative size, bad leading dimension, ... */
   LOOPS_ERR_INVALID_CSR = 2,  /* row_ptr not monotone / wrong ends, column out of range  */
-  LOOPS_ERR_UNSUPPORTED = 3,  /* dtype or size this build does not handle               */
+  LOOPS_ERR_UNSUPPORTED = 3,  /* dtype or size the library does not handle              */
   LOOPS_ERR_OOM = 4,          /* a host or device allocation failed                     */
   LOOPS_ERR_CUDA = 5,         /* a CUDA runtime call failed (message in last_error)     */
   LOOPS_ERR_TIMEOUT = 6,      /* a bounded device-side wait gave up (see loops_plan_check) */
